@@ -1,0 +1,199 @@
+"""One step of the perturbed preconditioned inverse iteration (Alg. 2).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Readings of the paper used here:
+* Step size of Remark omegamin: with z_1 = Sx/||Sx||, z_2 = Sr/||Sr|| and the
+  lower eigenvector v of the 2x2 pencil, the update of Alg. 2 is
+  x* = (v_1/||Sx||) x + (v_2/||Sr||) r, i.e. omega = -(v_2 ||Sx||)/(v_1 ||Sr||);
+  the printed ratio ||Sr||/||Sx|| is inverted relative to that derivation.
+  v is scaled so that v^T G_E v = 1 (then ||x*||_A^2 = lambda_*) and v_1 > 0.
+* Delta_A solves sqrt(1 - D^2) - rho D = q in closed form,
+  D = (-q rho + sqrt(1 + rho^2 - q^2)) / (1 + rho^2).
+* Residual terms s_{k,k'} = S_k (H_gamma - lambda) S_{k'} x are formed from the
+  exact u_{k'} = (H_gamma - lambda) S_{k'} x; ties in the norm sort are broken
+  by (k, k') ascending.
+* The eta_res loop is capped at MAX_ETA_RETRIES passes.
+* Delta_A is clamped at 0: at machine precision lambda_* can exceed lambda^n,
+  q then exceeds 1 and the closed form turns (slightly) negative.
+"""
+
+import math
+
+import numpy as np
+
+from . import bsmps as B
+
+MAX_ETA_RETRIES = 60
+
+
+class SolverParams:
+    def __init__(self, c, delta, eps_num=None, t_eig=0.5, tau=1e-8):
+        self.c = c                      # spectral equivalence constant, Eq. (specequivA)
+        self.delta = delta              # gap bound delta >= lambda_2/(lambda_2 - lambda_1)
+        self.eps_num = 0.5 * (1.0 - c) if eps_num is None else eps_num   # Sec. 7.1.3
+        self.t_eig = t_eig
+        self.tau = tau
+
+    @property
+    def zeta_res(self):
+        return self.eps_num / (1.0 + self.c)     # Lemma truncr
+
+
+class SolverState:
+    def __init__(self):
+        self.eta_res = math.inf
+        self.n = 0
+        self.history = []
+
+
+def pair_sums(a, b, prec, mpo=None):
+    """sum_{k,k'} <O S_k a, S_k' b> with O = mpo (H_gamma) or the identity (Eq. (exactrq))."""
+    tot = 0.0
+    for k in range(prec.n_terms):
+        fa0, fa1 = prec.factors(k)
+        Sa = B.scale_sites(a, fa0, fa1)
+        for kp in range(prec.n_terms):
+            fb0, fb1 = prec.factors(kp)
+            Sb = B.scale_sites(b, fb0, fb1)
+            tot += B.dot(Sa, Sb, mpo)
+    return tot
+
+
+def rayleigh(x, prec, mpo):
+    """lambda(x) and ||x||_A^2 (Eq. (exactrq), (rayleigh1))."""
+    num = pair_sums(x, x, prec, mpo)
+    den = pair_sums(x, x, prec, None)
+    return num / den, num, den
+
+
+def residual_terms(x, lam, prec, mpo):
+    """s_{k,k'} = S_k (H_gamma - lambda) S_k' x and their norms (Sec. 5.3.1)."""
+    terms = []
+    for kp in range(prec.n_terms):
+        f0, f1 = prec.factors(kp)
+        u = B.apply_exact(mpo, B.scale_sites(x, f0, f1), shift=-lam)
+        for k in range(prec.n_terms):
+            g0, g1 = prec.factors(k)
+            s = B.scale_sites(u, g0, g1)
+            terms.append(((k, kp), s, B.norm(s)))
+    return terms
+
+
+def assemble_residual(terms, eta):
+    """res_eta(x) (Sec. 5.3.1): sort by norm, drop the first J_0 terms whose norms
+    sum to <= eta/3, add the rest with y_j = trunc_{eps_j}(y_{j-1} + s_j),
+    eps_j = eta ||s_j|| / (3 sum_{i>J_0} ||s_i||), finish with trunc_{eta/3}."""
+    order = sorted(terms, key=lambda e: (e[2], e[0]))
+    acc = 0.0
+    j0 = 0
+    while j0 < len(order) and acc + order[j0][2] <= eta / 3.0:
+        acc += order[j0][2]
+        j0 += 1
+    rest = order[j0:]
+    tail = sum(e[2] for e in rest)
+    y = None
+    for (_, s, ns) in rest:
+        eps_j = eta * ns / (3.0 * tail) if tail > 0 else 0.0
+        z = s if y is None else B.add(y, s)
+        y, _, _ = B.truncate(z, eps_j)
+    if y is None:
+        return None
+    y, _, _ = B.truncate(y, eta / 3.0)
+    return y
+
+
+def bdelta(rho, delta):
+    """b_delta(rho) of Eq. (bbetarho); None when the square root is not real."""
+    disc = 1.0 - 4.0 * (delta - 1.0) * delta * rho * rho
+    if disc < 0.0:
+        return None
+    return 2.0 * delta / (1.0 + 2.0 * delta * rho * rho + math.sqrt(disc))
+
+
+def eigvec_bound(rho, delta):
+    """2 sin(1/2 arcsin(sqrt(delta b_delta(rho)) rho)) (Thm. aposterbound); inf if invalid."""
+    b = bdelta(rho, delta)
+    if b is None:
+        return math.inf
+    arg = math.sqrt(delta * b) * rho
+    if arg > 1.0:
+        return math.inf
+    return 2.0 * math.sin(0.5 * math.asin(arg))
+
+
+def releig_bound(rho, delta):
+    """Relative eigenvalue bound of Eq. (releigerr); inf if invalid."""
+    b = bdelta(rho, delta)
+    if b is None or b * rho * rho >= 1.0:
+        return math.inf
+    return b / (1.0 - b * rho * rho) * rho * rho
+
+
+def rr2(GH, GE):
+    """Lower eigenpair of the 2x2 pencil (GH, GE) (library generalized eigh)."""
+    import scipy.linalg
+    w, v = scipy.linalg.eigh(GH, GE)
+    vec = v[:, 0]
+    vec = vec / math.sqrt(vec @ GE @ vec)
+    if vec[0] < 0:
+        vec = -vec
+    return float(w[0]), vec
+
+
+def delta_A(rho, q):
+    disc = max(1.0 + rho * rho - q * q, 0.0)
+    return max((-q * rho + math.sqrt(disc)) / (1.0 + rho * rho), 0.0)
+
+
+def step(x, mpo, prec, params, state):
+    """One pass of the loop body of Alg. 2.  Returns (x_next, info).  When the
+    termination test holds, x_next is the normalised x^n and info['converged']."""
+    lam, num, den = rayleigh(x, prec, mpo)
+    x = B.scale(x, 1.0 / math.sqrt(num))                 # x / ||x||_A
+    zeta = params.zeta_res
+    terms = residual_terms(x, lam, prec, mpo)
+    sum_norms = sum(e[2] for e in terms)
+    eta = min(2.0 * state.eta_res, 0.8 * zeta * sum_norms)
+    tries = 0
+    while True:
+        r = assemble_residual(terms, eta)
+        rnorm = 0.0 if r is None else B.norm(r)
+        if rnorm >= (1.0 + 1.0 / zeta) * eta or tries >= MAX_ETA_RETRIES:
+            break
+        eta *= 0.8
+        tries += 1
+    state.eta_res = eta
+    rho = (rnorm + eta) / math.sqrt(1.0 - params.c)     # ||x||_A = 1
+    bound = eigvec_bound(rho, params.delta)
+    info = {"n": state.n, "lambda": lam, "rho": rho, "eta_res": eta,
+            "res_norm": rnorm, "eta_tries": tries, "bound": bound,
+            "releig_bound": releig_bound(rho, params.delta), "converged": False}
+    if bound <= params.tau or r is None:
+        info["converged"] = True
+        state.history.append(info)
+        return x, info
+    # 2x2 Rayleigh-Ritz on span{x, r} in the normalised basis (Remark omegamin)
+    vecs = [x, r]
+    GH = np.zeros((2, 2))
+    GE = np.zeros((2, 2))
+    for i in range(2):
+        for j in range(2):
+            GH[i, j] = pair_sums(vecs[i], vecs[j], prec, mpo)
+            GE[i, j] = pair_sums(vecs[i], vecs[j], prec, None)
+    nrm = np.sqrt(np.diag(GE))
+    GHn = GH / np.outer(nrm, nrm)
+    GEn = GE / np.outer(nrm, nrm)
+    lam_star, v = rr2(GHn, GEn)
+    c1, c2 = v[0] / nrm[0], v[1] / nrm[1]
+    xstar = B.add(x, r, c1, c2)
+    xstar_A = math.sqrt(max(lam_star, 0.0))
+    q = math.sqrt(lam_star / (lam_star + params.t_eig * (lam - lam_star)))
+    dA = delta_A(rho, q)
+    eta_in = dA * xstar_A / math.sqrt(1.0 + params.c)
+    xnext, _, _ = B.truncate(xstar, eta_in)
+    info.update({"lambda_star": lam_star, "omega": -c2 / c1, "eta_in": eta_in,
+                 "delta_A": dA, "ranks": xnext.ranks()})
+    state.history.append(info)
+    state.n += 1
+    return xnext, info

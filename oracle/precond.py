@@ -1,0 +1,128 @@
+"""Exponential-sum preconditioner (Sec. 4.2-4.3, Thm. expsum, Cor. lrprecond).
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Readings of the paper used here:
+* beta_m = e^{mh} / t_min.  Substituting Eq. (expsum) into Eq. (Sdef) gives
+  S = alpha_0 h/sqrt(pi) sum_m e^{mh/2} exp(-e^{mh} D / t_min); the printed
+  e^{mh}/sqrt(t_min) (Sec. 4.3) does not follow from that substitution.
+* The per-site factor is alpha_m^{1/K} (the printed alpha_k^{1/K} is read as a typo).
+* t_min / t_max: the spectrum of D = sum theta_i a_i^* a_i on the N-particle space
+  consists of sums of N distinct theta_i, so t_min (t_max) is the sum of the N
+  smallest (largest) theta_i, taken per species when there are two.
+"""
+
+import math
+
+import numpy as np
+
+
+def expsum_params(c0, T):
+    """h, M^-, M^+ of Eq. (expsumparams)."""
+    h = math.pi ** 2 / math.log(8.0 * math.sqrt(2.0) / c0 + 1.0)
+    lg = abs(math.log(math.sqrt(math.pi) * c0 / 4.0))
+    m_plus = math.ceil(math.log(lg) / h)
+    m_minus = -math.ceil((2.0 * lg + math.log(T)) / h)
+    return h, m_minus, m_plus
+
+
+def expsum(t, h, m_minus, m_plus):
+    """S(t) of Eq. (expsum), an approximation of t^{-1/2} on [1, T]."""
+    t = np.asarray(t, dtype=np.float64)
+    acc = np.zeros_like(t)
+    for m in range(m_minus, m_plus + 1):
+        acc = acc + math.exp(m * h / 2.0) * np.exp(-math.exp(m * h) * t)
+    return h / math.sqrt(math.pi) * acc
+
+
+def theta_diag(t_so, v_so_fn, n_particles, gamma, K):
+    """theta_i = gamma/N + t_ii + sum_{j=k_i+1}^{k_i+N} (v_ijji - v_ijij),
+    k_i = max(0, i-N), 1-based (Sec. 7.1.1); returned 0-based."""
+    th = np.zeros(K)
+    N = n_particles
+    for i1 in range(1, K + 1):
+        ki = max(0, i1 - N)
+        acc = gamma / N + t_so(i1 - 1, i1 - 1)
+        for j1 in range(ki + 1, ki + N + 1):
+            i0, j0 = i1 - 1, j1 - 1
+            acc += v_so_fn(i0, j0, j0, i0) - v_so_fn(i0, j0, i0, j0)
+        th[i1 - 1] = acc
+    return th
+
+
+def spin_orbital_accessors(h, eri, spin):
+    """t_ij and v_ijkl = 1/2 (il|jk) of the spin-orbital Hamiltonian (Eq. (tvdef))."""
+    def sp(i):
+        return (i // 2, i % 2) if spin else (i, 0)
+
+    def t_so(i, j):
+        (p, a), (q, b) = sp(i), sp(j)
+        return h[p, q] if a == b else 0.0
+
+    def v_so(i, j, k, l):
+        (pi, si), (pj, sj), (pk, sk), (pl, sl) = sp(i), sp(j), sp(k), sp(l)
+        if si != sl or sj != sk:
+            return 0.0
+        return 0.5 * eri[pi, pl, pj, pk]
+
+    return t_so, v_so
+
+
+def spectrum_bounds(theta, species, target):
+    """[t_min, t_max] of D on the sector: sums of the smallest/largest N_s theta per species."""
+    lo = 0.0
+    hi = 0.0
+    for s in (0, 1):
+        vals = sorted(theta[t] for t in range(len(theta)) if species[t] == s)
+        n = target[s]
+        if n:
+            lo += sum(vals[:n])
+            hi += sum(vals[-n:])
+    return lo, hi
+
+
+def alpha0_and_c(c0, t_min, c_lower, c_upper):
+    """alpha_0 of Eq. (Sdef) and c of Eq. (precondcdef)."""
+    lo = c_lower * (1.0 - c0) ** 2
+    hi = c_upper * (1.0 + c0) ** 2
+    alpha0 = math.sqrt(2.0 / (t_min * (lo + hi)))
+    c = (hi - lo) / (hi + lo)
+    return alpha0, c
+
+
+class Preconditioner:
+    """S = sum_m S_m with S_m = (x)_i diag(alpha_m^{1/K}, alpha_m^{1/K} e^{-beta_m d_i}) (Sec. 4.3)."""
+
+    def __init__(self, d, t_min, t_max, c0, alpha0):
+        self.d = np.asarray(d, dtype=np.float64)
+        self.K = len(self.d)
+        self.t_min = t_min
+        self.t_max = t_max
+        self.c0 = c0
+        self.alpha0 = alpha0
+        self.h, self.m_minus, self.m_plus = expsum_params(c0, t_max / t_min)
+        self.ms = list(range(self.m_minus, self.m_plus + 1))
+
+    @property
+    def n_terms(self):
+        return len(self.ms)
+
+    def alpha(self, m):
+        return self.h * self.alpha0 / math.sqrt(math.pi) * math.exp(m * self.h / 2.0)
+
+    def beta(self, m):
+        return math.exp(m * self.h) / self.t_min
+
+    def factors(self, j):
+        """(f0, f1) per site for the j-th term (m = M^- + j)."""
+        m = self.ms[j]
+        a = self.alpha(m) ** (1.0 / self.K)
+        f0 = np.full(self.K, a)
+        f1 = a * np.exp(-self.beta(m) * self.d)
+        return f0, f1
+
+    def dense_diag(self, occupations):
+        """Diagonal of S on occupation vectors (rows of a 0/1 array): alpha_0 S(D/t_min)."""
+        occ = np.asarray(occupations, dtype=np.float64)
+        Dv = occ @ self.d
+        return self.alpha0 * expsum(Dv / self.t_min, self.h, self.m_minus, self.m_plus)
