@@ -1,0 +1,282 @@
+/*
+ * bsmps.h -- C ABI of the GB300 block-sparse MPS eigensolver.
+ *
+ * The library implements, on one CUDA device, the operations of the low-rank
+ * preconditioned inverse iteration for particle-number-conserving matrix
+ * product states ("Low-Rank Eigenvalue Solvers for Block-Sparse Matrix
+ * Product States"): Hamiltonian MPO construction, MPO x MPS application,
+ * block-sparse rank truncation, the exponential-sum preconditioner, inner
+ * products and the error-controlled PINVIT step (Alg. 2).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * Sites t = 0..K-1 (the paper numbers them 1..K); bonds b = 0..K, bond b
+ * separates sites < b from sites >= b.  With spin = 0 the K = n_orb sites
+ * are spinless orbitals (species 0).  With spin = 1 spatial orbital p owns the
+ * two sites 2p (species 0, "up") and 2p+1 (species 1, "down"), K = 2 n_orb.
+ * Occupying a site adds one particle of its species.  A sector at bond b is the
+ * pair (n0, n1) of particles on sites < b; valid sectors are those that can be
+ * completed to the target (n_up, n_dn) (Sec. 2.3, the sets K_k).  Sectors of a
+ * bond are sorted ascending by (n0, n1).
+ *
+ * Block layout ("flat layout") of an MPS: sites ascending; within a site the
+ * left sectors ascending, then sigma = 0 (unoccupied block, n -> n) and sigma = 1
+ * (occupied block, n -> n + e_species); each existing block is a dense
+ * rho_left x rho_right matrix stored row-major in float64 (Eq. (blockstructure)).
+ *
+ * Ownership: the library owns all device memory behind handles.  Host arrays
+ * passed in are read during the call only; host arrays passed out are written
+ * during the call and owned by the caller.  Every handle returned through an
+ * out-pointer is new and is released by the matching *_destroy call.
+ *
+ * Errors: every call returns a bsmps_status; no call aborts or throws across
+ * the ABI.  On failure the out-handles are left untouched and
+ * bsmps_last_error(ctx) describes the failure.  CUDA errors map to
+ * BSMPS_ERR_CUDA; a device that cannot satisfy an allocation gives
+ * BSMPS_ERR_OOM.
+ *
+ * Streams: all device work of a context is ordered on the stream given to
+ * bsmps_ctx_create (NULL: the legacy default stream).  Calls that return host
+ * scalars synchronise that stream before returning.
+ *
+ * Names: every symbol carries the bsmps_ prefix (a plain "truncate" would
+ * interpose the POSIX truncate(2) of the C library).
+ */
+#ifndef BSMPS_H
+#define BSMPS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BSMPS_API __attribute__((visibility("default")))
+#else
+#define BSMPS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsmps_ctx_s* bsmps_ctx;
+typedef struct bsmps_mps_s* bsmps_mps;
+typedef struct bsmps_mpo_s* bsmps_mpo;
+
+typedef enum {
+    BSMPS_OK = 0,
+    BSMPS_ERR_INVALID_ARG = 1, /* null handle, negative size, inconsistent arrays */
+    BSMPS_ERR_CHARGE = 2,      /* particle numbers / sectors not realisable */
+    BSMPS_ERR_OOM = 3,         /* device allocation failed */
+    BSMPS_ERR_RANK_CAP = 4,    /* result would exceed a hard capacity */
+    BSMPS_ERR_NOT_SPD = 5,     /* preconditioner data violates t_min > 0 */
+    BSMPS_ERR_NUMERIC = 6,     /* NaN / Inf detected in a scalar of the step */
+    BSMPS_ERR_TIMEOUT = 7,     /* a bounded device wait gave up */
+    BSMPS_ERR_CUDA = 8         /* any other CUDA runtime error */
+} bsmps_status;
+
+/* Exponential-sum preconditioner data (Sec. 4.2-4.3, Cor. lrprecond).
+ * d: the K diagonal coefficients d_i of D = sum_i d_i a_i^* a_i (theta_i of
+ * Sec. 7.1.1), host array of length K, read during the calls that take it.
+ * [t_min, t_max] must contain the spectrum of D on the sector (t_min > 0).
+ * c0 in (0,1) sets h, M^-, M^+ by Eq. (expsumparams); alpha0 is the scaling of
+ * Eq. (Sdef).  The library forms S = sum_m S_m with
+ * S_m = (x)_i diag(alpha_m^{1/K}, alpha_m^{1/K} exp(-beta_m d_i)),
+ * alpha_m = h alpha0 / sqrt(pi) e^{mh/2}, beta_m = e^{mh} / t_min. */
+typedef struct {
+    int K;
+    const double* d;
+    double t_min;
+    double t_max;
+    double c0;
+    double alpha0;
+} bsmps_precond;
+
+/* Constants of Alg. 2: c (Eq. (specequivA)), delta >= lambda_2/(lambda_2 -
+ * lambda_1) (Sec. 5.4), eps_num in (0, 1-c) (Lemma truncr; Sec. 7.1.3 uses
+ * (1-c)/2), t_eig in (0,1) (Thm. conv (ii)), tau the eigenvector tolerance of
+ * the termination test (Thm. aposterbound). */
+typedef struct {
+    double c;
+    double delta;
+    double eps_num;
+    double t_eig;
+    double tau;
+} bsmps_solver_params;
+
+/* State carried between steps: eta_res of the previous step (start with
+ * +INFINITY as in Alg. 2) and the step counter n. */
+typedef struct {
+    double eta_res;
+    int n;
+} bsmps_solver_state;
+
+/* Scalars reported by one step. */
+typedef struct {
+    double lambda;        /* lambda(x^n), Eq. (exactrq) */
+    double rho;           /* rho^n, Eq. (rhobound) */
+    double eta_res;       /* accepted residual tolerance */
+    double res_norm;      /* ||res_eta(x^n)|| */
+    int eta_tries;        /* passes of the eta_res loop beyond the first */
+    double bound;         /* eigenvector bound of Thm. aposterbound (+inf if invalid) */
+    double releig_bound;  /* relative eigenvalue bound, Eq. (releigerr) (+inf if invalid) */
+    double lambda_star;   /* lower Ritz value of the 2x2 problem (Remark omegamin) */
+    double omega;         /* step size: x* is proportional to x - omega r */
+    double eta_in;        /* truncation tolerance of the iterate (Sec. 5.3.2) */
+    double delta_A;
+    int converged;        /* 1 when the termination test of Alg. 2 held */
+    int max_rank;         /* largest bond dimension of the returned iterate */
+    double flops;         /* algorithmic FP64 flops issued by the step */
+} bsmps_step_info;
+
+BSMPS_API const char* bsmps_status_string(bsmps_status s);
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` ordering its work on `stream`
+ * (a cudaStream_t, or NULL).  Errors: INVALID_ARG (out NULL), CUDA. */
+BSMPS_API bsmps_status bsmps_ctx_create(int device, void* stream, bsmps_ctx* out);
+BSMPS_API bsmps_status bsmps_ctx_destroy(bsmps_ctx ctx);
+/* Wait for all work of the context. */
+BSMPS_API bsmps_status bsmps_ctx_sync(bsmps_ctx ctx);
+/* Message of the last failed call on this context ("" if none). */
+BSMPS_API const char* bsmps_last_error(bsmps_ctx ctx);
+/* Number of kernel launches issued by the context so far. */
+BSMPS_API int64_t bsmps_ctx_launch_count(bsmps_ctx ctx);
+
+/* Kernel profiler.  enable != 0 brackets every launch with CUDA events on the
+ * context stream and records its kind and algorithmic flops / bytes (this
+ * adds two event records per launch); enable = 0 stops recording.
+ * bsmps_ctx_kernel_stats synchronises the stream and returns, for kernel kind
+ * `kind` (0 copy, 1 grouped GEMM, 2 QR, 3 SVD, 4 sum of squares), the number
+ * of recorded launches, their summed device time in ms and summed
+ * algorithmic FP64 flops and bytes; `reset` != 0 clears the records after
+ * reading.  Errors: INVALID_ARG (kind out of range), CUDA. */
+BSMPS_API bsmps_status bsmps_ctx_profile(bsmps_ctx ctx, int enable);
+BSMPS_API bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset, int64_t* launches,
+                                              double* ms, double* flops, double* bytes);
+
+/* ---- MPS ----------------------------------------------------------------- */
+
+/* Number of float64 entries of a fresh random iterate of maximal rank r_max
+ * (block dims rho = min(left count, right count) if these fit r_max in total,
+ * else min(left, right, floor(r_max * left*right / sum left*right)); sectors
+ * of dim 0 dropped).  Errors: INVALID_ARG, CHARGE. */
+BSMPS_API bsmps_status bsmps_mps_random_size(int n_orb, int spin, int n_up, int n_dn, int r_max,
+                                   int64_t* n_values);
+
+/* New iterate.  init = 0: e_1, the rank-one lowest determinant with the first
+ * n_up species-0 and n_dn species-1 sites occupied (Sec. 7.1.4); values
+ * ignored.  init = 1: blocks of the rule above filled from `values` (host,
+ * n_values entries in flat layout, see bsmps_mps_random_size).
+ * Errors: INVALID_ARG, CHARGE, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_mps_create(bsmps_ctx ctx, int n_orb, int spin, int n_up, int n_dn,
+                              int r_max, int init, const double* values, int64_t n_values,
+                              bsmps_mps* out);
+
+/* New iterate with explicit sectors: n_sectors[b] (b = 0..K) sectors per
+ * bond, `sectors` the concatenated (n0, n1, dim) int triples per bond,
+ * ascending; values in flat layout.  Errors: INVALID_ARG, CHARGE, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_mps_import(bsmps_ctx ctx, int n_orb, int spin, int n_up, int n_dn,
+                              const int* n_sectors, const int* sectors,
+                              const double* values, int64_t n_values, bsmps_mps* out);
+
+/* Shape queries: K; per-bond sector counts (K+1 ints) and their total; the
+ * (n0, n1, dim) triples; the number of float64 entries in flat layout. */
+BSMPS_API bsmps_status bsmps_mps_num_sites(bsmps_mps x, int* K);
+BSMPS_API bsmps_status bsmps_mps_num_sectors(bsmps_mps x, int* per_bond, int* total);
+BSMPS_API bsmps_status bsmps_mps_sectors(bsmps_mps x, int* triples);
+BSMPS_API bsmps_status bsmps_mps_size(bsmps_mps x, int64_t* n_values);
+/* Copy the blocks to host memory in flat layout (synchronises). */
+BSMPS_API bsmps_status bsmps_mps_export(bsmps_mps x, double* values);
+BSMPS_API bsmps_status bsmps_mps_destroy(bsmps_mps x);
+
+/* ---- MPO ----------------------------------------------------------------- */
+
+/* MPO of H_gamma = H + gamma I for the second-quantized Hamiltonian
+ * H = sum t_ij a_i^* a_j + sum v_ijkl a_i^* a_j^* a_k a_l (Eq. (hamil)),
+ * v_ijkl = 1/2 (il|jk) (Eq. (tvdef), chemist notation), gamma folded into the
+ * diagonal as t_ii + gamma/N (Sec. 7.1.1).
+ * h: n_orb x n_orb row-major; eri: n_orb^4 row-major (pq|rs), both host.
+ * With spin = 1 the spatial integrals are expanded to the interleaved
+ * spin-orbitals.  Construction: Jordan--Wigner terms merged by canonical
+ * site-local factors and wired as a finite-state MPO (channels: identity,
+ * placed-prefix, remaining-suffix, finished; the prefix/suffix choice for
+ * half-placed terms switches at bond K/2), ranks within Thm. opranks.
+ * compress_tol: canonical terms with |coefficient| <= compress_tol are
+ * dropped (0: keep every nonzero term).  Errors: INVALID_ARG, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_mpo_from_integrals(bsmps_ctx ctx, int n_orb, const double* h,
+                                      const double* eri, int spin, int n_particles,
+                                      double gamma, double compress_tol, bsmps_mpo* out);
+/* Bond dims (K+1 ints), per-site entry count, entries (a, b, sigma_out,
+ * sigma_in) int quadruples with weights, and channel charges (pairs per
+ * channel) of a bond. */
+BSMPS_API bsmps_status bsmps_mpo_bond_dims(bsmps_mpo W, int* dims);
+BSMPS_API bsmps_status bsmps_mpo_num_entries(bsmps_mpo W, int site, int* n);
+BSMPS_API bsmps_status bsmps_mpo_entries(bsmps_mpo W, int site, int* quads, double* w);
+BSMPS_API bsmps_status bsmps_mpo_channel_charges(bsmps_mpo W, int bond, int* pairs);
+BSMPS_API bsmps_status bsmps_mpo_destroy(bsmps_mpo W);
+
+/* ---- operations (all results are new handles) -------------------------- */
+
+/* y = (H_gamma + shift I) x (Sec. 2.4).  tol = 0 and r_max = 0: exact
+ * application, bond basis = MPO channel x x's basis, grouped by sector
+ * (channel-major), sectors that no complete path reaches dropped.  Otherwise
+ * y = trunc_tol of that result capped at r_max (see bsmps_truncate).
+ * flops (may be NULL): algorithmic FP64 flops issued.
+ * Errors: INVALID_ARG (mismatched sites/species), OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_apply_H(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift,
+                           double tol, int r_max, bsmps_mps* y, double* flops);
+
+/* trunc_eps (Sec. 2.2, Eq. (ttsvdquasiopt)): QR sweep left to right (diag R
+ * >= 0), then right to left SVD of [X_b(n,0) | X_b(n,1)] per left sector;
+ * at every bond the pooled singular values are discarded from the smallest
+ * while their squared sum stays <= eps^2/(K-1) (so ||x - y|| <= eps), a cut
+ * inside a cluster of relative gap < 1e-10 moves to keep the cluster; then at
+ * most r_max (> 0) are kept.  disc_tol / disc_cap (may be NULL): Frobenius
+ * norms discarded by the tolerance / by the cap.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_truncate(bsmps_ctx ctx, bsmps_mps x, double eps, int r_max,
+                            bsmps_mps* y, double* disc_tol, double* disc_cap);
+
+/* out = alpha x + beta y by block concatenation (Sec. 2.3).  Errors:
+ * INVALID_ARG (different sites / targets), OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_add(bsmps_ctx ctx, bsmps_mps x, bsmps_mps y, double alpha, double beta,
+                       bsmps_mps* out);
+
+/* out = x with every sigma=0 block of site t scaled by f0[t] and every sigma=1
+ * block by f1[t] (f0, f1 host arrays of length K): the action of one
+ * rank-one diagonal Kronecker operator (Sec. 4.3). */
+BSMPS_API bsmps_status bsmps_scale_sites(bsmps_ctx ctx, bsmps_mps x, const double* f0, const double* f1,
+                               bsmps_mps* out);
+
+/* y = S_m x for term = m - M^- in [0, #S), or y = S x = sum_m S_m x
+ * (block concatenation of the scaled copies, rank #S times) for term = -1
+ * (Sec. 4.3).  n_terms (may be NULL) receives #S = M^+ - M^- + 1.
+ * Errors: INVALID_ARG, NOT_SPD (t_min <= 0 or t_max < t_min), OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_precondition(bsmps_ctx ctx, const bsmps_precond* p, int term, bsmps_mps x,
+                                bsmps_mps* y, int* n_terms);
+
+/* out = <a, O b> in float64 with O = (H_gamma + shift I) given by W, or the
+ * identity when W is NULL (left-to-right environment recursion). */
+BSMPS_API bsmps_status bsmps_dot(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, double shift,
+                       double* out);
+
+/* One pass of the loop body of Alg. 2 on x^n = *x:
+ * lambda^n (Eq. (exactrq)), normalisation in the A-norm, the residual
+ * res_eta from the terms S_k (H_gamma - lambda) S_k' x (Sec. 5.3.1, eta_res
+ * started at min(2 eta_res, 4/5 zeta sum ||s_j||) and multiplied by 4/5 until
+ * accepted), rho^n (Eq. (rhobound)), the termination test (Thm.
+ * aposterbound), the 2x2 Rayleigh-Ritz step (Remark omegamin) and
+ * x^{n+1} = trunc_{eta_in}(x*) (Sec. 5.3.2).
+ * *x is replaced by x^{n+1} (or by the normalised x^n when the test holds);
+ * the old handle is destroyed by the call.  state is updated in place.
+ * Errors: INVALID_ARG, NOT_SPD, NUMERIC, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
+                                   const bsmps_solver_params* params,
+                                   bsmps_solver_state* state, bsmps_mps* x,
+                                   bsmps_step_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSMPS_H */

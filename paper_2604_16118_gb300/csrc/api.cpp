@@ -1,0 +1,462 @@
+// extern "C" entry points of the block-sparse MPS library (see include/bsmps.h).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "solver.h"
+
+struct bsmps_ctx_s {
+    bsm::Context c;
+};
+struct bsmps_mps_s {
+    std::unique_ptr<bsm::Mps> m;
+};
+struct bsmps_mpo_s {
+    bsm::Context* ctx;
+    bsm::Mpo W;
+};
+
+namespace bsm {
+
+void* Context::alloc(size_t bytes) {
+    if (bytes == 0) return nullptr;
+    void* p = nullptr;
+    BSM_CUDA(cudaMallocAsync(&p, bytes, stream));
+    return p;
+}
+
+void Context::free(void* p) {
+    if (p) cudaFreeAsync(p, stream);
+}
+
+}  // namespace bsm
+
+namespace {
+
+thread_local std::string g_err;
+
+template <class F>
+bsmps_status guarded(bsmps_ctx ctx, F&& f) {
+    try {
+        f();
+        return BSMPS_OK;
+    } catch (const bsm::Error& e) {
+        if (ctx) ctx->c.last_error = e.what();
+        g_err = e.what();
+        return e.code;
+    } catch (const std::bad_alloc& e) {
+        if (ctx) ctx->c.last_error = "host allocation failed";
+        g_err = "host allocation failed";
+        return BSMPS_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (ctx) ctx->c.last_error = e.what();
+        g_err = e.what();
+        return BSMPS_ERR_INVALID_ARG;
+    }
+}
+
+bsm::Context* C(bsmps_ctx ctx) {
+    BSM_REQUIRE(ctx != nullptr, BSMPS_ERR_INVALID_ARG, "null context");
+    BSM_CUDA(cudaSetDevice(ctx->c.device));
+    return &ctx->c;
+}
+
+const bsm::Mps* M(bsmps_mps x) {
+    BSM_REQUIRE(x != nullptr && x->m, BSMPS_ERR_INVALID_ARG, "null MPS handle");
+    return x->m.get();
+}
+
+bsmps_mps wrap(bsm::MpsPtr p) {
+    bsmps_mps h = new bsmps_mps_s;
+    h->m = std::move(p);
+    return h;
+}
+
+bsm::Charge target_of(int n_up, int n_dn, int spin) {
+    BSM_REQUIRE(n_up >= 0 && (spin ? n_dn >= 0 : true), BSMPS_ERR_CHARGE, "negative particle number");
+    return spin ? bsm::Charge{n_up, n_dn} : bsm::Charge{n_up, 0};
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bsmps_status_string(bsmps_status s) {
+    switch (s) {
+        case BSMPS_OK: return "ok";
+        case BSMPS_ERR_INVALID_ARG: return "invalid argument";
+        case BSMPS_ERR_CHARGE: return "particle numbers or sectors not realisable";
+        case BSMPS_ERR_OOM: return "device out of memory";
+        case BSMPS_ERR_RANK_CAP: return "rank capacity exceeded";
+        case BSMPS_ERR_NOT_SPD: return "preconditioner data not positive";
+        case BSMPS_ERR_NUMERIC: return "non-finite scalar";
+        case BSMPS_ERR_TIMEOUT: return "bounded device wait gave up";
+        case BSMPS_ERR_CUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+bsmps_status bsmps_ctx_create(int device, void* stream, bsmps_ctx* out) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(out != nullptr, BSMPS_ERR_INVALID_ARG, "null out pointer");
+        BSM_CUDA(cudaSetDevice(device));
+        cudaMemPool_t pool;
+        BSM_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = UINT64_MAX;
+        BSM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        bsmps_ctx c = new bsmps_ctx_s;
+        c->c.device = device;
+        c->c.stream = (cudaStream_t)stream;
+        *out = c;
+    });
+}
+
+bsmps_status bsmps_ctx_destroy(bsmps_ctx ctx) {
+    if (!ctx) return BSMPS_ERR_INVALID_ARG;
+    bsmps_status s = guarded(nullptr, [&] {
+        ctx->c.sync();
+        for (auto& r : ctx->c.prof) {
+            cudaEventDestroy(r.e0);
+            cudaEventDestroy(r.e1);
+        }
+        for (auto e : ctx->c.event_pool) cudaEventDestroy(e);
+    });
+    delete ctx;
+    return s;
+}
+
+bsmps_status bsmps_ctx_sync(bsmps_ctx ctx) {
+    return guarded(ctx, [&] { C(ctx)->sync(); });
+}
+
+const char* bsmps_last_error(bsmps_ctx ctx) { return ctx ? ctx->c.last_error.c_str() : g_err.c_str(); }
+
+int64_t bsmps_ctx_launch_count(bsmps_ctx ctx) { return ctx ? ctx->c.launches : 0; }
+
+bsmps_status bsmps_ctx_profile(bsmps_ctx ctx, int enable) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        c->profiling = enable != 0;
+    });
+}
+
+bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset, int64_t* launches, double* ms,
+                                    double* flops, double* bytes) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(kind >= 0 && kind < bsm::KK_COUNT, BSMPS_ERR_INVALID_ARG, "kernel kind out of range");
+        c->sync();
+        int64_t n = 0;
+        double t = 0.0, f = 0.0, b = 0.0;
+        for (auto& r : c->prof) {
+            if (r.kind != kind) continue;
+            float e = 0.0f;
+            BSM_CUDA(cudaEventElapsedTime(&e, r.e0, r.e1));
+            n++;
+            t += e;
+            f += r.flops;
+            b += r.bytes;
+        }
+        if (launches) *launches = n;
+        if (ms) *ms = t;
+        if (flops) *flops = f;
+        if (bytes) *bytes = b;
+        if (reset) {
+            for (auto& r : c->prof) {
+                c->event_pool.push_back(r.e0);
+                c->event_pool.push_back(r.e1);
+            }
+            c->prof.clear();
+        }
+    });
+}
+
+bsmps_status bsmps_mps_random_size(int n_orb, int spin, int n_up, int n_dn, int r_max, int64_t* n_values) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(n_orb > 0 && r_max > 0 && n_values, BSMPS_ERR_INVALID_ARG, "n_orb, r_max > 0 required");
+        bsm::Layout L = bsm::default_layout(bsm::species_of(n_orb, spin), target_of(n_up, n_dn, spin), r_max);
+        *n_values = L.total();
+    });
+}
+
+bsmps_status bsmps_mps_create(bsmps_ctx ctx, int n_orb, int spin, int n_up, int n_dn, int r_max, int init,
+                              const double* values, int64_t n_values, bsmps_mps* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(n_orb > 0 && out, BSMPS_ERR_INVALID_ARG, "n_orb > 0 and out required");
+        const auto species = bsm::species_of(n_orb, spin);
+        const bsm::Charge tgt = target_of(n_up, n_dn, spin);
+        bsm::Layout L;
+        std::vector<double> ones;
+        const double* src = values;
+        if (init == 0) {
+            L = bsm::e1_layout(species, tgt);
+            ones.assign((size_t)L.total(), 1.0);
+            src = ones.data();
+        } else {
+            BSM_REQUIRE(r_max > 0, BSMPS_ERR_INVALID_ARG, "r_max > 0 required");
+            L = bsm::default_layout(species, tgt, r_max);
+            BSM_REQUIRE(values && n_values == L.total(), BSMPS_ERR_INVALID_ARG,
+                        "values must hold exactly bsmps_mps_random_size entries");
+        }
+        bsm::MpsPtr x(bsm::new_mps(c, L, false));
+        bsm::mps_upload(x.get(), src);
+        *out = wrap(std::move(x));
+    });
+}
+
+bsmps_status bsmps_mps_import(bsmps_ctx ctx, int n_orb, int spin, int n_up, int n_dn, const int* n_sectors,
+                              const int* sectors, const double* values, int64_t n_values, bsmps_mps* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(n_orb > 0 && n_sectors && sectors && out, BSMPS_ERR_INVALID_ARG, "null argument");
+        bsm::Layout L;
+        L.species = bsm::species_of(n_orb, spin);
+        L.K = (int)L.species.size();
+        L.target = target_of(n_up, n_dn, spin);
+        L.bonds.resize(L.K + 1);
+        int64_t pos = 0;
+        for (int b = 0; b <= L.K; ++b) {
+            BSM_REQUIRE(n_sectors[b] >= 0, BSMPS_ERR_INVALID_ARG, "negative sector count");
+            for (int i = 0; i < n_sectors[b]; ++i, ++pos) {
+                L.bonds[b].q.push_back({sectors[3 * pos], sectors[3 * pos + 1]});
+                L.bonds[b].dim.push_back(sectors[3 * pos + 2]);
+            }
+        }
+        bsm::check_layout(L);
+        L.rebuild_blocks();
+        BSM_REQUIRE(n_values == L.total() && (values || n_values == 0), BSMPS_ERR_INVALID_ARG,
+                    "values must match the sector dims");
+        bsm::MpsPtr x(bsm::new_mps(c, L, false));
+        if (n_values > 0) bsm::mps_upload(x.get(), values);
+        *out = wrap(std::move(x));
+    });
+}
+
+bsmps_status bsmps_mps_num_sites(bsmps_mps x, int* K) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(K, BSMPS_ERR_INVALID_ARG, "null out");
+        *K = M(x)->lay.K;
+    });
+}
+
+bsmps_status bsmps_mps_num_sectors(bsmps_mps x, int* per_bond, int* total) {
+    return guarded(nullptr, [&] {
+        const bsm::Layout& L = M(x)->lay;
+        int tot = 0;
+        for (int b = 0; b <= L.K; ++b) {
+            if (per_bond) per_bond[b] = (int)L.bonds[b].q.size();
+            tot += (int)L.bonds[b].q.size();
+        }
+        if (total) *total = tot;
+    });
+}
+
+bsmps_status bsmps_mps_sectors(bsmps_mps x, int* triples) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(triples, BSMPS_ERR_INVALID_ARG, "null out");
+        const bsm::Layout& L = M(x)->lay;
+        int64_t pos = 0;
+        for (int b = 0; b <= L.K; ++b)
+            for (size_t i = 0; i < L.bonds[b].q.size(); ++i, ++pos) {
+                triples[3 * pos] = L.bonds[b].q[i].q0;
+                triples[3 * pos + 1] = L.bonds[b].q[i].q1;
+                triples[3 * pos + 2] = L.bonds[b].dim[i];
+            }
+    });
+}
+
+bsmps_status bsmps_mps_size(bsmps_mps x, int64_t* n) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(n, BSMPS_ERR_INVALID_ARG, "null out");
+        *n = M(x)->lay.total();
+    });
+}
+
+bsmps_status bsmps_mps_export(bsmps_mps x, double* values) {
+    return guarded(nullptr, [&] {
+        const bsm::Mps* m = M(x);
+        BSM_REQUIRE(values || m->lay.total() == 0, BSMPS_ERR_INVALID_ARG, "null out");
+        BSM_CUDA(cudaSetDevice(m->ctx->device));
+        bsm::mps_download(m, values);
+    });
+}
+
+bsmps_status bsmps_mps_destroy(bsmps_mps x) {
+    if (!x) return BSMPS_ERR_INVALID_ARG;
+    return guarded(nullptr, [&] {
+        if (x->m) BSM_CUDA(cudaSetDevice(x->m->ctx->device));
+        delete x;
+    });
+}
+
+bsmps_status bsmps_mpo_from_integrals(bsmps_ctx ctx, int n_orb, const double* h, const double* eri, int spin,
+                                      int n_particles, double gamma, double compress_tol, bsmps_mpo* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(out, BSMPS_ERR_INVALID_ARG, "null out");
+        BSM_REQUIRE(n_particles > 0, BSMPS_ERR_CHARGE, "n_particles must be positive");
+        bsmps_mpo W = new bsmps_mpo_s;
+        W->ctx = c;
+        try {
+            W->W = bsm::build_mpo(n_orb, h, eri, spin, n_particles, gamma, compress_tol);
+        } catch (...) {
+            delete W;
+            throw;
+        }
+        *out = W;
+    });
+}
+
+bsmps_status bsmps_mpo_bond_dims(bsmps_mpo W, int* dims) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(W && dims, BSMPS_ERR_INVALID_ARG, "null argument");
+        for (int b = 0; b <= W->W.K; ++b) dims[b] = W->W.bond_dim(b);
+    });
+}
+
+bsmps_status bsmps_mpo_num_entries(bsmps_mpo W, int site, int* n) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(W && n && site >= 0 && site < W->W.K, BSMPS_ERR_INVALID_ARG, "bad argument");
+        *n = (int)W->W.entries[site].size();
+    });
+}
+
+bsmps_status bsmps_mpo_entries(bsmps_mpo W, int site, int* quads, double* w) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(W && quads && w && site >= 0 && site < W->W.K, BSMPS_ERR_INVALID_ARG, "bad argument");
+        const auto& E = W->W.entries[site];
+        for (size_t i = 0; i < E.size(); ++i) {
+            quads[4 * i] = E[i].a;
+            quads[4 * i + 1] = E[i].b;
+            quads[4 * i + 2] = E[i].so;
+            quads[4 * i + 3] = E[i].si;
+            w[i] = E[i].w;
+        }
+    });
+}
+
+bsmps_status bsmps_mpo_channel_charges(bsmps_mpo W, int bond, int* pairs) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(W && pairs && bond >= 0 && bond <= W->W.K, BSMPS_ERR_INVALID_ARG, "bad argument");
+        const auto& ch = W->W.charges[bond];
+        for (size_t i = 0; i < ch.size(); ++i) {
+            pairs[2 * i] = ch[i].q0;
+            pairs[2 * i + 1] = ch[i].q1;
+        }
+    });
+}
+
+bsmps_status bsmps_mpo_destroy(bsmps_mpo W) {
+    if (!W) return BSMPS_ERR_INVALID_ARG;
+    delete W;
+    return BSMPS_OK;
+}
+
+bsmps_status bsmps_apply_H(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift, double tol, int r_max,
+                           bsmps_mps* y, double* flops) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(W && y, BSMPS_ERR_INVALID_ARG, "null argument");
+        BSM_REQUIRE(tol >= 0.0 && r_max >= 0, BSMPS_ERR_INVALID_ARG, "tol >= 0 and r_max >= 0 required");
+        const double f0 = c->flops;
+        bsm::MpsPtr r = bsm::op_apply_exact(c, W->W, M(x), shift);
+        if (tol > 0.0 || r_max > 0) r = bsm::op_truncate(c, r.get(), tol, r_max, nullptr, nullptr);
+        c->sync();
+        if (flops) *flops = c->flops - f0;
+        *y = wrap(std::move(r));
+    });
+}
+
+bsmps_status bsmps_truncate(bsmps_ctx ctx, bsmps_mps x, double eps, int r_max, bsmps_mps* y, double* disc_tol,
+                            double* disc_cap) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(y && eps >= 0.0 && r_max >= 0, BSMPS_ERR_INVALID_ARG, "bad argument");
+        bsm::MpsPtr r = bsm::op_truncate(c, M(x), eps, r_max, disc_tol, disc_cap);
+        c->sync();
+        *y = wrap(std::move(r));
+    });
+}
+
+bsmps_status bsmps_add(bsmps_ctx ctx, bsmps_mps x, bsmps_mps y, double alpha, double beta, bsmps_mps* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(out, BSMPS_ERR_INVALID_ARG, "null out");
+        const int K = M(x)->lay.K;
+        std::vector<double> a(K, 1.0), b(K, 1.0);
+        a[0] = alpha;
+        b[0] = beta;
+        bsm::MpsPtr r = bsm::op_concat(c, {{M(x), a, a}, {M(y), b, b}});
+        c->sync();
+        *out = wrap(std::move(r));
+    });
+}
+
+bsmps_status bsmps_scale_sites(bsmps_ctx ctx, bsmps_mps x, const double* f0, const double* f1, bsmps_mps* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(out && f0 && f1, BSMPS_ERR_INVALID_ARG, "null argument");
+        const int K = M(x)->lay.K;
+        bsm::MpsPtr r = bsm::op_scale_sites(c, M(x), std::vector<double>(f0, f0 + K),
+                                            std::vector<double>(f1, f1 + K));
+        c->sync();
+        *out = wrap(std::move(r));
+    });
+}
+
+bsmps_status bsmps_precondition(bsmps_ctx ctx, const bsmps_precond* p, int term, bsmps_mps x, bsmps_mps* y,
+                                int* n_terms) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(y, BSMPS_ERR_INVALID_ARG, "null out");
+        const bsm::PrecondTerms P = bsm::make_precond(p);
+        BSM_REQUIRE(p->K == M(x)->lay.K, BSMPS_ERR_INVALID_ARG, "precond K differs from the MPS");
+        if (n_terms) *n_terms = P.n_terms();
+        BSM_REQUIRE(term >= -1 && term < P.n_terms(), BSMPS_ERR_INVALID_ARG, "term out of range");
+        bsm::MpsPtr r;
+        if (term >= 0) {
+            r = bsm::op_scale_sites(c, M(x), P.f0[term], P.f1[term]);
+        } else {
+            std::vector<bsm::ConcatTerm> terms;
+            for (int k = 0; k < P.n_terms(); ++k) terms.push_back({M(x), P.f0[k], P.f1[k]});
+            r = bsm::op_concat(c, terms);
+        }
+        c->sync();
+        *y = wrap(std::move(r));
+    });
+}
+
+bsmps_status bsmps_dot(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, double shift, double* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(out, BSMPS_ERR_INVALID_ARG, "null out");
+        bsm::EnvProblem pr{M(a), M(b), W ? &W->W : nullptr, shift};
+        *out = bsm::op_dot_batch(c, {pr})[0];
+    });
+}
+
+bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
+                                   const bsmps_solver_params* params, bsmps_solver_state* state, bsmps_mps* x,
+                                   bsmps_step_info* info) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(W && params && state && x && *x && info, BSMPS_ERR_INVALID_ARG, "null argument");
+        BSM_REQUIRE(params->c > 0.0 && params->c < 1.0 && params->delta > 1.0 && params->eps_num > 0.0 &&
+                        params->eps_num < 1.0 - params->c && params->t_eig > 0.0 && params->t_eig < 1.0,
+                    BSMPS_ERR_INVALID_ARG, "solver parameters out of range");
+        const bsm::PrecondTerms P = bsm::make_precond(p);
+        BSM_REQUIRE(p->K == M(*x)->lay.K, BSMPS_ERR_INVALID_ARG, "precond K differs from the MPS");
+        bsmps_step_info inf;
+        bsmps_solver_state st = *state;
+        bsm::MpsPtr r = bsm::eigensolve_step(c, W->W, P, *params, st, M(*x), inf);
+        c->sync();
+        *state = st;
+        *info = inf;
+        bsmps_mps old = *x;
+        *x = wrap(std::move(r));
+        delete old;
+    });
+}
+
+}  // extern "C"

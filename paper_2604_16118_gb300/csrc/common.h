@@ -1,0 +1,169 @@
+// Internal structures of the block-sparse MPS library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/bsmps.h"
+
+namespace bsm {
+
+struct Error : public std::runtime_error {
+    bsmps_status code;
+    Error(bsmps_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define BSM_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            throw ::bsm::Error(e_ == cudaErrorMemoryAllocation ? BSMPS_ERR_OOM            \
+                                                               : BSMPS_ERR_CUDA,          \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));       \
+        }                                                                                 \
+    } while (0)
+
+#define BSM_REQUIRE(cond, code, msg)                              \
+    do {                                                          \
+        if (!(cond)) throw ::bsm::Error((code), (msg));           \
+    } while (0)
+
+struct Charge {
+    int q0 = 0, q1 = 0;
+    bool operator<(const Charge& o) const { return q0 != o.q0 ? q0 < o.q0 : q1 < o.q1; }
+    bool operator==(const Charge& o) const { return q0 == o.q0 && q1 == o.q1; }
+    bool operator!=(const Charge& o) const { return !(*this == o); }
+    Charge operator+(const Charge& o) const { return {q0 + o.q0, q1 + o.q1}; }
+    Charge operator-(const Charge& o) const { return {q0 - o.q0, q1 - o.q1}; }
+};
+
+inline Charge site_delta(int species, int sigma) {
+    return species == 0 ? Charge{sigma, 0} : Charge{0, sigma};
+}
+
+// Sectors of one bond, ascending by charge.
+struct Bond {
+    std::vector<Charge> q;
+    std::vector<int> dim;
+    int find(const Charge& c) const;   // index or -1
+    int total() const;
+};
+
+// One dense block of a core: left sector index li (bond t), right sector ri
+// (bond t+1), occupation sigma; row-major rows x cols at offset off in the core.
+struct Block {
+    int li, ri, sigma, rows, cols;
+    int64_t off;
+};
+
+struct Layout {
+    int K = 0;
+    std::vector<int> species;          // per site
+    Charge target;
+    std::vector<Bond> bonds;           // K+1
+    std::vector<std::vector<Block>> blocks;   // per site, layout order
+    std::vector<int64_t> core_size;    // per site (entries)
+    void rebuild_blocks();             // from bonds
+    int64_t total() const;
+    int block_index(int t, int li, int sigma) const;  // -1 if absent
+};
+
+std::vector<int> species_of(int n_orb, int spin);
+std::vector<std::vector<Charge>> valid_sectors(const std::vector<int>& species, Charge target);
+Layout default_layout(const std::vector<int>& species, Charge target, int r_max);
+Layout e1_layout(const std::vector<int>& species, Charge target);
+void check_layout(const Layout& L);
+
+// MPO: per site a sorted list of entries; per bond channel charges.
+struct MpoEntry {
+    int a, b, so, si;
+    double w;
+};
+
+struct Mpo {
+    int K = 0;
+    std::vector<int> species;
+    std::vector<std::vector<Charge>> charges;     // per bond, per channel
+    std::vector<std::vector<MpoEntry>> entries;   // per site, sorted (a, b, so, si)
+    int shift_entry[2] = {-1, -1};                // site-0 entries (I->F, s, s)
+    int bond_dim(int b) const { return (int)charges[b].size(); }
+};
+
+Mpo build_mpo(int n_orb, const double* h, const double* eri, int spin, int n_particles,
+              double gamma, double compress_tol);
+
+struct Context;
+
+// Device MPS: one device buffer per core (row-major blocks in layout order).
+struct Mps {
+    Context* ctx = nullptr;
+    Layout lay;
+    std::vector<double*> core;   // device pointers (nullptr when the core is empty)
+    ~Mps();
+};
+
+// Per-launch record of the optional profiler (events resolved on query).
+struct ProfRec {
+    int kind;
+    double flops, bytes;
+    cudaEvent_t e0, e1;
+};
+
+enum KernelKind { KK_COPY = 0, KK_GEMM = 1, KK_QR = 2, KK_SVD = 3, KK_SUMSQ = 4, KK_COUNT = 5 };
+
+struct Context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    int64_t launches = 0;
+    double flops = 0.0;              // algorithmic FP64 flops issued (running total)
+    bool profiling = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event();
+    void prof_begin(cudaEvent_t* e0);
+    void prof_end(int kind, double flops, double bytes, cudaEvent_t e0);
+    // scratch for task uploads and temporaries
+    void* alloc(size_t bytes);
+    void free(void* p);
+    template <class T>
+    T* upload(const std::vector<T>& v) {
+        if (v.empty()) return nullptr;
+        T* d = (T*)alloc(v.size() * sizeof(T));
+        BSM_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                 stream));
+        return d;
+    }
+    void sync() { BSM_CUDA(cudaStreamSynchronize(stream)); }
+};
+
+// RAII holder for temporary device allocations of one operation.
+struct Scratch {
+    Context* ctx;
+    std::vector<void*> ptrs;
+    explicit Scratch(Context* c) : ctx(c) {}
+    ~Scratch() {
+        for (void* p : ptrs) ctx->free(p);
+    }
+    template <class T>
+    T* up(const std::vector<T>& v) {
+        T* p = ctx->upload(v);
+        if (p) ptrs.push_back(p);
+        return p;
+    }
+    double* dbl(size_t n) {
+        if (n == 0) return nullptr;
+        double* p = (double*)ctx->alloc(n * sizeof(double));
+        ptrs.push_back(p);
+        return p;
+    }
+};
+
+Mps* new_mps(Context* ctx, const Layout& L, bool zero);   // allocates cores
+
+}  // namespace bsm

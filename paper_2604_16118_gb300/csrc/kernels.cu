@@ -1,0 +1,503 @@
+// Device kernels: block scatter/copy, segmented FP64 grouped GEMM, batched
+// Householder QR and batched one-sided Jacobi SVD for the small dense blocks of
+// a block-sparse MPS.  All arithmetic is float64.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.h"
+
+namespace bsm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int64_t kCopyChunk = 16384;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over the block; every thread gets the result
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+struct CopyChunk {
+    int task;
+    int64_t beg, end;
+};
+
+__global__ void __launch_bounds__(kThreads) k_copy(const CopyTask* __restrict__ tasks,
+                                                   const CopyChunk* __restrict__ chunks) {
+    const CopyChunk ch = chunks[blockIdx.x];
+    const CopyTask tk = tasks[ch.task];
+    for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
+        const int i = (int)(e / tk.cols), j = (int)(e % tk.cols);
+        const int64_t si = tk.src_cm ? (int64_t)j * tk.src_ld + i : (int64_t)i * tk.src_ld + j;
+        const int64_t di = tk.dst_cm ? (int64_t)j * tk.dst_ld + i : (int64_t)i * tk.dst_ld + j;
+        const double v = tk.f * tk.src[si];
+        if (tk.accumulate)
+            tk.dst[di] += v;
+        else
+            tk.dst[di] = v;
+    }
+}
+
+struct GemmTile {
+    int out, m0, n0;
+};
+
+constexpr int kTile = 32;
+
+// 32 x 32 output tile per CTA; thread (ty, tx) owns rows ty + 8 r (r < 4), column tx.
+__global__ void __launch_bounds__(kThreads) k_gemm(const GemmOut* __restrict__ outs,
+                                                   const GemmIn* __restrict__ ins,
+                                                   const GemmTile* __restrict__ tiles) {
+    __shared__ double As[kTile][kTile + 1];   // [k][m]
+    __shared__ double Bs[kTile][kTile + 1];   // [k][n]
+    const GemmTile tl = tiles[blockIdx.x];
+    const GemmOut o = outs[tl.out];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = o.beg; c < o.end; ++c) {
+        const GemmIn in = ins[c];
+        for (int k0 = 0; k0 < in.K; k0 += kTile) {
+            for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+                int mm, kk;
+                if (in.transA) {
+                    kk = idx / kTile;
+                    mm = idx % kTile;
+                } else {
+                    mm = idx / kTile;
+                    kk = idx % kTile;
+                }
+                const int gm = tl.m0 + mm, gk = k0 + kk;
+                double v = 0.0;
+                if (gm < o.M && gk < in.K)
+                    v = in.transA ? in.A[(int64_t)gk * in.lda + gm] : in.A[(int64_t)gm * in.lda + gk];
+                As[kk][mm] = in.alpha * v;
+            }
+            for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+                const int kk = idx / kTile, nn = idx % kTile;
+                const int gk = k0 + kk, gn = tl.n0 + nn;
+                Bs[kk][nn] = (gk < in.K && gn < o.N) ? in.B[(int64_t)gk * in.ldb + gn] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < kTile; ++kk) {
+                const double b = Bs[kk][tx];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] = fma(As[kk][ty + 8 * r], b, acc[r]);
+            }
+            __syncthreads();
+        }
+    }
+    const int gn = tl.n0 + tx;
+    if (gn >= o.N) return;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int gm = tl.m0 + ty + 8 * r;
+        if (gm < o.M) {
+            double* cp = o.C + (int64_t)gm * o.ldc + gn;
+            *cp = o.beta == 0.0 ? acc[r] : o.beta * (*cp) + acc[r];
+        }
+    }
+}
+
+// Householder QR, one CTA per matrix, working in global memory (L1/L2 resident
+// for the small blocks).  Reflector H = I - tau v v^T with v_j = 1,
+// beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x/(alpha - beta).
+__global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ tasks) {
+    __shared__ double red[33];
+    __shared__ double s_tau, s_scale;
+    const QrTask tk = tasks[blockIdx.x];
+    const int M = tk.M, N = tk.N, k = M < N ? M : N;
+    double* A = tk.A;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j < k; ++j) {
+        double s = 0.0;
+        for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) {
+            const double v = A[(int64_t)j * M + i];
+            s += v * v;
+        }
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) {
+            const double alpha = A[(int64_t)j * M + j];
+            if (s == 0.0) {
+                s_tau = 0.0;
+                s_scale = 0.0;
+            } else {
+                const double nrm = sqrt(alpha * alpha + s);
+                const double beta = alpha >= 0.0 ? -nrm : nrm;
+                s_tau = (beta - alpha) / beta;
+                s_scale = 1.0 / (alpha - beta);
+                A[(int64_t)j * M + j] = beta;
+            }
+            tk.tau[j] = s_tau;
+        }
+        __syncthreads();
+        const double tau = s_tau, scale = s_scale;
+        if (tau != 0.0) {
+            for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) A[(int64_t)j * M + i] *= scale;
+            __syncthreads();
+            for (int c = j + 1 + warp; c < N; c += kWarps) {
+                // read A(j, c) before the warp-synchronous reduction: lane 0 rewrites it after
+                const double a_jc = A[(int64_t)c * M + j];
+                double w = 0.0;
+                for (int i = j + 1 + lane; i < M; i += 32) w += A[(int64_t)j * M + i] * A[(int64_t)c * M + i];
+                w = warp_sum(w) + a_jc;
+                const double tw = tau * w;
+                if (lane == 0) A[(int64_t)c * M + j] -= tw;
+                for (int i = j + 1 + lane; i < M; i += 32) A[(int64_t)c * M + i] -= tw * A[(int64_t)j * M + i];
+            }
+        }
+        __syncthreads();
+    }
+    // R (k x N row-major) from the upper trapezoid
+    for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += kThreads) {
+        const int r = (int)(e / N), c = (int)(e % N);
+        tk.R[e] = c >= r ? A[(int64_t)c * M + r] : 0.0;
+    }
+    // Q = H_0 ... H_{k-1} applied to the first k columns of I (backward accumulation)
+    double* Q = tk.Q;
+    for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += kThreads) {
+        const int i = (int)(e % M), c = (int)(e / M);
+        Q[e] = i == c ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = k - 1; j >= 0; --j) {
+        const double tau = tk.tau[j];
+        if (tau == 0.0) continue;
+        for (int c = j + warp; c < k; c += kWarps) {
+            const double q_jc = Q[(int64_t)c * M + j];
+            double w = 0.0;
+            for (int i = j + 1 + lane; i < M; i += 32) w += A[(int64_t)j * M + i] * Q[(int64_t)c * M + i];
+            w = warp_sum(w) + q_jc;
+            const double tw = tau * w;
+            if (lane == 0) Q[(int64_t)c * M + j] -= tw;
+            for (int i = j + 1 + lane; i < M; i += 32) Q[(int64_t)c * M + i] -= tw * A[(int64_t)j * M + i];
+        }
+        __syncthreads();
+    }
+    // diag(R) >= 0
+    for (int j = warp; j < k; j += kWarps) {
+        if (tk.R[(int64_t)j * N + j] < 0.0) {
+            for (int c = lane; c < N; c += 32) tk.R[(int64_t)j * N + c] = -tk.R[(int64_t)j * N + c];
+            for (int i = lane; i < M; i += 32) Q[(int64_t)j * M + i] = -Q[(int64_t)j * M + i];
+        }
+    }
+}
+
+__device__ __forceinline__ int rr_player(int pos, int round, int n2) {
+    return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1;
+}
+
+constexpr int kMaxSweeps = 60;
+
+// One-sided (Hestenes) Jacobi SVD, parallel round-robin pair order, one CTA
+// per matrix.  Rotation: zeta = (b - a)/(2 g), t = sign(zeta)/(|zeta| +
+// sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t; a pair is rotated while
+// |g| > tol sqrt(a b), tol = len * DBL_EPSILON.
+__global__ void __launch_bounds__(kThreads) k_svd(const SvdTask* __restrict__ tasks,
+                                                  int* __restrict__ perm_pool,
+                                                  const int64_t* __restrict__ perm_off) {
+    __shared__ int s_rot;
+    const SvdTask tk = tasks[blockIdx.x];
+    const int len = tk.wide ? tk.N : tk.M;
+    const int n = tk.wide ? tk.M : tk.N;
+    double* G = tk.G;
+    double* V = tk.V;
+    int* perm = perm_pool + perm_off[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += kThreads)
+        V[e] = (e % n) == (e / n) ? 1.0 : 0.0;
+    __syncthreads();
+    const double tol = (double)len * DBL_EPSILON;
+    const int n2 = n + (n & 1);
+    for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
+        if (threadIdx.x == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < n2 - 1; ++round) {
+            for (int pi = warp; pi < n2 / 2; pi += kWarps) {
+                int p = rr_player(pi, round, n2), q = rr_player(n2 - 1 - pi, round, n2);
+                if (p >= n || q >= n) continue;
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int i = lane; i < len; i += 32) {
+                    const double xp = G[(int64_t)p * len + i], xq = G[(int64_t)q * len + i];
+                    a += xp * xp;
+                    b += xq * xq;
+                    g += xp * xq;
+                }
+                a = warp_sum(a);
+                b = warp_sum(b);
+                g = warp_sum(g);
+                if (fabs(g) > tol * sqrt(a * b) && g != 0.0) {
+                    const double zeta = (b - a) / (2.0 * g);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                    for (int i = lane; i < len; i += 32) {
+                        const double xp = G[(int64_t)p * len + i], xq = G[(int64_t)q * len + i];
+                        G[(int64_t)p * len + i] = c * xp - s * xq;
+                        G[(int64_t)q * len + i] = s * xp + c * xq;
+                    }
+                    for (int i = lane; i < n; i += 32) {
+                        const double vp = V[(int64_t)p * n + i], vq = V[(int64_t)q * n + i];
+                        V[(int64_t)p * n + i] = c * vp - s * vq;
+                        V[(int64_t)q * n + i] = s * vp + c * vq;
+                    }
+                    if (lane == 0) s_rot = 1;
+                }
+            }
+            __syncthreads();
+        }
+        if (!s_rot) break;
+        __syncthreads();
+    }
+    // column norms -> S (unsorted, in the S buffer), then stable descending order
+    for (int j = warp; j < n; j += kWarps) {
+        double a = 0.0;
+        for (int i = lane; i < len; i += 32) {
+            const double x = G[(int64_t)j * len + i];
+            a += x * x;
+        }
+        a = warp_sum(a);
+        if (lane == 0) tk.S[j] = sqrt(a);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+        const double si = tk.S[i];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+            const double sj = tk.S[j];
+            rank += (sj > si || (sj == si && j < i)) ? 1 : 0;
+        }
+        perm[rank] = i;
+    }
+    __syncthreads();
+    const int k = n;
+    // US (M x k row-major) and Vt (k x N row-major)
+    for (int64_t e = threadIdx.x; e < (int64_t)tk.M * k; e += kThreads) {
+        const int i = (int)(e / k), r = (int)(e % k);
+        const int j = perm[r];
+        tk.US[e] = tk.wide ? V[(int64_t)j * n + i] * tk.S[j] : G[(int64_t)j * len + i];
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)k * tk.N; e += kThreads) {
+        const int r = (int)(e / tk.N), c = (int)(e % tk.N);
+        const int j = perm[r];
+        double v;
+        if (tk.wide) {
+            const double sj = tk.S[j];
+            v = sj > 0.0 ? G[(int64_t)j * len + c] / sj : 0.0;
+        } else {
+            v = V[(int64_t)j * n + c];
+        }
+        tk.Vt[e] = v;
+    }
+    __syncthreads();
+    // sorted singular values (overwrite S in order; read the old values first)
+    double* sorted = tk.G;   // G is no longer needed: reuse its first k entries
+    for (int r = threadIdx.x; r < k; r += kThreads) sorted[r] = tk.S[perm[r]];
+    __syncthreads();
+    for (int r = threadIdx.x; r < k; r += kThreads) tk.S[r] = sorted[r];
+    __syncthreads();
+    // sign: the largest |entry| of every row of Vt is positive
+    for (int r = warp; r < k; r += kWarps) {
+        double best = -1.0;
+        int bi = 0;
+        for (int c = lane; c < tk.N; c += 32) {
+            const double a = fabs(tk.Vt[(int64_t)r * tk.N + c]);
+            if (a > best) {
+                best = a;
+                bi = c;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (tk.Vt[(int64_t)r * tk.N + bi] < 0.0) {
+            for (int c = lane; c < tk.N; c += 32) tk.Vt[(int64_t)r * tk.N + c] = -tk.Vt[(int64_t)r * tk.N + c];
+            for (int i = lane; i < tk.M; i += 32) tk.US[(int64_t)i * k + r] = -tk.US[(int64_t)i * k + r];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sumsq(const double* const* __restrict__ xs,
+                                                    const int64_t* __restrict__ ns,
+                                                    double* __restrict__ out) {
+    __shared__ double red[33];
+    const double* x = xs[blockIdx.x];
+    const int64_t n = ns[blockIdx.x];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) s += x[i] * x[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+void check_launch(Context* ctx) {
+    ctx->launches++;
+    BSM_CUDA(cudaGetLastError());
+}
+
+// RAII bracket of one launch for the optional profiler
+struct ProfScope {
+    Context* ctx;
+    int kind;
+    double flops, bytes;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(Context* c, int k, double f, double b) : ctx(c), kind(k), flops(f), bytes(b) {
+        if (ctx->profiling) ctx->prof_begin(&e0);
+    }
+    void done() {
+        if (ctx->profiling) ctx->prof_end(kind, flops, bytes, e0);
+    }
+};
+
+}  // namespace
+
+cudaEvent_t Context::take_event() {
+    cudaEvent_t e;
+    if (!event_pool.empty()) {
+        e = event_pool.back();
+        event_pool.pop_back();
+    } else {
+        BSM_CUDA(cudaEventCreate(&e));
+    }
+    return e;
+}
+
+void Context::prof_begin(cudaEvent_t* e0) {
+    *e0 = take_event();
+    BSM_CUDA(cudaEventRecord(*e0, stream));
+}
+
+void Context::prof_end(int kind, double fl, double by, cudaEvent_t e0) {
+    cudaEvent_t e1 = take_event();
+    BSM_CUDA(cudaEventRecord(e1, stream));
+    prof.push_back({kind, fl, by, e0, e1});
+}
+
+void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
+    if (tasks.empty()) return;
+    std::vector<CopyChunk> chunks;
+    for (int i = 0; i < (int)tasks.size(); ++i) {
+        const int64_t n = (int64_t)tasks[i].rows * tasks[i].cols;
+        for (int64_t b = 0; b < n; b += kCopyChunk) chunks.push_back({i, b, std::min(n, b + kCopyChunk)});
+    }
+    if (chunks.empty()) return;
+    double by = 0.0;
+    for (const CopyTask& t : tasks) by += (t.accumulate ? 24.0 : 16.0) * t.rows * (double)t.cols;
+    Scratch s(ctx);
+    CopyTask* dt = s.up(tasks);
+    CopyChunk* dc = s.up(chunks);
+    ProfScope ps(ctx, KK_COPY, 0.0, by);
+    k_copy<<<(unsigned)chunks.size(), kThreads, 0, ctx->stream>>>(dt, dc);
+    check_launch(ctx);
+    ps.done();
+}
+
+void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins) {
+    if (outs.empty()) return;
+    std::vector<GemmTile> tiles;
+    double fl = 0.0, by = 0.0;
+    for (int o = 0; o < (int)outs.size(); ++o) {
+        const GemmOut& g = outs[o];
+        for (int m0 = 0; m0 < g.M; m0 += kTile)
+            for (int n0 = 0; n0 < g.N; n0 += kTile) tiles.push_back({o, m0, n0});
+        for (int c = g.beg; c < g.end; ++c) {
+            fl += 2.0 * g.M * g.N * (double)ins[c].K;
+            by += 8.0 * ((double)g.M * ins[c].K + (double)ins[c].K * g.N);
+        }
+        by += 8.0 * g.M * (double)g.N * (g.beta == 0.0 ? 1.0 : 2.0);
+    }
+    if (tiles.empty()) return;
+    ctx->flops += fl;
+    Scratch s(ctx);
+    GemmOut* d_o = s.up(outs);
+    GemmIn* d_i = s.up(ins);
+    GemmTile* d_t = s.up(tiles);
+    ProfScope ps(ctx, KK_GEMM, fl, by);
+    k_gemm<<<(unsigned)tiles.size(), kThreads, 0, ctx->stream>>>(d_o, d_i, d_t);
+    check_launch(ctx);
+    ps.done();
+}
+
+void launch_qr(Context* ctx, const std::vector<QrTask>& tasks) {
+    if (tasks.empty()) return;
+    double fl = 0.0, by = 0.0;
+    for (const QrTask& t : tasks) {
+        const double m = t.M, n = t.N, k = std::min(m, n);
+        fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k;   // factorisation
+        fl += 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;                     // forming Q
+        by += 8.0 * (m * n + m * k + k * n);
+    }
+    ctx->flops += fl;
+    Scratch s(ctx);
+    QrTask* d = s.up(tasks);
+    ProfScope ps(ctx, KK_QR, fl, by);
+    k_qr<<<(unsigned)tasks.size(), kThreads, 0, ctx->stream>>>(d);
+    check_launch(ctx);
+    ps.done();
+}
+
+void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
+    if (tasks.empty()) return;
+    std::vector<int64_t> poff;
+    int64_t tot = 0;
+    double fl = 0.0, by = 0.0;
+    for (const SvdTask& t : tasks) {
+        poff.push_back(tot);
+        const double n = std::min(t.M, t.N), len = std::max(t.M, t.N);
+        tot += (int64_t)n;
+        fl += 6.0 * 6.0 * n * n * (len + n) / 2.0;   // nominal: 6 sweeps of n^2/2 rotations
+        by += 8.0 * (2.0 * t.M * (double)t.N + t.M * n + n + n * n);
+    }
+    ctx->flops += fl;
+    Scratch s(ctx);
+    SvdTask* d = s.up(tasks);
+    int64_t* d_off = s.up(poff);
+    int* perm = (int*)ctx->alloc(sizeof(int) * (size_t)std::max<int64_t>(tot, 1));
+    s.ptrs.push_back(perm);
+    ProfScope ps(ctx, KK_SVD, fl, by);
+    k_svd<<<(unsigned)tasks.size(), kThreads, 0, ctx->stream>>>(d, perm, d_off);
+    check_launch(ctx);
+    ps.done();
+}
+
+void launch_sumsq(Context* ctx, const std::vector<const double*>& xs, const std::vector<int64_t>& ns,
+                  double* out_dev) {
+    if (xs.empty()) return;
+    Scratch s(ctx);
+    const double** d_x = s.up(xs);
+    int64_t* d_n = s.up(ns);
+    double by = 0.0;
+    for (int64_t n : ns) by += 8.0 * n;
+    ProfScope ps(ctx, KK_SUMSQ, 2.0 * by / 8.0, by);
+    k_sumsq<<<(unsigned)xs.size(), kThreads, 0, ctx->stream>>>(d_x, d_n, out_dev);
+    check_launch(ctx);
+    ps.done();
+}
+
+}  // namespace bsm

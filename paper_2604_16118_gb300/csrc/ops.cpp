@@ -1,0 +1,683 @@
+// Host orchestration of the block-sparse MPS operations (Sec. 2.2-2.4).
+#include "ops.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+#include "kernels.h"
+
+namespace bsm {
+
+Mps::~Mps() {
+    if (ctx)
+        for (double* p : core)
+            if (p) ctx->free(p);
+}
+
+Mps* new_mps(Context* ctx, const Layout& L, bool zero) {
+    MpsPtr x(new Mps);
+    x->ctx = ctx;
+    x->lay = L;
+    x->core.assign(L.K, nullptr);
+    for (int t = 0; t < L.K; ++t) {
+        const int64_t n = L.core_size[t];
+        if (n > 0) {
+            x->core[t] = (double*)ctx->alloc((size_t)n * sizeof(double));
+            if (zero) BSM_CUDA(cudaMemsetAsync(x->core[t], 0, (size_t)n * sizeof(double), ctx->stream));
+        }
+    }
+    return x.release();
+}
+
+static MpsPtr make_mps(Context* ctx, const Layout& L, bool zero) { return MpsPtr(new_mps(ctx, L, zero)); }
+
+void mps_upload(Mps* x, const double* host) {
+    int64_t off = 0;
+    for (int t = 0; t < x->lay.K; ++t) {
+        const int64_t n = x->lay.core_size[t];
+        if (n > 0)
+            BSM_CUDA(cudaMemcpyAsync(x->core[t], host + off, (size_t)n * sizeof(double),
+                                     cudaMemcpyHostToDevice, x->ctx->stream));
+        off += n;
+    }
+    x->ctx->sync();
+}
+
+void mps_download(const Mps* x, double* host) {
+    int64_t off = 0;
+    for (int t = 0; t < x->lay.K; ++t) {
+        const int64_t n = x->lay.core_size[t];
+        if (n > 0)
+            BSM_CUDA(cudaMemcpyAsync(host + off, x->core[t], (size_t)n * sizeof(double),
+                                     cudaMemcpyDeviceToHost, x->ctx->stream));
+        off += n;
+    }
+    x->ctx->sync();
+}
+
+bool same_space(const Layout& a, const Layout& b) {
+    return a.K == b.K && a.species == b.species && a.target == b.target;
+}
+
+// per-site lookup (left sector index, sigma) -> block index
+static std::vector<int> block_lookup(const Layout& L, int t) {
+    std::vector<int> idx(L.bonds[t].q.size() * 2, -1);
+    for (int i = 0; i < (int)L.blocks[t].size(); ++i)
+        idx[L.blocks[t][i].li * 2 + L.blocks[t][i].sigma] = i;
+    return idx;
+}
+
+static void rebuild_site(Layout& L, int t) {
+    L.blocks[t].clear();
+    int64_t off = 0;
+    const Bond& bl = L.bonds[t];
+    const Bond& br = L.bonds[t + 1];
+    for (int li = 0; li < (int)bl.q.size(); ++li)
+        for (int sg = 0; sg < 2; ++sg) {
+            const int ri = br.find(bl.q[li] + site_delta(L.species[t], sg));
+            if (ri < 0) continue;
+            Block bk{li, ri, sg, bl.dim[li], br.dim[ri], off};
+            off += (int64_t)bk.rows * bk.cols;
+            L.blocks[t].push_back(bk);
+        }
+    L.core_size[t] = off;
+}
+
+MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms) {
+    BSM_REQUIRE(!terms.empty(), BSMPS_ERR_INVALID_ARG, "concat of nothing");
+    const Layout& L0 = terms[0].x->lay;
+    for (auto& tm : terms)
+        BSM_REQUIRE(same_space(tm.x->lay, L0), BSMPS_ERR_INVALID_ARG,
+                    "MPS of different sites or particle numbers");
+    const int K = L0.K;
+    Layout R;
+    R.K = K;
+    R.species = L0.species;
+    R.target = L0.target;
+    R.bonds.resize(K + 1);
+    // offsets[i][b][sector of R]
+    std::vector<std::vector<std::vector<int>>> offs(terms.size(), std::vector<std::vector<int>>(K + 1));
+    for (int b = 0; b <= K; ++b) {
+        std::vector<Charge> qs;
+        for (auto& tm : terms)
+            for (auto& q : tm.x->lay.bonds[b].q) qs.push_back(q);
+        std::sort(qs.begin(), qs.end());
+        qs.erase(std::unique(qs.begin(), qs.end()), qs.end());
+        R.bonds[b].q = qs;
+        R.bonds[b].dim.assign(qs.size(), 0);
+        for (size_t i = 0; i < terms.size(); ++i) offs[i][b].assign(qs.size(), 0);
+        for (size_t s = 0; s < qs.size(); ++s) {
+            int acc = 0;
+            for (size_t i = 0; i < terms.size(); ++i) {
+                offs[i][b][s] = (b == 0 || b == K) ? 0 : acc;
+                const int j = terms[i].x->lay.bonds[b].find(qs[s]);
+                if (j >= 0) acc += terms[i].x->lay.bonds[b].dim[j];
+            }
+            R.bonds[b].dim[s] = (b == 0 || b == K) ? 1 : acc;
+        }
+    }
+    R.rebuild_blocks();
+    MpsPtr y = make_mps(ctx, R, true);
+    std::vector<std::vector<CopyTask>> per_term(terms.size());
+    for (size_t i = 0; i < terms.size(); ++i) {
+        const Mps* x = terms[i].x;
+        for (int t = 0; t < K; ++t) {
+            const std::vector<int> look = block_lookup(R, t);
+            for (const Block& bk : x->lay.blocks[t]) {
+                const int li = R.bonds[t].find(x->lay.bonds[t].q[bk.li]);
+                const int ri = R.bonds[t + 1].find(x->lay.bonds[t + 1].q[bk.ri]);
+                const Block& rb = R.blocks[t][look[li * 2 + bk.sigma]];
+                const int r0 = offs[i][t][li], c0 = offs[i][t + 1][ri];
+                double f = 1.0;
+                const std::vector<double>& fv = bk.sigma ? terms[i].f1 : terms[i].f0;
+                if (!fv.empty()) f = fv[t];
+                CopyTask ct{x->core[t] + bk.off, y->core[t] + rb.off + (int64_t)r0 * rb.cols + c0,
+                            bk.rows, bk.cols, bk.cols, rb.cols, 0, 0, K == 1 ? 1 : 0, f};
+                per_term[i].push_back(ct);
+            }
+        }
+    }
+    if (K == 1) {
+        for (auto& v : per_term) launch_copy(ctx, v);   // same destination: one launch per term
+    } else {
+        std::vector<CopyTask> all;
+        for (auto& v : per_term) all.insert(all.end(), v.begin(), v.end());
+        launch_copy(ctx, all);
+    }
+    return y;
+}
+
+MpsPtr op_scale_sites(Context* ctx, const Mps* x, const std::vector<double>& f0,
+                      const std::vector<double>& f1) {
+    MpsPtr y = make_mps(ctx, x->lay, false);
+    std::vector<CopyTask> tasks;
+    for (int t = 0; t < x->lay.K; ++t)
+        for (const Block& bk : x->lay.blocks[t]) {
+            const double f = bk.sigma ? (f1.empty() ? 1.0 : f1[t]) : (f0.empty() ? 1.0 : f0[t]);
+            tasks.push_back({x->core[t] + bk.off, y->core[t] + bk.off, bk.rows, bk.cols, bk.cols,
+                             bk.cols, 0, 0, 0, f});
+        }
+    launch_copy(ctx, tasks);
+    return y;
+}
+
+MpsPtr op_apply_exact(Context* ctx, const Mpo& W, const Mps* x, double shift) {
+    const Layout& X = x->lay;
+    BSM_REQUIRE(W.K == X.K && W.species == X.species, BSMPS_ERR_INVALID_ARG,
+                "MPO and MPS act on different sites");
+    const int K = X.K;
+    const auto valid = valid_sectors(X.species, X.target);
+    Layout Y;
+    Y.K = K;
+    Y.species = X.species;
+    Y.target = X.target;
+    Y.bonds.resize(K + 1);
+    // chan_off[b][sector][channel] = row offset of the channel's segment (-1: absent)
+    std::vector<std::vector<std::vector<int>>> chan_off(K + 1);
+    for (int b = 0; b <= K; ++b) {
+        const int w = W.bond_dim(b);
+        for (const Charge& m : valid[b]) {
+            std::vector<int> co(w, -1);
+            int tot = 0;
+            for (int a = 0; a < w; ++a) {
+                const int ni = X.bonds[b].find(m - W.charges[b][a]);
+                if (ni < 0) continue;
+                co[a] = tot;
+                tot += X.bonds[b].dim[ni];
+            }
+            if (tot > 0) {
+                Y.bonds[b].q.push_back(m);
+                Y.bonds[b].dim.push_back(tot);
+                chan_off[b].push_back(co);
+            }
+        }
+    }
+    Y.rebuild_blocks();
+    MpsPtr y = make_mps(ctx, Y, true);
+    std::vector<CopyTask> tasks;
+    double fl = 0.0;
+    for (int t = 0; t < K; ++t) {
+        const std::vector<int> look = block_lookup(Y, t);
+        const auto& ents = W.entries[t];
+        for (int ei = 0; ei < (int)ents.size(); ++ei) {
+            const MpoEntry& e = ents[ei];
+            double w = e.w;
+            if (t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1])) w += shift;
+            for (const Block& bk : X.blocks[t]) {
+                if (bk.sigma != e.si) continue;
+                const int ml = Y.bonds[t].find(X.bonds[t].q[bk.li] + W.charges[t][e.a]);
+                const int mr = Y.bonds[t + 1].find(X.bonds[t + 1].q[bk.ri] + W.charges[t + 1][e.b]);
+                if (ml < 0 || mr < 0) continue;
+                const int ra = chan_off[t][ml][e.a], rb = chan_off[t + 1][mr][e.b];
+                const int yb = look[ml * 2 + e.so];
+                if (ra < 0 || rb < 0 || yb < 0) continue;
+                const Block& yk = Y.blocks[t][yb];
+                tasks.push_back({x->core[t] + bk.off, y->core[t] + yk.off + (int64_t)ra * yk.cols + rb,
+                                 bk.rows, bk.cols, bk.cols, yk.cols, 0, 0, 0, w});
+                fl += 2.0 * bk.rows * bk.cols;
+            }
+        }
+    }
+    ctx->flops += fl;
+    launch_copy(ctx, tasks);
+    return y;
+}
+
+std::vector<int> choose_cut(std::vector<SvEntry> sv, int n_sectors, double tol2, int r_max,
+                            double* tol_disc2, double* cap_disc2) {
+    std::sort(sv.begin(), sv.end(), [](const SvEntry& a, const SvEntry& b) {
+        if (a.s != b.s) return a.s > b.s;
+        if (a.sector != b.sector) return a.sector < b.sector;
+        return a.j < b.j;
+    });
+    const double rtol = 1e-10;
+    const int n = (int)sv.size();
+    int keep = n;
+    double acc = 0.0;
+    while (keep > 0) {
+        const double s = sv[keep - 1].s;
+        if (acc + s * s <= tol2) {
+            acc += s * s;
+            keep -= 1;
+        } else {
+            break;
+        }
+    }
+    while (keep > 0 && keep < n && sv[keep].s >= sv[keep - 1].s * (1.0 - rtol)) keep += 1;
+    double td = 0.0;
+    for (int i = keep; i < n; ++i) td += sv[i].s * sv[i].s;
+    double cd = 0.0;
+    if (r_max > 0 && keep > r_max) {
+        int k2 = r_max;
+        while (k2 > 0 && sv[k2].s >= sv[k2 - 1].s * (1.0 - rtol)) k2 -= 1;
+        if (k2 == 0) k2 = r_max;
+        for (int i = k2; i < keep; ++i) cd += sv[i].s * sv[i].s;
+        keep = k2;
+    }
+    *tol_disc2 += td;
+    *cap_disc2 += cd;
+    std::vector<int> cnt(n_sectors, 0);
+    for (int i = 0; i < keep; ++i) cnt[sv[i].sector]++;
+    return cnt;
+}
+
+MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
+                   double* disc_cap) {
+    const int K = x->lay.K;
+    Layout L = x->lay;
+    std::vector<double*> cores = x->core;
+    std::vector<char> owned(K, 0);
+    auto release = [&](int t) {
+        if (owned[t] && cores[t]) ctx->free(cores[t]);
+        cores[t] = nullptr;
+        owned[t] = 0;
+    };
+    struct Guard {
+        std::vector<double*>* c;
+        std::vector<char>* o;
+        Context* ctx;
+        bool active = true;
+        ~Guard() {
+            if (!active) return;
+            for (size_t t = 0; t < c->size(); ++t)
+                if ((*o)[t] && (*c)[t]) ctx->free((*c)[t]);
+        }
+    } guard{&cores, &owned, ctx};
+    auto alloc_core = [&](int64_t n) -> double* {
+        return n > 0 ? (double*)ctx->alloc((size_t)n * sizeof(double)) : nullptr;
+    };
+
+    // ---- left-to-right QR sweep ----
+    for (int t = 0; t + 1 < K; ++t) {
+        Scratch s(ctx);
+        const Bond& bm = L.bonds[t + 1];
+        const int nm = (int)bm.q.size();
+        std::vector<int> Mrows(nm, 0), krank(nm, 0);
+        std::vector<std::vector<std::pair<int, int>>> stack(nm);   // (block index, row offset)
+        for (int bi = 0; bi < (int)L.blocks[t].size(); ++bi) {
+            const Block& bk = L.blocks[t][bi];
+            stack[bk.ri].push_back({bi, Mrows[bk.ri]});
+            Mrows[bk.ri] += bk.rows;
+        }
+        std::vector<double*> Am(nm, nullptr), Qm(nm, nullptr), Rm(nm, nullptr);
+        std::vector<CopyTask> gather;
+        std::vector<QrTask> qr;
+        for (int mi = 0; mi < nm; ++mi) {
+            const int M = Mrows[mi], N = bm.dim[mi];
+            if (M == 0) continue;
+            const int k = std::min(M, N);
+            krank[mi] = k;
+            Am[mi] = s.dbl((size_t)M * N);
+            Qm[mi] = s.dbl((size_t)M * k);
+            Rm[mi] = s.dbl((size_t)k * N);
+            double* tau = s.dbl((size_t)k);
+            for (auto& pr : stack[mi]) {
+                const Block& bk = L.blocks[t][pr.first];
+                gather.push_back({cores[t] + bk.off, Am[mi] + pr.second, bk.rows, bk.cols, bk.cols, M,
+                                  0, 1, 0, 1.0});
+            }
+            qr.push_back({Am[mi], Qm[mi], Rm[mi], tau, M, N});
+        }
+        launch_copy(ctx, gather);
+        launch_qr(ctx, qr);
+        Layout Ln = L;
+        {
+            Bond nb;
+            for (int mi = 0; mi < nm; ++mi)
+                if (krank[mi] > 0) {
+                    nb.q.push_back(bm.q[mi]);
+                    nb.dim.push_back(krank[mi]);
+                }
+            Ln.bonds[t + 1] = nb;
+            rebuild_site(Ln, t);
+            rebuild_site(Ln, t + 1);
+        }
+        double* nt = alloc_core(Ln.core_size[t]);
+        double* nt1 = alloc_core(Ln.core_size[t + 1]);
+        std::vector<CopyTask> qcopy;
+        for (const Block& nbk : Ln.blocks[t]) {
+            const int mi = bm.find(Ln.bonds[t + 1].q[nbk.ri]);
+            // row offset of this (li, sigma) block in the old stack
+            int r0 = -1;
+            for (auto& pr : stack[mi]) {
+                const Block& ob = L.blocks[t][pr.first];
+                if (ob.li == nbk.li && ob.sigma == nbk.sigma) r0 = pr.second;
+            }
+            qcopy.push_back({Qm[mi] + r0, nt + nbk.off, nbk.rows, nbk.cols, Mrows[mi], nbk.cols, 1, 0, 0,
+                             1.0});
+        }
+        launch_copy(ctx, qcopy);
+        std::vector<GemmOut> outs;
+        std::vector<GemmIn> ins;
+        const std::vector<int> oldlook = block_lookup(L, t + 1);
+        for (const Block& nbk : Ln.blocks[t + 1]) {
+            const int mi = bm.find(Ln.bonds[t + 1].q[nbk.li]);
+            const Block& ob = L.blocks[t + 1][oldlook[mi * 2 + nbk.sigma]];
+            outs.push_back({nt1 + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
+                            (int)ins.size() + 1, 0.0});
+            ins.push_back({Rm[mi], cores[t + 1] + ob.off, ob.rows, bm.dim[mi], ob.cols, 0, 1.0});
+        }
+        launch_gemm(ctx, outs, ins);
+        release(t);
+        release(t + 1);
+        cores[t] = nt;
+        owned[t] = 1;
+        cores[t + 1] = nt1;
+        owned[t + 1] = 1;
+        L = Ln;
+    }
+
+    // ---- right-to-left SVD sweep ----
+    const double tol2 = K > 1 ? eps * eps / (K - 1) : 0.0;
+    double td2 = 0.0, cd2 = 0.0;
+    for (int t = K - 1; t >= 1; --t) {
+        Scratch s(ctx);
+        const Bond& bn = L.bonds[t];
+        const int nn = (int)bn.q.size();
+        std::vector<int> c0(nn, 0), c1(nn, 0), b0(nn, -1), b1(nn, -1), kk(nn, 0);
+        for (int bi = 0; bi < (int)L.blocks[t].size(); ++bi) {
+            const Block& bk = L.blocks[t][bi];
+            if (bk.sigma == 0) {
+                c0[bk.li] = bk.cols;
+                b0[bk.li] = bi;
+            } else {
+                c1[bk.li] = bk.cols;
+                b1[bk.li] = bi;
+            }
+        }
+        std::vector<double*> US(nn, nullptr), Vt(nn, nullptr);
+        std::vector<int64_t> soff(nn, 0);
+        int64_t stot = 0;
+        for (int ni = 0; ni < nn; ++ni) {
+            const int M = bn.dim[ni], N = c0[ni] + c1[ni];
+            kk[ni] = N > 0 ? std::min(M, N) : 0;
+            soff[ni] = stot;
+            stot += kk[ni];
+        }
+        double* S_all = s.dbl((size_t)std::max<int64_t>(stot, 1));
+        std::vector<CopyTask> gather;
+        std::vector<SvdTask> svd;
+        for (int ni = 0; ni < nn; ++ni) {
+            if (kk[ni] == 0) continue;
+            const int M = bn.dim[ni], N = c0[ni] + c1[ni], k = kk[ni];
+            const int wide = M < N ? 1 : 0;
+            double* G = s.dbl((size_t)M * N);
+            double* V = s.dbl((size_t)k * k);
+            US[ni] = s.dbl((size_t)M * k);
+            Vt[ni] = s.dbl((size_t)k * N);
+            for (int part = 0; part < 2; ++part) {
+                const int bi = part == 0 ? b0[ni] : b1[ni];
+                if (bi < 0) continue;
+                const Block& bk = L.blocks[t][bi];
+                const int coff = part == 0 ? 0 : c0[ni];
+                if (wide)
+                    gather.push_back({cores[t] + bk.off, G + coff, bk.rows, bk.cols, bk.cols, N, 0, 0, 0, 1.0});
+                else
+                    gather.push_back({cores[t] + bk.off, G + (int64_t)coff * M, bk.rows, bk.cols, bk.cols, M,
+                                      0, 1, 0, 1.0});
+            }
+            svd.push_back({G, V, S_all + soff[ni], US[ni], Vt[ni], M, N, wide});
+        }
+        launch_copy(ctx, gather);
+        launch_svd(ctx, svd);
+        std::vector<double> S_h((size_t)stot);
+        if (stot > 0) {
+            BSM_CUDA(cudaMemcpyAsync(S_h.data(), S_all, (size_t)stot * sizeof(double),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+            ctx->sync();
+        }
+        std::vector<SvEntry> sv;
+        for (int ni = 0; ni < nn; ++ni)
+            for (int j = 0; j < kk[ni]; ++j) sv.push_back({S_h[soff[ni] + j], ni, j});
+        const std::vector<int> keep = choose_cut(sv, nn, tol2, r_max, &td2, &cd2);
+        Layout Ln = L;
+        {
+            Bond nb;
+            for (int ni = 0; ni < nn; ++ni)
+                if (keep[ni] > 0) {
+                    nb.q.push_back(bn.q[ni]);
+                    nb.dim.push_back(keep[ni]);
+                }
+            Ln.bonds[t] = nb;
+            rebuild_site(Ln, t - 1);
+            rebuild_site(Ln, t);
+        }
+        double* nt = alloc_core(Ln.core_size[t]);
+        double* ntm = alloc_core(Ln.core_size[t - 1]);
+        std::vector<CopyTask> vcopy;
+        for (const Block& nbk : Ln.blocks[t]) {
+            const int ni = bn.find(Ln.bonds[t].q[nbk.li]);
+            const int coff = nbk.sigma == 0 ? 0 : c0[ni];
+            const int N = c0[ni] + c1[ni];
+            vcopy.push_back({Vt[ni] + coff, nt + nbk.off, nbk.rows, nbk.cols, N, nbk.cols, 0, 0, 0, 1.0});
+        }
+        launch_copy(ctx, vcopy);
+        std::vector<GemmOut> outs;
+        std::vector<GemmIn> ins;
+        const std::vector<int> oldlook = block_lookup(L, t - 1);
+        for (const Block& nbk : Ln.blocks[t - 1]) {
+            const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
+            const Block& ob = L.blocks[t - 1][oldlook[nbk.li * 2 + nbk.sigma]];
+            outs.push_back({ntm + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
+                            (int)ins.size() + 1, 0.0});
+            ins.push_back({cores[t - 1] + ob.off, US[ni], bn.dim[ni], ob.cols, kk[ni], 0, 1.0});
+        }
+        launch_gemm(ctx, outs, ins);
+        release(t);
+        release(t - 1);
+        cores[t] = nt;
+        owned[t] = 1;
+        cores[t - 1] = ntm;
+        owned[t - 1] = 1;
+        L = Ln;
+    }
+    if (disc_tol) *disc_tol = std::sqrt(td2);
+    if (disc_cap) *disc_cap = std::sqrt(cd2);
+
+    MpsPtr y(new Mps);
+    y->ctx = ctx;
+    y->lay = L;
+    y->core.assign(K, nullptr);
+    for (int t = 0; t < K; ++t) {
+        if (owned[t]) {
+            y->core[t] = cores[t];
+        } else if (L.core_size[t] > 0) {   // untouched core (K == 1): copy
+            y->core[t] = alloc_core(L.core_size[t]);
+            BSM_CUDA(cudaMemcpyAsync(y->core[t], cores[t], (size_t)L.core_size[t] * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        owned[t] = 0;
+    }
+    guard.active = false;
+    return y;
+}
+
+namespace {
+struct EnvBlk {
+    int c, ia, ib;
+    int rows, cols;
+    double* ptr;
+};
+
+Mpo identity_mpo(const Layout& L) {
+    Mpo I;
+    I.K = L.K;
+    I.species = L.species;
+    I.charges.assign(L.K + 1, std::vector<Charge>(1, Charge{0, 0}));
+    I.entries.assign(L.K, {{0, 0, 0, 0, 1.0}, {0, 0, 1, 1, 1.0}});
+    return I;
+}
+}  // namespace
+
+std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs) {
+    const int P = (int)probs.size();
+    std::vector<double> result(P, 0.0);
+    if (P == 0) return result;
+    const int K = probs[0].a->lay.K;
+    std::vector<Mpo> ids;
+    ids.reserve(P);
+    std::vector<const Mpo*> ops(P);
+    for (int p = 0; p < P; ++p) {
+        const EnvProblem& pr = probs[p];
+        BSM_REQUIRE(same_space(pr.a->lay, pr.b->lay) && pr.a->lay.K == K, BSMPS_ERR_INVALID_ARG,
+                    "dot of MPS of different spaces");
+        if (pr.W) {
+            BSM_REQUIRE(pr.W->K == K && pr.W->species == pr.a->lay.species, BSMPS_ERR_INVALID_ARG,
+                        "MPO and MPS act on different sites");
+            ops[p] = pr.W;
+        } else {
+            ids.push_back(identity_mpo(pr.a->lay));
+            ops[p] = &ids.back();
+        }
+    }
+    // bond 0 environments: [[1]] on (channel 0, sector 0, sector 0)
+    std::vector<std::vector<EnvBlk>> E(P);
+    Scratch keep0(ctx);
+    double* one = nullptr;
+    {
+        std::vector<double> v(1, 1.0);
+        one = keep0.up(v);
+    }
+    for (int p = 0; p < P; ++p) {
+        const Layout& A = probs[p].a->lay;
+        const Layout& B = probs[p].b->lay;
+        if (!A.bonds[0].q.empty() && !B.bonds[0].q.empty()) E[p].push_back({0, 0, 0, 1, 1, one});
+    }
+    double* prevbuf = nullptr;
+    for (int t = 0; t < K; ++t) {
+        // ---- structure of this site ----
+        struct TBlk {
+            int env, sigma, rows, cols;
+            int64_t off;
+        };
+        std::vector<std::vector<TBlk>> T(P);
+        // contributions: key (d, ra, rb) -> list of (T index, alpha) and the a-block
+        std::vector<std::map<std::tuple<int, int, int>, std::vector<std::tuple<int, int, double>>>> contrib(P);
+        int64_t tot_T = 0;
+        for (int p = 0; p < P; ++p) {
+            const Layout& A = probs[p].a->lay;
+            const Layout& B = probs[p].b->lay;
+            const std::vector<int> blook = block_lookup(B, t);
+            const std::vector<int> alook = block_lookup(A, t);
+            // T blocks: env e x b-block (ib, si)
+            std::vector<std::array<int, 2>> tidx(E[p].size(), {-1, -1});
+            for (int e = 0; e < (int)E[p].size(); ++e)
+                for (int si = 0; si < 2; ++si) {
+                    const int bb = blook[E[p][e].ib * 2 + si];
+                    if (bb < 0) continue;
+                    tidx[e][si] = (int)T[p].size();
+                    T[p].push_back({e, si, E[p][e].rows, B.blocks[t][bb].cols, tot_T});
+                    tot_T += (int64_t)E[p][e].rows * B.blocks[t][bb].cols;
+                }
+            // env blocks by channel
+            std::map<int, std::vector<int>> by_chan;
+            for (int e = 0; e < (int)E[p].size(); ++e) by_chan[E[p][e].c].push_back(e);
+            const Mpo& W = *ops[p];
+            for (int ei = 0; ei < (int)W.entries[t].size(); ++ei) {
+                const MpoEntry& me = W.entries[t][ei];
+                auto it = by_chan.find(me.a);
+                if (it == by_chan.end()) continue;
+                double w = me.w;
+                if (probs[p].W && t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1]))
+                    w += probs[p].shift;
+                double fa = 1.0, fb = 1.0;
+                if (me.so == 0 ? probs[p].fa0 : probs[p].fa1) fa = (*(me.so == 0 ? probs[p].fa0 : probs[p].fa1))[t];
+                if (me.si == 0 ? probs[p].fb0 : probs[p].fb1) fb = (*(me.si == 0 ? probs[p].fb0 : probs[p].fb1))[t];
+                const double alpha = w * fa * fb;
+                for (int e : it->second) {
+                    const int ab = alook[E[p][e].ia * 2 + me.so];
+                    const int ti = tidx[e][me.si];
+                    if (ab < 0 || ti < 0) continue;
+                    const int bb = blook[E[p][e].ib * 2 + me.si];
+                    const int ra = A.blocks[t][ab].ri, rb = B.blocks[t][bb].ri;
+                    contrib[p][std::make_tuple(me.b, ra, rb)].push_back(std::make_tuple(ti, ab, alpha));
+                }
+            }
+        }
+        // ---- buffers ----
+        int64_t tot_E = 0;
+        std::vector<std::vector<EnvBlk>> En(P);
+        for (int p = 0; p < P; ++p) {
+            const Layout& A = probs[p].a->lay;
+            const Layout& B = probs[p].b->lay;
+            for (auto& kv : contrib[p]) {
+                const int d = std::get<0>(kv.first), ra = std::get<1>(kv.first), rb = std::get<2>(kv.first);
+                En[p].push_back({d, ra, rb, A.bonds[t + 1].dim[ra], B.bonds[t + 1].dim[rb],
+                                 (double*)(intptr_t)tot_E});
+                tot_E += (int64_t)A.bonds[t + 1].dim[ra] * B.bonds[t + 1].dim[rb];
+            }
+        }
+        Scratch s(ctx);
+        double* Tbuf = s.dbl((size_t)std::max<int64_t>(tot_T, 1));
+        double* Ebuf = (double*)ctx->alloc(sizeof(double) * (size_t)std::max<int64_t>(tot_E, 1));
+        // stage 1: T = E * X_b(ib, si)
+        std::vector<GemmOut> o1;
+        std::vector<GemmIn> i1;
+        for (int p = 0; p < P; ++p) {
+            const Layout& B = probs[p].b->lay;
+            const std::vector<int> blook = block_lookup(B, t);
+            for (const TBlk& tb : T[p]) {
+                const EnvBlk& eb = E[p][tb.env];
+                const Block& bk = B.blocks[t][blook[eb.ib * 2 + tb.sigma]];
+                o1.push_back({Tbuf + tb.off, tb.rows, tb.cols, tb.cols, (int)i1.size(), (int)i1.size() + 1, 0.0});
+                i1.push_back({eb.ptr, probs[p].b->core[t] + bk.off, eb.cols, eb.cols, bk.cols, 0, 1.0});
+            }
+        }
+        launch_gemm(ctx, o1, i1);
+        // stage 2: E'(d, ra, rb) = sum alpha X_a(ia, so)^T T
+        std::vector<GemmOut> o2;
+        std::vector<GemmIn> i2;
+        for (int p = 0; p < P; ++p) {
+            const Layout& A = probs[p].a->lay;
+            int q = 0;
+            for (auto& kv : contrib[p]) {
+                EnvBlk& nb = En[p][q++];
+                nb.ptr = Ebuf + (int64_t)(intptr_t)nb.ptr;
+                const int beg = (int)i2.size();
+                for (auto& c : kv.second) {
+                    const TBlk& tb = T[p][std::get<0>(c)];
+                    const Block& ab = A.blocks[t][std::get<1>(c)];
+                    i2.push_back({probs[p].a->core[t] + ab.off, Tbuf + tb.off, ab.rows, ab.cols, tb.cols, 1,
+                                  std::get<2>(c)});
+                }
+                o2.push_back({nb.ptr, nb.rows, nb.cols, nb.cols, beg, (int)i2.size(), 0.0});
+            }
+        }
+        launch_gemm(ctx, o2, i2);
+        if (prevbuf) ctx->free(prevbuf);
+        prevbuf = Ebuf;
+        E.swap(En);
+    }
+    // bond K: sum of the remaining 1x1 blocks
+    std::vector<CopyTask> g;
+    Scratch s(ctx);
+    double* res = s.dbl((size_t)P);
+    BSM_CUDA(cudaMemsetAsync(res, 0, sizeof(double) * P, ctx->stream));
+    std::vector<std::vector<CopyTask>> rounds;
+    for (int p = 0; p < P; ++p)
+        for (size_t e = 0; e < E[p].size(); ++e) {
+            if (rounds.size() <= e) rounds.resize(e + 1);
+            rounds[e].push_back({E[p][e].ptr, res + p, 1, 1, 1, 1, 0, 0, 1, 1.0});
+        }
+    for (auto& r : rounds) launch_copy(ctx, r);
+    BSM_CUDA(cudaMemcpyAsync(result.data(), res, sizeof(double) * P, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    if (prevbuf) ctx->free(prevbuf);
+    return result;
+}
+
+double op_core0_norm(Context* ctx, const Mps* x) {
+    if (x->lay.K == 0 || x->lay.core_size[0] == 0) return 0.0;
+    Scratch s(ctx);
+    double* d = s.dbl(1);
+    launch_sumsq(ctx, {x->core[0]}, {x->lay.core_size[0]}, d);
+    double h = 0.0;
+    BSM_CUDA(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    return std::sqrt(h);
+}
+
+}  // namespace bsm

@@ -1,0 +1,63 @@
+// MPS operations on the device (host orchestration of the kernels).
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "common.h"
+
+namespace bsm {
+
+using MpsPtr = std::unique_ptr<Mps>;
+
+void mps_upload(Mps* x, const double* host_flat);
+void mps_download(const Mps* x, double* host_flat);
+
+// One term of a block concatenation: x with its sigma=0 / sigma=1 blocks of
+// site t scaled by f0[t] / f1[t] (empty vectors: 1).
+struct ConcatTerm {
+    const Mps* x;
+    std::vector<double> f0, f1;
+};
+
+// sum_i term_i by block concatenation (Sec. 2.3): union of sectors, inner
+// bonds stacked in term order, first core side by side, last core stacked.
+MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms);
+MpsPtr op_scale_sites(Context* ctx, const Mps* x, const std::vector<double>& f0,
+                      const std::vector<double>& f1);
+
+// y = (H_gamma + shift I) x exactly (Sec. 2.4).
+MpsPtr op_apply_exact(Context* ctx, const Mpo& W, const Mps* x, double shift);
+
+// trunc_eps with rank cap (Sec. 2.2); discarded norms are returned.
+MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
+                   double* disc_cap);
+
+// Which pooled singular values of one bond survive (Sec. 2.2); entries
+// (sigma, sector, j).  Returns kept counts per sector.
+struct SvEntry {
+    double s;
+    int sector, j;
+};
+std::vector<int> choose_cut(std::vector<SvEntry> sv, int n_sectors, double tol2, int r_max,
+                            double* tol_disc2, double* cap_disc2);
+
+// <S_a a, O S_b b> for a batch of problems, O = (H_gamma + shift) or identity.
+struct EnvProblem {
+    const Mps* a;
+    const Mps* b;
+    const Mpo* W;               // nullptr: identity
+    double shift;
+    const std::vector<double>* fa0 = nullptr;   // per-site scalings of a (nullptr: 1)
+    const std::vector<double>* fa1 = nullptr;
+    const std::vector<double>* fb0 = nullptr;
+    const std::vector<double>* fb1 = nullptr;
+};
+std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs);
+
+// Frobenius norm of core 0 (the norm of a right-orthogonalised MPS).
+double op_core0_norm(Context* ctx, const Mps* x);
+
+bool same_space(const Layout& a, const Layout& b);
+
+}  // namespace bsm

@@ -1,0 +1,30 @@
+// Preconditioner terms and the Alg. 2 step.
+#pragma once
+
+#include <tuple>
+#include <vector>
+
+#include "ops.h"
+
+namespace bsm {
+
+constexpr int kMaxEtaRetries = 60;
+
+struct PrecondTerms {
+    double h = 0.0;
+    int m_minus = 0, m_plus = 0;
+    std::vector<std::vector<double>> f0, f1;   // per term, per site
+    int n_terms() const { return (int)f0.size(); }
+};
+
+PrecondTerms make_precond(const bsmps_precond* p);
+std::vector<double> pair_sums(Context* ctx, const PrecondTerms& P,
+                              const std::vector<std::tuple<const Mps*, const Mps*, const Mpo*>>& jobs);
+double eigvec_bound(double rho, double delta);
+double releig_bound(double rho, double delta);
+void rr2(const double H[2][2], const double E[2][2], double* mu, double v[2]);
+double delta_A(double rho, double q);
+MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
+                       bsmps_solver_state& st, const Mps* x, bsmps_step_info& info);
+
+}  // namespace bsm

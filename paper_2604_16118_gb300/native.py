@@ -1,0 +1,375 @@
+"""Thin Python binding of the C ABI in include/bsmps.h (argument marshalling only).
+
+Every computation runs in libbsmps.so; importing this module fails loudly when
+the library has not been built (there is no CPU fallback).
+"""
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libbsmps.so")
+
+OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CHARGE", 3: "OOM", 4: "RANK_CAP", 5: "NOT_SPD",
+          6: "NUMERIC", 7: "TIMEOUT", 8: "CUDA"}
+
+
+class BsmpsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Precond(C.Structure):
+    _fields_ = [("K", C.c_int), ("d", C.POINTER(C.c_double)), ("t_min", C.c_double),
+                ("t_max", C.c_double), ("c0", C.c_double), ("alpha0", C.c_double)]
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("c", C.c_double), ("delta", C.c_double), ("eps_num", C.c_double),
+                ("t_eig", C.c_double), ("tau", C.c_double)]
+
+
+class SolverState(C.Structure):
+    _fields_ = [("eta_res", C.c_double), ("n", C.c_int)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("rho", C.c_double), ("eta_res", C.c_double),
+                ("res_norm", C.c_double), ("eta_tries", C.c_int), ("bound", C.c_double),
+                ("releig_bound", C.c_double), ("lambda_star", C.c_double), ("omega", C.c_double),
+                ("eta_in", C.c_double), ("delta_A", C.c_double), ("converged", C.c_int),
+                ("max_rank", C.c_int), ("flops", C.c_double)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["lambda"] = d.pop("lambda_")
+        return d
+
+
+_vp = C.c_void_p
+_i = C.c_int
+_d = C.c_double
+_i64 = C.c_int64
+_pd = C.POINTER(C.c_double)
+_pi = C.POINTER(C.c_int)
+_pi64 = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "bsmps_status_string": (C.c_char_p, [_i]),
+    "bsmps_ctx_create": (_i, [_i, _vp, C.POINTER(_vp)]),
+    "bsmps_ctx_destroy": (_i, [_vp]),
+    "bsmps_ctx_sync": (_i, [_vp]),
+    "bsmps_last_error": (C.c_char_p, [_vp]),
+    "bsmps_ctx_launch_count": (_i64, [_vp]),
+    "bsmps_ctx_profile": (_i, [_vp, _i]),
+    "bsmps_ctx_kernel_stats": (_i, [_vp, _i, _i, _pi64, _pd, _pd, _pd]),
+    "bsmps_mps_random_size": (_i, [_i, _i, _i, _i, _i, _pi64]),
+    "bsmps_mps_create": (_i, [_vp, _i, _i, _i, _i, _i, _i, _pd, _i64, C.POINTER(_vp)]),
+    "bsmps_mps_import": (_i, [_vp, _i, _i, _i, _i, _pi, _pi, _pd, _i64, C.POINTER(_vp)]),
+    "bsmps_mps_num_sites": (_i, [_vp, _pi]),
+    "bsmps_mps_num_sectors": (_i, [_vp, _pi, _pi]),
+    "bsmps_mps_sectors": (_i, [_vp, _pi]),
+    "bsmps_mps_size": (_i, [_vp, _pi64]),
+    "bsmps_mps_export": (_i, [_vp, _pd]),
+    "bsmps_mps_destroy": (_i, [_vp]),
+    "bsmps_mpo_from_integrals": (_i, [_vp, _i, _pd, _pd, _i, _i, _d, _d, C.POINTER(_vp)]),
+    "bsmps_mpo_bond_dims": (_i, [_vp, _pi]),
+    "bsmps_mpo_num_entries": (_i, [_vp, _i, _pi]),
+    "bsmps_mpo_entries": (_i, [_vp, _i, _pi, _pd]),
+    "bsmps_mpo_channel_charges": (_i, [_vp, _i, _pi]),
+    "bsmps_mpo_destroy": (_i, [_vp]),
+    "bsmps_apply_H": (_i, [_vp, _vp, _vp, _d, _d, _i, C.POINTER(_vp), _pd]),
+    "bsmps_truncate": (_i, [_vp, _vp, _d, _i, C.POINTER(_vp), _pd, _pd]),
+    "bsmps_add": (_i, [_vp, _vp, _vp, _d, _d, C.POINTER(_vp)]),
+    "bsmps_scale_sites": (_i, [_vp, _vp, _pd, _pd, C.POINTER(_vp)]),
+    "bsmps_precondition": (_i, [_vp, C.POINTER(Precond), _i, _vp, C.POINTER(_vp), _pi]),
+    "bsmps_dot": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
+    "bsmps_eigensolve_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
+                                   C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(StepInfo)]),
+}
+
+DECLARED = tuple(_SIGS.keys())
+
+
+def load(path=None):
+    path = _LIB_PATH if path is None else path
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2604_16118_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def _check(ctx, code):
+    if code != OK:
+        msg = lib().bsmps_last_error(ctx.h if ctx is not None else None)
+        raise BsmpsError(code, (msg or b"").decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_pd)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(_pi)
+
+
+class Context:
+    """bsmps_ctx: a device and the stream all work is ordered on."""
+
+    def __init__(self, device=0, stream=None):
+        h = _vp()
+        self.h = None
+        _check(None, lib().bsmps_ctx_create(device, stream, C.byref(h)))
+        self.h = h
+
+    def sync(self):
+        _check(self, lib().bsmps_ctx_sync(self.h))
+
+    def launch_count(self):
+        return int(lib().bsmps_ctx_launch_count(self.h))
+
+    KERNELS = ("copy", "gemm", "qr", "svd", "sumsq")
+
+    def profile(self, enable=True):
+        _check(self, lib().bsmps_ctx_profile(self.h, 1 if enable else 0))
+
+    def kernel_stats(self, reset=True):
+        """{kind: (launches, ms, flops, bytes)} of the profiled launches."""
+        out = {}
+        for k, name in enumerate(self.KERNELS):
+            n = C.c_int64()
+            ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+            _check(self, lib().bsmps_ctx_kernel_stats(self.h, k, 1 if (reset and k == len(self.KERNELS) - 1) else 0,
+                                                      C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+            out[name] = (n.value, ms.value, fl.value, by.value)
+        return out
+
+    def close(self):
+        if self.h:
+            lib().bsmps_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MPS:
+    """bsmps_mps handle."""
+
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().bsmps_mps_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    @property
+    def K(self):
+        k = C.c_int()
+        _check(self.ctx, lib().bsmps_mps_num_sites(self.h, C.byref(k)))
+        return k.value
+
+    def bonds(self):
+        """Per bond: {(n0, n1): dim} in ascending sector order."""
+        K = self.K
+        per = np.zeros(K + 1, dtype=np.int32)
+        tot = C.c_int()
+        _check(self.ctx, lib().bsmps_mps_num_sectors(self.h, _iptr(per), C.byref(tot)))
+        tr = np.zeros(3 * max(tot.value, 1), dtype=np.int32)
+        _check(self.ctx, lib().bsmps_mps_sectors(self.h, _iptr(tr)))
+        out = []
+        pos = 0
+        for b in range(K + 1):
+            d = {}
+            for _ in range(per[b]):
+                d[(int(tr[3 * pos]), int(tr[3 * pos + 1]))] = int(tr[3 * pos + 2])
+                pos += 1
+            out.append(d)
+        return out
+
+    def ranks(self):
+        return [sum(b.values()) for b in self.bonds()]
+
+    def size(self):
+        n = C.c_int64()
+        _check(self.ctx, lib().bsmps_mps_size(self.h, C.byref(n)))
+        return n.value
+
+    def export(self):
+        v = np.zeros(max(self.size(), 1))
+        _check(self.ctx, lib().bsmps_mps_export(self.h, _dptr(v)))
+        return v[:self.size()]
+
+
+class MPO:
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().bsmps_mpo_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def bond_dims(self, K):
+        d = np.zeros(K + 1, dtype=np.int32)
+        _check(self.ctx, lib().bsmps_mpo_bond_dims(self.h, _iptr(d)))
+        return [int(v) for v in d]
+
+    def entries(self, site):
+        n = C.c_int()
+        _check(self.ctx, lib().bsmps_mpo_num_entries(self.h, site, C.byref(n)))
+        q = np.zeros(4 * max(n.value, 1), dtype=np.int32)
+        w = np.zeros(max(n.value, 1))
+        _check(self.ctx, lib().bsmps_mpo_entries(self.h, site, _iptr(q), _dptr(w)))
+        return [(int(q[4 * i]), int(q[4 * i + 1]), int(q[4 * i + 2]), int(q[4 * i + 3]), float(w[i]))
+                for i in range(n.value)]
+
+    def channel_charges(self, bond, width):
+        p = np.zeros(2 * max(width, 1), dtype=np.int32)
+        _check(self.ctx, lib().bsmps_mpo_channel_charges(self.h, bond, _iptr(p)))
+        return [(int(p[2 * i]), int(p[2 * i + 1])) for i in range(width)]
+
+
+def mps_random_size(n_orb, spin, n_up, n_dn, r_max):
+    n = C.c_int64()
+    _check(None, lib().bsmps_mps_random_size(n_orb, spin, n_up, n_dn, r_max, C.byref(n)))
+    return n.value
+
+
+def mps_create(ctx, n_orb, spin, n_up, n_dn, r_max=1, values=None):
+    """e_1 when values is None, else the random-rule iterate filled from values."""
+    h = _vp()
+    if values is None:
+        _check(ctx, lib().bsmps_mps_create(ctx.h, n_orb, spin, n_up, n_dn, r_max, 0, None, 0, C.byref(h)))
+    else:
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        _check(ctx, lib().bsmps_mps_create(ctx.h, n_orb, spin, n_up, n_dn, r_max, 1, _dptr(v), len(v),
+                                            C.byref(h)))
+    return MPS(ctx, h)
+
+
+def mps_import(ctx, n_orb, spin, n_up, n_dn, bonds, values):
+    """bonds: per bond {(n0, n1): dim}; values: flat layout."""
+    per = np.array([len(b) for b in bonds], dtype=np.int32)
+    tr = []
+    for b in bonds:
+        for q in sorted(b):
+            tr += [q[0], q[1], b[q]]
+    tr = np.array(tr if tr else [0], dtype=np.int32)
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    if len(v) == 0:
+        v = np.zeros(1)
+        n = 0
+    else:
+        n = len(v)
+    h = _vp()
+    _check(ctx, lib().bsmps_mps_import(ctx.h, n_orb, spin, n_up, n_dn, _iptr(per), _iptr(tr), _dptr(v), n,
+                                        C.byref(h)))
+    return MPS(ctx, h)
+
+
+def mpo_from_integrals(ctx, h, eri, spin, n_particles, gamma=0.0, compress_tol=0.0):
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    ee = np.ascontiguousarray(eri, dtype=np.float64)
+    out = _vp()
+    _check(ctx, lib().bsmps_mpo_from_integrals(ctx.h, hh.shape[0], _dptr(hh), _dptr(ee), spin, n_particles,
+                                                gamma, compress_tol, C.byref(out)))
+    return MPO(ctx, out)
+
+
+def apply_H(ctx, mpo, x, shift=0.0, tol=0.0, r_max=0):
+    y = _vp()
+    fl = C.c_double()
+    _check(ctx, lib().bsmps_apply_H(ctx.h, mpo.h, x.h, shift, tol, r_max, C.byref(y), C.byref(fl)))
+    return MPS(ctx, y), fl.value
+
+
+def truncate(ctx, x, eps, r_max=0):
+    y = _vp()
+    dt = C.c_double()
+    dc = C.c_double()
+    _check(ctx, lib().bsmps_truncate(ctx.h, x.h, eps, r_max, C.byref(y), C.byref(dt), C.byref(dc)))
+    return MPS(ctx, y), dt.value, dc.value
+
+
+def add(ctx, x, y, alpha=1.0, beta=1.0):
+    o = _vp()
+    _check(ctx, lib().bsmps_add(ctx.h, x.h, y.h, alpha, beta, C.byref(o)))
+    return MPS(ctx, o)
+
+
+def scale_sites(ctx, x, f0, f1):
+    a = np.ascontiguousarray(f0, dtype=np.float64)
+    b = np.ascontiguousarray(f1, dtype=np.float64)
+    o = _vp()
+    _check(ctx, lib().bsmps_scale_sites(ctx.h, x.h, _dptr(a), _dptr(b), C.byref(o)))
+    return MPS(ctx, o)
+
+
+def make_precond(d, t_min, t_max, c0, alpha0):
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    p = Precond(len(d), _dptr(d), t_min, t_max, c0, alpha0)
+    p._keep = d
+    return p
+
+
+def precondition(ctx, p, x, term=-1):
+    o = _vp()
+    n = C.c_int()
+    _check(ctx, lib().bsmps_precondition(ctx.h, C.byref(p), term, x.h, C.byref(o), C.byref(n)))
+    return MPS(ctx, o), n.value
+
+
+def dot(ctx, a, b, mpo=None, shift=0.0):
+    out = C.c_double()
+    _check(ctx, lib().bsmps_dot(ctx.h, a.h, b.h, mpo.h if mpo is not None else None, shift, C.byref(out)))
+    return out.value
+
+
+def solver_params(c, delta, eps_num=None, t_eig=0.5, tau=1e-8):
+    return SolverParams(c, delta, 0.5 * (1.0 - c) if eps_num is None else eps_num, t_eig, tau)
+
+
+def solver_state():
+    return SolverState(math.inf, 0)
+
+
+def eigensolve_step(ctx, mpo, p, params, state, x):
+    """One Alg. 2 step; returns (x_next, info dict).  x's handle is consumed."""
+    h = _vp(x.h.value)
+    info = StepInfo()
+    code = lib().bsmps_eigensolve_step(ctx.h, mpo.h, C.byref(p), C.byref(params), C.byref(state), C.byref(h),
+                                       C.byref(info))
+    _check(ctx, code)
+    x.h = None          # destroyed by the library
+    return MPS(ctx, h), info.as_dict()
