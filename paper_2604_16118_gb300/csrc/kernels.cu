@@ -205,43 +205,59 @@ __device__ __forceinline__ int rr_player(int pos, int round, int n2) {
     return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1;
 }
 
-constexpr int kMaxSweeps = 60;
+constexpr int kMaxSweeps = 40;
+constexpr int kSmemJacobiMax = 110;   // 2 k^2 doubles <= 193 KB of shared memory
 
-// One-sided (Hestenes) Jacobi SVD, parallel round-robin pair order, one CTA
-// per matrix.  Rotation: zeta = (b - a)/(2 g), t = sign(zeta)/(|zeta| +
-// sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t; a pair is rotated while
-// |g| > tol sqrt(a b), tol = len * DBL_EPSILON.
-__global__ void __launch_bounds__(kThreads) k_svd(const SvdTask* __restrict__ tasks,
-                                                  int* __restrict__ perm_pool,
-                                                  const int64_t* __restrict__ perm_off) {
+// One-sided Jacobi task on a k x k matrix G (column-major, overwritten by the
+// rotated columns) with the accumulated rotations in V (column-major).
+struct JacTask {
+    double* G;
+    double* V;
+    double* Sraw;    // column norms of the rotated G (unsorted)
+    int k;
+    int smem;        // 1: iterate in shared memory
+};
+
+// One-sided (Hestenes) Jacobi, parallel round-robin pair order, one CTA per
+// matrix.  Rotation: zeta = (b - a)/(2 g), t = sign(zeta)/(|zeta| +
+// sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t.  A pair is rotated while
+// |g| > k eps sqrt(a b) and both columns are above the numerical-zero level
+// (k eps ||G||_F); a sweep without rotations ends the iteration.
+__global__ void __launch_bounds__(kThreads) k_jacobi(const JacTask* __restrict__ tasks) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
     __shared__ int s_rot;
-    const SvdTask tk = tasks[blockIdx.x];
-    const int len = tk.wide ? tk.N : tk.M;
-    const int n = tk.wide ? tk.M : tk.N;
-    double* G = tk.G;
-    double* V = tk.V;
-    int* perm = perm_pool + perm_off[blockIdx.x];
+    const JacTask tk = tasks[blockIdx.x];
+    const int k = tk.k;
+    double* G = tk.smem ? sm : tk.G;
+    double* V = tk.smem ? sm + (int64_t)k * k : tk.V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += kThreads)
-        V[e] = (e % n) == (e / n) ? 1.0 : 0.0;
-    __syncthreads();
-    const double tol = (double)len * DBL_EPSILON;
-    const int n2 = n + (n & 1);
-    for (int sweep = 0; sweep < kMaxSweeps && n > 1; ++sweep) {
+    double f = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += kThreads) {
+        const double v = tk.G[e];
+        if (tk.smem) G[e] = v;
+        f += v * v;
+        V[e] = (e % k) == (e / k) ? 1.0 : 0.0;
+    }
+    f = block_sum(f, red);
+    const double tol = (double)k * DBL_EPSILON;
+    const double tiny2 = tol * tol * f;
+    const int n2 = k + (k & 1);
+    for (int sweep = 0; sweep < kMaxSweeps && k > 1; ++sweep) {
         if (threadIdx.x == 0) s_rot = 0;
         __syncthreads();
         for (int round = 0; round < n2 - 1; ++round) {
             for (int pi = warp; pi < n2 / 2; pi += kWarps) {
                 int p = rr_player(pi, round, n2), q = rr_player(n2 - 1 - pi, round, n2);
-                if (p >= n || q >= n) continue;
+                if (p >= k || q >= k) continue;
                 if (p > q) {
                     const int tmp = p;
                     p = q;
                     q = tmp;
                 }
                 double a = 0.0, b = 0.0, g = 0.0;
-                for (int i = lane; i < len; i += 32) {
-                    const double xp = G[(int64_t)p * len + i], xq = G[(int64_t)q * len + i];
+                for (int i = lane; i < k; i += 32) {
+                    const double xp = G[(int64_t)p * k + i], xq = G[(int64_t)q * k + i];
                     a += xp * xp;
                     b += xq * xq;
                     g += xp * xq;
@@ -249,74 +265,91 @@ __global__ void __launch_bounds__(kThreads) k_svd(const SvdTask* __restrict__ ta
                 a = warp_sum(a);
                 b = warp_sum(b);
                 g = warp_sum(g);
-                if (fabs(g) > tol * sqrt(a * b) && g != 0.0) {
+                if (g != 0.0 && fabs(g) > tol * sqrt(a * b) && fmin(a, b) > tiny2) {
                     const double zeta = (b - a) / (2.0 * g);
                     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    for (int i = lane; i < len; i += 32) {
-                        const double xp = G[(int64_t)p * len + i], xq = G[(int64_t)q * len + i];
-                        G[(int64_t)p * len + i] = c * xp - s * xq;
-                        G[(int64_t)q * len + i] = s * xp + c * xq;
-                    }
-                    for (int i = lane; i < n; i += 32) {
-                        const double vp = V[(int64_t)p * n + i], vq = V[(int64_t)q * n + i];
-                        V[(int64_t)p * n + i] = c * vp - s * vq;
-                        V[(int64_t)q * n + i] = s * vp + c * vq;
+                    for (int i = lane; i < k; i += 32) {
+                        const double xp = G[(int64_t)p * k + i], xq = G[(int64_t)q * k + i];
+                        G[(int64_t)p * k + i] = c * xp - s * xq;
+                        G[(int64_t)q * k + i] = s * xp + c * xq;
+                        const double vp = V[(int64_t)p * k + i], vq = V[(int64_t)q * k + i];
+                        V[(int64_t)p * k + i] = c * vp - s * vq;
+                        V[(int64_t)q * k + i] = s * vp + c * vq;
                     }
                     if (lane == 0) s_rot = 1;
                 }
             }
             __syncthreads();
         }
-        if (!s_rot) break;
+        const int rot = s_rot;
         __syncthreads();
+        if (!rot) break;
     }
-    // column norms -> S (unsorted, in the S buffer), then stable descending order
-    for (int j = warp; j < n; j += kWarps) {
+    for (int j = warp; j < k; j += kWarps) {
         double a = 0.0;
-        for (int i = lane; i < len; i += 32) {
-            const double x = G[(int64_t)j * len + i];
+        for (int i = lane; i < k; i += 32) {
+            const double x = G[(int64_t)j * k + i];
             a += x * x;
         }
         a = warp_sum(a);
-        if (lane == 0) tk.S[j] = sqrt(a);
+        if (lane == 0) tk.Sraw[j] = sqrt(a);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-        const double si = tk.S[i];
+    if (tk.smem) {
+        for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += kThreads) {
+            tk.G[e] = G[e];
+            tk.V[e] = V[e];
+        }
+    }
+}
+
+// Assemble the SVD of M (M x N) from QR + Jacobi of the triangular factor:
+// tall (M >= N): M = Q R, R^T = G, G V = U' S  =>  U = Q V, Vt = U'^T;
+// wide (M < N):  M^T = Q R, R^T = G, G V = U' S => U = U', Vt = (Q V)^T.
+// QVt = (Q V)^T (k x len, row-major) comes from a grouped GEMM.
+struct SvdFin {
+    const double* G;
+    const double* QVt;
+    const double* Sraw;
+    double* S;
+    double* US;
+    double* Vt;
+    int* perm;
+    int M, N, k, len, wide;
+};
+
+__global__ void __launch_bounds__(kThreads) k_svd_finalize(const SvdFin* __restrict__ tasks) {
+    const SvdFin tk = tasks[blockIdx.x];
+    const int k = tk.k, len = tk.len;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < k; i += kThreads) {
+        const double si = tk.Sraw[i];
         int rank = 0;
-        for (int j = 0; j < n; ++j) {
-            const double sj = tk.S[j];
+        for (int j = 0; j < k; ++j) {
+            const double sj = tk.Sraw[j];
             rank += (sj > si || (sj == si && j < i)) ? 1 : 0;
         }
-        perm[rank] = i;
+        tk.perm[rank] = i;
     }
     __syncthreads();
-    const int k = n;
-    // US (M x k row-major) and Vt (k x N row-major)
     for (int64_t e = threadIdx.x; e < (int64_t)tk.M * k; e += kThreads) {
         const int i = (int)(e / k), r = (int)(e % k);
-        const int j = perm[r];
-        tk.US[e] = tk.wide ? V[(int64_t)j * n + i] * tk.S[j] : G[(int64_t)j * len + i];
+        const int p = tk.perm[r];
+        tk.US[e] = tk.wide ? tk.G[(int64_t)p * k + i] : tk.Sraw[p] * tk.QVt[(int64_t)p * len + i];
     }
     for (int64_t e = threadIdx.x; e < (int64_t)k * tk.N; e += kThreads) {
         const int r = (int)(e / tk.N), c = (int)(e % tk.N);
-        const int j = perm[r];
+        const int p = tk.perm[r];
         double v;
         if (tk.wide) {
-            const double sj = tk.S[j];
-            v = sj > 0.0 ? G[(int64_t)j * len + c] / sj : 0.0;
+            v = tk.QVt[(int64_t)p * len + c];
         } else {
-            v = V[(int64_t)j * n + c];
+            const double sp = tk.Sraw[p];
+            v = sp > 0.0 ? tk.G[(int64_t)p * k + c] / sp : 0.0;
         }
         tk.Vt[e] = v;
     }
-    __syncthreads();
-    // sorted singular values (overwrite S in order; read the old values first)
-    double* sorted = tk.G;   // G is no longer needed: reuse its first k entries
-    for (int r = threadIdx.x; r < k; r += kThreads) sorted[r] = tk.S[perm[r]];
-    __syncthreads();
-    for (int r = threadIdx.x; r < k; r += kThreads) tk.S[r] = sorted[r];
+    for (int r = threadIdx.x; r < k; r += kThreads) tk.S[r] = tk.Sraw[tk.perm[r]];
     __syncthreads();
     // sign: the largest |entry| of every row of Vt is positive
     for (int r = warp; r < k; r += kWarps) {
@@ -464,24 +497,78 @@ void launch_qr(Context* ctx, const std::vector<QrTask>& tasks) {
 
 void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
     if (tasks.empty()) return;
-    std::vector<int64_t> poff;
-    int64_t tot = 0;
+    Scratch s(ctx);
+    // 1. Householder QR of M (tall) or M^T (wide): Q is len x k, R is k x k
+    std::vector<QrTask> qr;
+    std::vector<double*> Q(tasks.size()), R(tasks.size()), V(tasks.size()), Sraw(tasks.size()), QVt(tasks.size());
+    std::vector<int*> perm(tasks.size());
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        const SvdTask& t = tasks[i];
+        const int k = std::min(t.M, t.N), len = std::max(t.M, t.N);
+        Q[i] = s.dbl((size_t)len * k);
+        R[i] = s.dbl((size_t)k * k);
+        V[i] = s.dbl((size_t)k * k);
+        Sraw[i] = s.dbl((size_t)k);
+        QVt[i] = s.dbl((size_t)k * len);
+        perm[i] = (int*)ctx->alloc(sizeof(int) * (size_t)k);
+        s.ptrs.push_back(perm[i]);
+        qr.push_back({t.G, Q[i], R[i], s.dbl((size_t)k), t.wide ? t.N : t.M, t.wide ? t.M : t.N});
+    }
+    launch_qr(ctx, qr);
+    // 2. one-sided Jacobi on G = R^T (the row-major R is G column-major)
+    std::vector<JacTask> small, large;
+    int kmax_small = 1;
     double fl = 0.0, by = 0.0;
-    for (const SvdTask& t : tasks) {
-        poff.push_back(tot);
-        const double n = std::min(t.M, t.N), len = std::max(t.M, t.N);
-        tot += (int64_t)n;
-        fl += 6.0 * 6.0 * n * n * (len + n) / 2.0;   // nominal: 6 sweeps of n^2/2 rotations
-        by += 8.0 * (2.0 * t.M * (double)t.N + t.M * n + n + n * n);
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        const int k = std::min(tasks[i].M, tasks[i].N);
+        JacTask jt{R[i], V[i], Sraw[i], k, k <= kSmemJacobiMax ? 1 : 0};
+        if (jt.smem) {
+            small.push_back(jt);
+            kmax_small = std::max(kmax_small, k);
+        } else {
+            large.push_back(jt);
+        }
+        fl += 54.0 * (double)k * k * k;   // nominal: 6 sweeps of k^2/2 pairs x 18k flops
+        by += 8.0 * 3.0 * k * (double)k;
     }
     ctx->flops += fl;
-    Scratch s(ctx);
-    SvdTask* d = s.up(tasks);
-    int64_t* d_off = s.up(poff);
-    int* perm = (int*)ctx->alloc(sizeof(int) * (size_t)std::max<int64_t>(tot, 1));
-    s.ptrs.push_back(perm);
-    ProfScope ps(ctx, KK_SVD, fl, by);
-    k_svd<<<(unsigned)tasks.size(), kThreads, 0, ctx->stream>>>(d, perm, d_off);
+    {
+        ProfScope ps(ctx, KK_SVD, fl, by);
+        if (!small.empty()) {
+            JacTask* d = s.up(small);
+            const size_t smem = sizeof(double) * 2 * (size_t)kmax_small * kmax_small;
+            BSM_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_jacobi<<<(unsigned)small.size(), kThreads, smem, ctx->stream>>>(d);
+            check_launch(ctx);
+        }
+        if (!large.empty()) {
+            JacTask* d = s.up(large);
+            k_jacobi<<<(unsigned)large.size(), kThreads, 0, ctx->stream>>>(d);
+            check_launch(ctx);
+        }
+        ps.done();
+    }
+    // 3. (Q V)^T = V^T Q^T: A = V column-major read as V^T row-major, B = Q column-major = Q^T row-major
+    std::vector<GemmOut> outs;
+    std::vector<GemmIn> ins;
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        const int k = std::min(tasks[i].M, tasks[i].N), len = std::max(tasks[i].M, tasks[i].N);
+        outs.push_back({QVt[i], k, len, len, (int)ins.size(), (int)ins.size() + 1, 0.0});
+        ins.push_back({V[i], Q[i], k, k, len, 0, 1.0});
+    }
+    launch_gemm(ctx, outs, ins);
+    // 4. sort, assemble U S and V^T, sign convention
+    std::vector<SvdFin> fin;
+    double fb = 0.0;
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        const SvdTask& t = tasks[i];
+        const int k = std::min(t.M, t.N), len = std::max(t.M, t.N);
+        fin.push_back({R[i], QVt[i], Sraw[i], t.S, t.US, t.Vt, perm[i], t.M, t.N, k, len, t.wide});
+        fb += 8.0 * ((double)t.M * k + (double)k * t.N + 2.0 * k * (double)len);
+    }
+    SvdFin* d = s.up(fin);
+    ProfScope ps(ctx, KK_SVD, 0.0, fb);
+    k_svd_finalize<<<(unsigned)fin.size(), kThreads, 0, ctx->stream>>>(d);
     check_launch(ctx);
     ps.done();
 }

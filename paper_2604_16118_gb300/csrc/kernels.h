@@ -47,15 +47,15 @@ struct QrTask {
     int M, N;
 };
 
-// One-sided Jacobi SVD of an M x N matrix.  The working matrix G (len x n,
-// column-major, n = min(M, N)) is A itself when M >= N ("tall", G = A
-// column-major) or A^T when M < N ("wide", G = A^T column-major, i.e. A
-// row-major).  Outputs: S (k, descending), US = U diag(S) (M x k, row-major),
-// Vt (k x N, row-major); the largest-|.| entry of every row of Vt is positive.
-// V is n x n workspace.
+// SVD of an M x N matrix A, k = min(M, N), given in G: A column-major when
+// M >= N ("tall"), A row-major (= A^T column-major) when M < N ("wide"); G is
+// destroyed.  Householder QR of A (tall) or A^T (wide), one-sided Jacobi on the
+// k x k triangular factor, then assembly.  Outputs: S (k, descending),
+// US = U diag(S) (M x k, row-major), Vt (k x N, row-major); the largest-|.|
+// entry of every row of Vt is positive.
 struct SvdTask {
     double* G;
-    double* V;
+    double* V;        // unused (kept for layout compatibility)
     double* S;
     double* US;
     double* Vt;
