@@ -48,7 +48,8 @@ def setup(ctx, nat, seed, L=32, r_max=256):
     tmin, tmax = problem.spectrum_bounds(th, 1, n, n)
     W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, 1, 2 * n, gamma)
     p = nat.make_precond(th, tmin, tmax, prm["c0"], prm["alpha0"])
-    sp = nat.solver_params(prm["c"], prm["delta"], eps_num=prm["eps_num"], t_eig=prm["t_eig"], tau=1e-8)
+    sp = nat.solver_params(prm["c"], prm["delta"], eps_num=prm["eps_num"], t_eig=prm["t_eig"], tau=1e-8,
+                           r_max=r_max)
     nval = nat.mps_random_size(L, 1, n, n, r_max)
     x = nat.mps_create(ctx, L, 1, n, n, r_max, random_block_values(nval, seed))
     return dict(wl=wl, W=W, p=p, sp=sp, x=x, gamma=gamma, theta=th, tmin=tmin, tmax=tmax, prm=prm)

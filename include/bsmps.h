@@ -93,13 +93,19 @@ typedef struct {
 /* Constants of Alg. 2: c (Eq. (specequivA)), delta >= lambda_2/(lambda_2 -
  * lambda_1) (Sec. 5.4), eps_num in (0, 1-c) (Lemma truncr; Sec. 7.1.3 uses
  * (1-c)/2), t_eig in (0,1) (Thm. conv (ii)), tau the eigenvector tolerance of
- * the termination test (Thm. aposterbound). */
+ * the termination test (Thm. aposterbound).  r_max > 0 caps the ranks of the
+ * truncated iterate x^{n+1} (0: no cap).  u_rel: each exactly applied term
+ * u_k' = (H_gamma - lambda) S_k' x is compressed once by trunc at
+ * u_rel ||u_k'|| before the residual sum (1e-13 keeps the terms exact to
+ * working precision; 0 disables). */
 typedef struct {
     double c;
     double delta;
     double eps_num;
     double t_eig;
     double tau;
+    int r_max;
+    double u_rel;
 } bsmps_solver_params;
 
 /* State carried between steps: eta_res of the previous step (start with
@@ -125,6 +131,7 @@ typedef struct {
     int converged;        /* 1 when the termination test of Alg. 2 held */
     int max_rank;         /* largest bond dimension of the returned iterate */
     double flops;         /* algorithmic FP64 flops issued by the step */
+    double cap_discarded; /* norm discarded by the r_max cap of the iterate */
 } bsmps_step_info;
 
 BSMPS_API const char* bsmps_status_string(bsmps_status s);

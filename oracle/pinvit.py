@@ -10,9 +10,14 @@ Readings of the paper used here:
   v is scaled so that v^T G_E v = 1 (then ||x*||_A^2 = lambda_*) and v_1 > 0.
 * Delta_A solves sqrt(1 - D^2) - rho D = q in closed form,
   D = (-q rho + sqrt(1 + rho^2 - q^2)) / (1 + rho^2).
-* Residual terms s_{k,k'} = S_k (H_gamma - lambda) S_{k'} x are formed from the
-  exact u_{k'} = (H_gamma - lambda) S_{k'} x; ties in the norm sort are broken
-  by (k, k') ascending.
+* Residual terms s_{k,k'} = S_k (H_gamma - lambda) S_{k'} x are formed from
+  u_{k'} = (H_gamma - lambda) S_{k'} x, applied exactly and then compressed
+  once with trunc at U_REL ||u_{k'}|| (U_REL = 1e-13, far below any eta_res
+  the iteration reaches, so the terms stay exact to working precision); ties in
+  the norm sort are broken by (k, k') ascending.
+* The iterate truncation x^{n+1} = trunc_{eta_in}(x*) is capped at r_max ranks
+  when r_max > 0 (the workload's maximal MPS rank); the cap's discarded norm
+  is reported separately.
 * The eta_res loop is capped at MAX_ETA_RETRIES passes.
 * Delta_A is clamped at 0: at machine precision lambda_* can exceed lambda^n,
   q then exceeds 1 and the closed form turns (slightly) negative.
@@ -25,10 +30,12 @@ import numpy as np
 from . import bsmps as B
 
 MAX_ETA_RETRIES = 60
+U_REL = 1e-13
 
 
 class SolverParams:
-    def __init__(self, c, delta, eps_num=None, t_eig=0.5, tau=1e-8):
+    def __init__(self, c, delta, eps_num=None, t_eig=0.5, tau=1e-8, r_max=0):
+        self.r_max = r_max              # rank cap of the iterate (0: none)
         self.c = c                      # spectral equivalence constant, Eq. (specequivA)
         self.delta = delta              # gap bound delta >= lambda_2/(lambda_2 - lambda_1)
         self.eps_num = 0.5 * (1.0 - c) if eps_num is None else eps_num   # Sec. 7.1.3
@@ -73,6 +80,7 @@ def residual_terms(x, lam, prec, mpo):
     for kp in range(prec.n_terms):
         f0, f1 = prec.factors(kp)
         u = B.apply_exact(mpo, B.scale_sites(x, f0, f1), shift=-lam)
+        u, _, _ = B.truncate(u, U_REL * B.norm(u))
         for k in range(prec.n_terms):
             g0, g1 = prec.factors(k)
             s = B.scale_sites(u, g0, g1)
@@ -191,9 +199,9 @@ def step(x, mpo, prec, params, state):
     q = math.sqrt(lam_star / (lam_star + params.t_eig * (lam - lam_star)))
     dA = delta_A(rho, q)
     eta_in = dA * xstar_A / math.sqrt(1.0 + params.c)
-    xnext, _, _ = B.truncate(xstar, eta_in)
+    xnext, _, cap = B.truncate(xstar, eta_in, params.r_max)
     info.update({"lambda_star": lam_star, "omega": -c2 / c1, "eta_in": eta_in,
-                 "delta_A": dA, "ranks": xnext.ranks()})
+                 "delta_A": dA, "ranks": xnext.ranks(), "cap_discarded": cap})
     state.history.append(info)
     state.n += 1
     return xnext, info

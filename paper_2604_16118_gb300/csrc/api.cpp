@@ -443,7 +443,8 @@ bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_preco
         bsm::Context* c = C(ctx);
         BSM_REQUIRE(W && params && state && x && *x && info, BSMPS_ERR_INVALID_ARG, "null argument");
         BSM_REQUIRE(params->c > 0.0 && params->c < 1.0 && params->delta > 1.0 && params->eps_num > 0.0 &&
-                        params->eps_num < 1.0 - params->c && params->t_eig > 0.0 && params->t_eig < 1.0,
+                        params->eps_num < 1.0 - params->c && params->t_eig > 0.0 && params->t_eig < 1.0 &&
+                        params->r_max >= 0 && params->u_rel >= 0.0 && params->u_rel < 1e-3,
                     BSMPS_ERR_INVALID_ARG, "solver parameters out of range");
         const bsm::PrecondTerms P = bsm::make_precond(p);
         BSM_REQUIRE(p->K == M(*x)->lay.K, BSMPS_ERR_INVALID_ARG, "precond K differs from the MPS");

@@ -117,16 +117,24 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmOut* __restrict__ o
     }
 }
 
-// Householder QR, one CTA per matrix, working in global memory (L1/L2 resident
-// for the small blocks).  Reflector H = I - tau v v^T with v_j = 1,
-// beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta, v = x/(alpha - beta).
+// Householder QR, one CTA per matrix; the working set (A, Q, tau) lives in
+// shared memory when it fits (smem = 1), else in global memory.  Reflector
+// H = I - tau v v^T with v_j = 1, beta = -sign(alpha) ||x||,
+// tau = (beta - alpha)/beta, v = x/(alpha - beta).
 __global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ tasks) {
+    extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ double s_tau, s_scale;
     const QrTask tk = tasks[blockIdx.x];
     const int M = tk.M, N = tk.N, k = M < N ? M : N;
-    double* A = tk.A;
+    double* A = tk.smem ? sm : tk.A;
+    double* Q = tk.smem ? sm + (int64_t)M * N : tk.Q;
+    double* tau = tk.smem ? sm + (int64_t)M * N + (int64_t)M * k : tk.tau;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (tk.smem) {
+        for (int64_t e = threadIdx.x; e < (int64_t)M * N; e += kThreads) A[e] = tk.A[e];
+        __syncthreads();
+    }
     for (int j = 0; j < k; ++j) {
         double s = 0.0;
         for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) {
@@ -146,11 +154,11 @@ __global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ task
                 s_scale = 1.0 / (alpha - beta);
                 A[(int64_t)j * M + j] = beta;
             }
-            tk.tau[j] = s_tau;
+            tau[j] = s_tau;
         }
         __syncthreads();
-        const double tau = s_tau, scale = s_scale;
-        if (tau != 0.0) {
+        const double tj = s_tau, scale = s_scale;
+        if (tj != 0.0) {
             for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) A[(int64_t)j * M + i] *= scale;
             __syncthreads();
             for (int c = j + 1 + warp; c < N; c += kWarps) {
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ task
                 double w = 0.0;
                 for (int i = j + 1 + lane; i < M; i += 32) w += A[(int64_t)j * M + i] * A[(int64_t)c * M + i];
                 w = warp_sum(w) + a_jc;
-                const double tw = tau * w;
+                const double tw = tj * w;
                 if (lane == 0) A[(int64_t)c * M + j] -= tw;
                 for (int i = j + 1 + lane; i < M; i += 32) A[(int64_t)c * M + i] -= tw * A[(int64_t)j * M + i];
             }
@@ -172,32 +180,36 @@ __global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ task
         tk.R[e] = c >= r ? A[(int64_t)c * M + r] : 0.0;
     }
     // Q = H_0 ... H_{k-1} applied to the first k columns of I (backward accumulation)
-    double* Q = tk.Q;
     for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += kThreads) {
         const int i = (int)(e % M), c = (int)(e / M);
         Q[e] = i == c ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int j = k - 1; j >= 0; --j) {
-        const double tau = tk.tau[j];
-        if (tau == 0.0) continue;
+        const double tj = tau[j];
+        if (tj == 0.0) continue;
         for (int c = j + warp; c < k; c += kWarps) {
             const double q_jc = Q[(int64_t)c * M + j];
             double w = 0.0;
             for (int i = j + 1 + lane; i < M; i += 32) w += A[(int64_t)j * M + i] * Q[(int64_t)c * M + i];
             w = warp_sum(w) + q_jc;
-            const double tw = tau * w;
+            const double tw = tj * w;
             if (lane == 0) Q[(int64_t)c * M + j] -= tw;
             for (int i = j + 1 + lane; i < M; i += 32) Q[(int64_t)c * M + i] -= tw * A[(int64_t)j * M + i];
         }
         __syncthreads();
     }
-    // diag(R) >= 0
+    // diag(R) >= 0 (R is in global memory; every thread sees the final R after the barrier)
     for (int j = warp; j < k; j += kWarps) {
-        if (tk.R[(int64_t)j * N + j] < 0.0) {
+        const double rjj = A[(int64_t)j * M + j];
+        if (rjj < 0.0) {
             for (int c = lane; c < N; c += 32) tk.R[(int64_t)j * N + c] = -tk.R[(int64_t)j * N + c];
             for (int i = lane; i < M; i += 32) Q[(int64_t)j * M + i] = -Q[(int64_t)j * M + i];
         }
+    }
+    if (tk.smem) {
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += kThreads) tk.Q[e] = Q[e];
     }
 }
 
@@ -477,21 +489,43 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
     ps.done();
 }
 
-void launch_qr(Context* ctx, const std::vector<QrTask>& tasks) {
-    if (tasks.empty()) return;
+constexpr size_t kSmemBudget = 220 * 1024;
+
+void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in) {
+    if (tasks_in.empty()) return;
     double fl = 0.0, by = 0.0;
-    for (const QrTask& t : tasks) {
+    std::vector<QrTask> small, large;
+    size_t smem_max = 0;
+    for (QrTask t : tasks_in) {
         const double m = t.M, n = t.N, k = std::min(m, n);
         fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k;   // factorisation
         fl += 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;                     // forming Q
         by += 8.0 * (m * n + m * k + k * n);
+        const size_t need = sizeof(double) * ((size_t)t.M * t.N + (size_t)t.M * std::min(t.M, t.N) +
+                                              (size_t)std::min(t.M, t.N));
+        if (need <= kSmemBudget) {
+            t.smem = 1;
+            small.push_back(t);
+            smem_max = std::max(smem_max, need);
+        } else {
+            t.smem = 0;
+            large.push_back(t);
+        }
     }
     ctx->flops += fl;
     Scratch s(ctx);
-    QrTask* d = s.up(tasks);
     ProfScope ps(ctx, KK_QR, fl, by);
-    k_qr<<<(unsigned)tasks.size(), kThreads, 0, ctx->stream>>>(d);
-    check_launch(ctx);
+    if (!small.empty()) {
+        QrTask* d = s.up(small);
+        BSM_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+        k_qr<<<(unsigned)small.size(), kThreads, smem_max, ctx->stream>>>(d);
+        check_launch(ctx);
+    }
+    if (!large.empty()) {
+        QrTask* d = s.up(large);
+        k_qr<<<(unsigned)large.size(), kThreads, 0, ctx->stream>>>(d);
+        check_launch(ctx);
+    }
     ps.done();
 }
 

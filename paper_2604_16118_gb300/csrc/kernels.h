@@ -45,6 +45,7 @@ struct QrTask {
     double* R;
     double* tau;
     int M, N;
+    int smem = 0;     // set by launch_qr
 };
 
 // SVD of an M x N matrix A, k = min(M, N), given in G: A column-major when

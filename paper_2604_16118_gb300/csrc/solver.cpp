@@ -152,6 +152,15 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
         MpsPtr sx = op_scale_sites(ctx, x.get(), P.f0[kp], P.f1[kp]);
         u[kp] = op_apply_exact(ctx, W, sx.get(), -lam);
     }
+    if (prm.u_rel > 0.0) {
+        // one near-lossless compression per exactly applied term (trunc at u_rel ||u||)
+        std::vector<EnvProblem> up;
+        for (int kp = 0; kp < nt; ++kp) up.push_back({u[kp].get(), u[kp].get(), nullptr, 0.0});
+        const std::vector<double> un2 = op_dot_batch(ctx, up);
+        for (int kp = 0; kp < nt; ++kp)
+            u[kp] = op_truncate(ctx, u[kp].get(), prm.u_rel * std::sqrt(std::max(un2[kp], 0.0)), 0, nullptr,
+                                nullptr);
+    }
     std::vector<EnvProblem> nprobs;
     for (int kp = 0; kp < nt; ++kp)
         for (int k = 0; k < nt; ++k) {
@@ -263,7 +272,9 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
     const double q = std::sqrt(lam_star / (lam_star + prm.t_eig * (lam - lam_star)));
     const double dA = delta_A(rho, q);
     const double eta_in = dA * xstar_A / std::sqrt(1.0 + prm.c);
-    MpsPtr xn = op_truncate(ctx, xstar.get(), eta_in, 0, nullptr, nullptr);
+    double cap_disc = 0.0;
+    MpsPtr xn = op_truncate(ctx, xstar.get(), eta_in, prm.r_max, nullptr, &cap_disc);
+    info.cap_discarded = cap_disc;
     info.lambda_star = lam_star;
     info.omega = -c2 / c1;
     info.eta_in = eta_in;

@@ -30,7 +30,7 @@ class Precond(C.Structure):
 
 class SolverParams(C.Structure):
     _fields_ = [("c", C.c_double), ("delta", C.c_double), ("eps_num", C.c_double),
-                ("t_eig", C.c_double), ("tau", C.c_double)]
+                ("t_eig", C.c_double), ("tau", C.c_double), ("r_max", C.c_int), ("u_rel", C.c_double)]
 
 
 class SolverState(C.Structure):
@@ -42,7 +42,7 @@ class StepInfo(C.Structure):
                 ("res_norm", C.c_double), ("eta_tries", C.c_int), ("bound", C.c_double),
                 ("releig_bound", C.c_double), ("lambda_star", C.c_double), ("omega", C.c_double),
                 ("eta_in", C.c_double), ("delta_A", C.c_double), ("converged", C.c_int),
-                ("max_rank", C.c_int), ("flops", C.c_double)]
+                ("max_rank", C.c_int), ("flops", C.c_double), ("cap_discarded", C.c_double)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -356,8 +356,8 @@ def dot(ctx, a, b, mpo=None, shift=0.0):
     return out.value
 
 
-def solver_params(c, delta, eps_num=None, t_eig=0.5, tau=1e-8):
-    return SolverParams(c, delta, 0.5 * (1.0 - c) if eps_num is None else eps_num, t_eig, tau)
+def solver_params(c, delta, eps_num=None, t_eig=0.5, tau=1e-8, r_max=0, u_rel=1e-13):
+    return SolverParams(c, delta, 0.5 * (1.0 - c) if eps_num is None else eps_num, t_eig, tau, r_max, u_rel)
 
 
 def solver_state():
