@@ -3,20 +3,26 @@
 
 One step = one pass of Alg. 2 (Rayleigh quotient, exact MPO applies of the
 preconditioned terms, error-controlled residual sum with rank truncations,
-2x2 Rayleigh-Ritz, truncation of the update) on a seeded random iterate of
-the open Hubbard chain L = 32 (64 spin-orbital sites), half filling, t = 1,
-U = 4, maximal rank 256, FP64.
+2x2 Rayleigh-Ritz, truncation of the update) on the open Hubbard chain
+L = 32 (64 spin-orbital sites), half filling, t = 1, U = 4, maximal rank 256,
+FP64, started from e_1 (the paper's initial value, Sec. 7.1.4).  The W
+warm-up steps and the K timed steps are steps 0..W-1 and W..W+K-1 of that
+trajectory; the oracle arm times the identical steps.
 
-value: algorithmic FP64 TFLOP/s of the whole step (flops counted by the
+value: algorithmic FP64 TFLOP/s of the timed steps (flops counted by the
 library from the block index: grouped GEMMs 2mnk, Householder QR, nominal
 Jacobi SVD, exact MPO application 2 per written element) / device time.
 Usage (contract): python bench.py --gpus N --steps K --warmup W [--impl reference]
 """
 
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")   # the oracle baseline runs on one host core
+
 import argparse
 import json
 import math
-import os
 import subprocess
 import sys
 import time
@@ -27,7 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MPO·MPS apply TFLOP/s (% roofline); time to 1e-8 Eh, mixed+learned vs FP64"
-WORKLOAD = "hubbard_chain L=32 (K=64 spin-orbital sites), n_up=n_dn=16, t=1, U=4, r_max=256, FP64"
+WORKLOAD = ("hubbard_chain L=32 (K=64 spin-orbital sites), n_up=n_dn=16, t=1, U=4, r_max=256, FP64, "
+            "Alg. 2 trajectory from e_1")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -50,8 +57,11 @@ def setup(ctx, nat, seed, L=32, r_max=256):
     p = nat.make_precond(th, tmin, tmax, prm["c0"], prm["alpha0"])
     sp = nat.solver_params(prm["c"], prm["delta"], eps_num=prm["eps_num"], t_eig=prm["t_eig"], tau=1e-8,
                            r_max=r_max)
-    nval = nat.mps_random_size(L, 1, n, n, r_max)
-    x = nat.mps_create(ctx, L, 1, n, n, r_max, random_block_values(nval, seed))
+    if seed is None:
+        x = nat.mps_create(ctx, L, 1, n, n)                    # e_1
+    else:
+        nval = nat.mps_random_size(L, 1, n, n, r_max)
+        x = nat.mps_create(ctx, L, 1, n, n, r_max, random_block_values(nval, seed))
     return dict(wl=wl, W=W, p=p, sp=sp, x=x, gamma=gamma, theta=th, tmin=tmin, tmax=tmax, prm=prm)
 
 
@@ -131,85 +141,79 @@ def fp64_gemm_peak(torch, dev):
     return best
 
 
-def cpu_baseline(x_vals_seed=1000, L=32, r_max=256, budget_s=25.0):
-    """The oracle (as it stands) on a bounded sample of the same workload: one
-    exact MPO application to the random iterate followed by trunc_eps, i.e.
-    the apply-and-round unit of the residual; flops are the library's
-    algorithmic count for the identical operation."""
+def oracle_steps(n_steps, L=32, r_max=256):
+    """The oracle (as it stands) on the same trajectory: per-step wall times."""
     from oracle import bsmps as OB
     from oracle import fermion as OF
     from oracle import mpo as OM
+    from oracle import pinvit as OPI
+    from oracle import precond as OP
     from paper_2604_16118_gb300 import problem
-    from synth import hubbard_chain, random_block_values
+    from synth import hubbard_chain
+    prm = load_params(L)
     wl = hubbard_chain(L=L, r_max=r_max)
     n = L // 2
     gamma = problem.hubbard_shift(wl.h, n, n, margin=1.0)
-    species = OF.site_species(L, 1)
-    t0 = time.perf_counter()
     W = OM.build_mpo(wl.h, wl.eri, 1, 2 * n, gamma)
-    dims = OB.default_dims(species, (n, n), r_max)
-    tot = OB.BSMPS(species, (n, n), dims, [dict() for _ in species]).layout()[1]
-    x = OB.BSMPS.from_flat(species, (n, n), dims, random_block_values(tot, x_vals_seed))
-    t_setup = time.perf_counter() - t0
-    reps = 0
-    t1 = time.perf_counter()
-    while True:
-        y = OB.apply_exact(W, x, shift=-1.0)
-        nrm = math.sqrt(OB.dot(x, x))
-        OB.truncate(y, 1e-6 * nrm)
-        reps += 1
-        if time.perf_counter() - t1 > budget_s or reps >= 3:
-            break
-    dt = (time.perf_counter() - t1) / reps
-    return dt, reps, t_setup, nrm
+    t_so, v_so = OP.spin_orbital_accessors(wl.h, wl.eri, 1)
+    species = OF.site_species(L, 1)
+    th = OP.theta_diag(t_so, v_so, 2 * n, gamma, 2 * L)
+    tmin, tmax = OP.spectrum_bounds(th, species, (n, n))
+    prec = OP.Preconditioner(th, tmin, tmax, prm["c0"], prm["alpha0"])
+    params = OPI.SolverParams(prm["c"], prm["delta"], eps_num=prm["eps_num"], t_eig=prm["t_eig"], tau=1e-8,
+                              r_max=r_max)
+    st = OPI.SolverState()
+    x = OB.e1_mps(species, (n, n))
+    times, energies = [], []
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        x, info = OPI.step(x, W, prec, params, st)
+        times.append(time.perf_counter() - t0)
+        energies.append(info["lambda"] - gamma)
+    return times, energies
 
 
-def gpu_apply_round_flops(nat, ctx, L=32, r_max=256, seed=1000):
-    from paper_2604_16118_gb300 import problem
-    from synth import hubbard_chain, random_block_values
-    wl = hubbard_chain(L=L, r_max=r_max)
-    n = L // 2
-    gamma = problem.hubbard_shift(wl.h, n, n, margin=1.0)
-    W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, 1, 2 * n, gamma)
-    nval = nat.mps_random_size(L, 1, n, n, r_max)
-    x = nat.mps_create(ctx, L, 1, n, n, r_max, random_block_values(nval, seed))
-    nrm = math.sqrt(nat.dot(ctx, x, x))
-    _, fl = nat.apply_H(ctx, W, x, shift=-1.0, tol=1e-6 * nrm)
-    return fl
+def gpu_step_flops(nat, ctx, n_steps):
+    """Algorithmic flops of steps 0..n_steps-1 from e_1, counted by the library."""
+    S = setup(ctx, nat, seed=None)
+    st = nat.solver_state()
+    x = S["x"]
+    out = []
+    for _ in range(n_steps):
+        x, info = nat.eigensolve_step(ctx, S["W"], S["p"], S["sp"], st, x)
+        out.append(info["flops"])
+    return out
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    steps = []
+    n = args.warmup + args.steps
+    times, energies = oracle_steps(n)
+    tm = times[args.warmup:]
     flops = None
-    for _ in range(args.warmup + args.steps):
-        dt, reps, _, _ = cpu_baseline(budget_s=max(5.0, 60.0 / max(1, args.warmup + args.steps)))
-        steps.append(dt)
-    tm = steps[args.warmup:]
-    # flops of the sampled unit: the same algorithmic count the library reports
+    note = None
     try:
-        import torch  # noqa: F401
         from paper_2604_16118_gb300 import build, native as nat
         build.build()
         ctx = nat.Context(0)
-        flops = gpu_apply_round_flops(nat, ctx)
-    except Exception as e:  # no GPU: count from the oracle-independent formula is unavailable
-        flops = None
-        err = str(e)
+        flops = gpu_step_flops(nat, ctx, n)[args.warmup:]
+    except Exception as e:
+        note = "flop count needs the library on a GPU: " + str(e).splitlines()[0]
     ms = 1e3 * float(np.mean(tm))
-    val = (flops / (ms * 1e-3) / 1e12) if flops else None
+    val = (sum(flops) / sum(tm) / 1e12) if flops else None
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle sample: one exact apply + trunc_eps per step)"},
+            "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": "one exact MPO apply of the random r=256 iterate + trunc_eps(1e-6 ||x||) "
-                                       "per step (numpy, single process)"},
-            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    if flops is None:
-        line["note"] = "flop count needs the library on a GPU: " + err
+                             "sample": f"the identical Alg. 2 steps {args.warmup}..{n - 1} from e_1 "
+                                       "(numpy FP64 oracle, BLAS on 1 thread)"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "energy": energies[-1]}
+    if note:
+        line["note"] = note
     print(json.dumps(line))
     return 0
 
@@ -242,7 +246,7 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     ctx = nat.Context(local, stream.cuda_stream)
-    S = setup(ctx, nat, seed=1000 + rank)
+    S = setup(ctx, nat, seed=None)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     st = nat.solver_state()
     x = S["x"]
@@ -253,6 +257,7 @@ def main():
     for _ in range(args.warmup):
         x, _ = one_step(x)
     ctx.sync()
+    x_after_warmup = (x.export(), x.bonds(), st.eta_res, st.n)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -296,10 +301,10 @@ def main():
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     name, (nl, kms, kfl, kby) = dom
 
-    # end to end through the C ABI with host buffers
-    e2e_steps = max(1, min(args.steps, 2))
-    hx = x.export()
-    bonds = x.bonds()
+    # end to end through the C ABI with host buffers: the same K steps again from
+    # the post-warm-up iterate, uploaded from and read back to pinned host memory
+    e2e_steps = args.steps
+    hx, bonds, st.eta_res, st.n = x_after_warmup
     pinned = torch.empty(len(hx), dtype=torch.float64).pin_memory()
     pinned.numpy()[:] = hx
     h2d = d2h = 0
@@ -346,11 +351,14 @@ def main():
     if r["achieved"] is not None and r["peak"]:
         r["frac"] = r["achieved"] / r["peak"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, reps, _, _ = cpu_baseline()
-        fl = gpu_apply_round_flops(nat, ctx)
-        out["cpu_baseline"] = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                               "sample": f"one exact MPO apply + trunc_eps(1e-6 ||x||) of the random r=256 "
-                                         f"iterate, {reps} rep(s), {dt:.2f} s each (numpy, 1 process)"}
+        n = args.warmup + args.steps
+        times, energies = oracle_steps(n)
+        tm = times[args.warmup:]
+        out["cpu_baseline"] = {"value": total_flops / sum(tm) / 1e12, "unit": "TFLOP/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"the identical Alg. 2 steps {args.warmup}..{n - 1} from e_1 "
+                                         f"({sum(tm):.2f} s; numpy FP64 oracle, BLAS on 1 thread)",
+                               "energy_match": abs(energies[-1] - out["energy"])}
     if rank == 0:
         print(json.dumps(out))
     if dist:
