@@ -267,6 +267,25 @@ BSMPS_API bsmps_status bsmps_precondition(bsmps_ctx ctx, const bsmps_precond* p,
 BSMPS_API bsmps_status bsmps_dot(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, double shift,
                        double* out);
 
+/* Same result as bsmps_dot, computed without allocating device memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc (or any allocating routine) at the time they need an inner
+ * product -- for example code running under a device-memory budget enforced by
+ * another framework's allocator, or latency-critical loops that must not
+ * trigger an allocation.  a, b (and W) are ordinary handles created earlier.
+ * All temporaries (environment blocks, intermediate products, kernel task
+ * lists) live in one 32 MiB file-scope device array that every device which
+ * loads the library holds until the process exits.  The first call on a device
+ * resolves the array's device address (cudaGetSymbolAddress with that device
+ * current); make that first call before any stream capture.  Contractions
+ * whose temporaries do not fit the 32 MiB return BSMPS_ERR_RANK_CAP with the
+ * required size in bsmps_last_error.  Every call reuses the same array, so
+ * calls that overlap on the GPU (several streams or host threads at once)
+ * race and must be serialised by the caller.  Synchronises the context stream.
+ * Errors: INVALID_ARG, RANK_CAP, CUDA. */
+BSMPS_API bsmps_status bsmps_dot_noalloc(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W,
+                                         double shift, double* out);
+
 /* One pass of the loop body of Alg. 2 on x^n = *x:
  * lambda^n (Eq. (exactrq)), normalisation in the A-norm, the residual
  * res_eta from the terms S_k (H_gamma - lambda) S_k' x (Sec. 5.3.1, eta_res

@@ -436,6 +436,15 @@ bsmps_status bsmps_dot(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, dou
     });
 }
 
+bsmps_status bsmps_dot_noalloc(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, double shift,
+                               double* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(out, BSMPS_ERR_INVALID_ARG, "null out");
+        *out = bsm::op_dot_noalloc(c, M(a), M(b), W ? &W->W : nullptr, shift);
+    });
+}
+
 bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
                                    const bsmps_solver_params* params, bsmps_solver_state* state, bsmps_mps* x,
                                    bsmps_step_info* info) {

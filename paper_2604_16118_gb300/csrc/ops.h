@@ -55,6 +55,9 @@ struct EnvProblem {
 };
 std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs);
 
+// <a, O b> with every temporary in a fixed file-scope device array (no allocation).
+double op_dot_noalloc(Context* ctx, const Mps* a, const Mps* b, const Mpo* W, double shift);
+
 // Frobenius norm of core 0 (the norm of a right-orthogonalised MPS).
 double op_core0_norm(Context* ctx, const Mps* x);
 

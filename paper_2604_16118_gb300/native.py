@@ -88,6 +88,7 @@ _SIGS = {
     "bsmps_scale_sites": (_i, [_vp, _vp, _pd, _pd, C.POINTER(_vp)]),
     "bsmps_precondition": (_i, [_vp, C.POINTER(Precond), _i, _vp, C.POINTER(_vp), _pi]),
     "bsmps_dot": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
+    "bsmps_dot_noalloc": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
     "bsmps_eigensolve_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
                                    C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(StepInfo)]),
 }
@@ -353,6 +354,14 @@ def precondition(ctx, p, x, term=-1):
 def dot(ctx, a, b, mpo=None, shift=0.0):
     out = C.c_double()
     _check(ctx, lib().bsmps_dot(ctx.h, a.h, b.h, mpo.h if mpo is not None else None, shift, C.byref(out)))
+    return out.value
+
+
+def dot_noalloc(ctx, a, b, mpo=None, shift=0.0):
+    """bsmps_dot without device allocation (fixed 32 MiB scratch, see include/bsmps.h)."""
+    out = C.c_double()
+    _check(ctx, lib().bsmps_dot_noalloc(ctx.h, a.h, b.h, mpo.h if mpo is not None else None, shift,
+                                        C.byref(out)))
     return out.value
 
 
