@@ -4,36 +4,18 @@
 #include <cfloat>
 #include <cmath>
 
+#include "dense_dev.cuh"
 #include "kernels.h"
 
 namespace bsm {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+using dev::block_sum;
+using dev::kThreads;
+using dev::kWarps;
+using dev::warp_sum;
+
 constexpr int64_t kCopyChunk = 16384;
-
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// sum over the block; every thread gets the result
-__device__ double block_sum(double v, double* red) {
-    v = warp_sum(v);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < 32) {
-        t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        t = warp_sum(t);
-        if (threadIdx.x == 0) red[32] = t;
-    }
-    __syncthreads();
-    return red[32];
-}
 
 struct CopyChunk {
     int task;
@@ -124,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmOut* __restrict__ o
 __global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ tasks) {
     extern __shared__ double sm[];
     __shared__ double red[33];
-    __shared__ double s_tau, s_scale;
+    __shared__ double sh[2];
     const QrTask tk = tasks[blockIdx.x];
     const int M = tk.M, N = tk.N, k = M < N ? M : N;
     double* A = tk.smem ? sm : tk.A;
@@ -135,70 +117,13 @@ __global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ task
         for (int64_t e = threadIdx.x; e < (int64_t)M * N; e += kThreads) A[e] = tk.A[e];
         __syncthreads();
     }
-    for (int j = 0; j < k; ++j) {
-        double s = 0.0;
-        for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) {
-            const double v = A[(int64_t)j * M + i];
-            s += v * v;
-        }
-        s = block_sum(s, red);
-        if (threadIdx.x == 0) {
-            const double alpha = A[(int64_t)j * M + j];
-            if (s == 0.0) {
-                s_tau = 0.0;
-                s_scale = 0.0;
-            } else {
-                const double nrm = sqrt(alpha * alpha + s);
-                const double beta = alpha >= 0.0 ? -nrm : nrm;
-                s_tau = (beta - alpha) / beta;
-                s_scale = 1.0 / (alpha - beta);
-                A[(int64_t)j * M + j] = beta;
-            }
-            tau[j] = s_tau;
-        }
-        __syncthreads();
-        const double tj = s_tau, scale = s_scale;
-        if (tj != 0.0) {
-            for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) A[(int64_t)j * M + i] *= scale;
-            __syncthreads();
-            for (int c = j + 1 + warp; c < N; c += kWarps) {
-                // read A(j, c) before the warp-synchronous reduction: lane 0 rewrites it after
-                const double a_jc = A[(int64_t)c * M + j];
-                double w = 0.0;
-                for (int i = j + 1 + lane; i < M; i += 32) w += A[(int64_t)j * M + i] * A[(int64_t)c * M + i];
-                w = warp_sum(w) + a_jc;
-                const double tw = tj * w;
-                if (lane == 0) A[(int64_t)c * M + j] -= tw;
-                for (int i = j + 1 + lane; i < M; i += 32) A[(int64_t)c * M + i] -= tw * A[(int64_t)j * M + i];
-            }
-        }
-        __syncthreads();
-    }
+    dev::householder(A, tau, M, N, red, sh);
     // R (k x N row-major) from the upper trapezoid
     for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += kThreads) {
         const int r = (int)(e / N), c = (int)(e % N);
         tk.R[e] = c >= r ? A[(int64_t)c * M + r] : 0.0;
     }
-    // Q = H_0 ... H_{k-1} applied to the first k columns of I (backward accumulation)
-    for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += kThreads) {
-        const int i = (int)(e % M), c = (int)(e / M);
-        Q[e] = i == c ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    for (int j = k - 1; j >= 0; --j) {
-        const double tj = tau[j];
-        if (tj == 0.0) continue;
-        for (int c = j + warp; c < k; c += kWarps) {
-            const double q_jc = Q[(int64_t)c * M + j];
-            double w = 0.0;
-            for (int i = j + 1 + lane; i < M; i += 32) w += A[(int64_t)j * M + i] * Q[(int64_t)c * M + i];
-            w = warp_sum(w) + q_jc;
-            const double tw = tj * w;
-            if (lane == 0) Q[(int64_t)c * M + j] -= tw;
-            for (int i = j + 1 + lane; i < M; i += 32) Q[(int64_t)c * M + i] -= tw * A[(int64_t)j * M + i];
-        }
-        __syncthreads();
-    }
+    dev::form_q(A, tau, Q, M, k);
     // diag(R) >= 0 (R is in global memory; every thread sees the final R after the barrier)
     for (int j = warp; j < k; j += kWarps) {
         const double rjj = A[(int64_t)j * M + j];
@@ -213,11 +138,6 @@ __global__ void __launch_bounds__(kThreads) k_qr(const QrTask* __restrict__ task
     }
 }
 
-__device__ __forceinline__ int rr_player(int pos, int round, int n2) {
-    return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1;
-}
-
-constexpr int kMaxSweeps = 40;
 constexpr int kSmemJacobiMax = 110;   // 2 k^2 doubles <= 193 KB of shared memory
 
 // One-sided Jacobi task on a k x k matrix G (column-major, overwritten by the
@@ -230,11 +150,7 @@ struct JacTask {
     int smem;        // 1: iterate in shared memory
 };
 
-// One-sided (Hestenes) Jacobi, parallel round-robin pair order, one CTA per
-// matrix.  Rotation: zeta = (b - a)/(2 g), t = sign(zeta)/(|zeta| +
-// sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t.  A pair is rotated while
-// |g| > k eps sqrt(a b) and both columns are above the numerical-zero level
-// (k eps ||G||_F); a sweep without rotations ends the iteration.
+// One-sided Jacobi (dev::jacobi), one CTA per matrix, in shared memory when k <= kSmemJacobiMax.
 __global__ void __launch_bounds__(kThreads) k_jacobi(const JacTask* __restrict__ tasks) {
     extern __shared__ double sm[];
     __shared__ double red[33];
@@ -243,70 +159,11 @@ __global__ void __launch_bounds__(kThreads) k_jacobi(const JacTask* __restrict__
     const int k = tk.k;
     double* G = tk.smem ? sm : tk.G;
     double* V = tk.smem ? sm + (int64_t)k * k : tk.V;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double f = 0.0;
-    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += kThreads) {
-        const double v = tk.G[e];
-        if (tk.smem) G[e] = v;
-        f += v * v;
-        V[e] = (e % k) == (e / k) ? 1.0 : 0.0;
-    }
-    f = block_sum(f, red);
-    const double tol = (double)k * DBL_EPSILON;
-    const double tiny2 = tol * tol * f;
-    const int n2 = k + (k & 1);
-    for (int sweep = 0; sweep < kMaxSweeps && k > 1; ++sweep) {
-        if (threadIdx.x == 0) s_rot = 0;
+    if (tk.smem) {
+        for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += kThreads) G[e] = tk.G[e];
         __syncthreads();
-        for (int round = 0; round < n2 - 1; ++round) {
-            for (int pi = warp; pi < n2 / 2; pi += kWarps) {
-                int p = rr_player(pi, round, n2), q = rr_player(n2 - 1 - pi, round, n2);
-                if (p >= k || q >= k) continue;
-                if (p > q) {
-                    const int tmp = p;
-                    p = q;
-                    q = tmp;
-                }
-                double a = 0.0, b = 0.0, g = 0.0;
-                for (int i = lane; i < k; i += 32) {
-                    const double xp = G[(int64_t)p * k + i], xq = G[(int64_t)q * k + i];
-                    a += xp * xp;
-                    b += xq * xq;
-                    g += xp * xq;
-                }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                g = warp_sum(g);
-                if (g != 0.0 && fabs(g) > tol * sqrt(a * b) && fmin(a, b) > tiny2) {
-                    const double zeta = (b - a) / (2.0 * g);
-                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    for (int i = lane; i < k; i += 32) {
-                        const double xp = G[(int64_t)p * k + i], xq = G[(int64_t)q * k + i];
-                        G[(int64_t)p * k + i] = c * xp - s * xq;
-                        G[(int64_t)q * k + i] = s * xp + c * xq;
-                        const double vp = V[(int64_t)p * k + i], vq = V[(int64_t)q * k + i];
-                        V[(int64_t)p * k + i] = c * vp - s * vq;
-                        V[(int64_t)q * k + i] = s * vp + c * vq;
-                    }
-                    if (lane == 0) s_rot = 1;
-                }
-            }
-            __syncthreads();
-        }
-        const int rot = s_rot;
-        __syncthreads();
-        if (!rot) break;
     }
-    for (int j = warp; j < k; j += kWarps) {
-        double a = 0.0;
-        for (int i = lane; i < k; i += 32) {
-            const double x = G[(int64_t)j * k + i];
-            a += x * x;
-        }
-        a = warp_sum(a);
-        if (lane == 0) tk.Sraw[j] = sqrt(a);
-    }
+    dev::jacobi(G, V, tk.Sraw, k, red, &s_rot);
     if (tk.smem) {
         for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += kThreads) {
             tk.G[e] = G[e];
@@ -332,61 +189,7 @@ struct SvdFin {
 
 __global__ void __launch_bounds__(kThreads) k_svd_finalize(const SvdFin* __restrict__ tasks) {
     const SvdFin tk = tasks[blockIdx.x];
-    const int k = tk.k, len = tk.len;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < k; i += kThreads) {
-        const double si = tk.Sraw[i];
-        int rank = 0;
-        for (int j = 0; j < k; ++j) {
-            const double sj = tk.Sraw[j];
-            rank += (sj > si || (sj == si && j < i)) ? 1 : 0;
-        }
-        tk.perm[rank] = i;
-    }
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)tk.M * k; e += kThreads) {
-        const int i = (int)(e / k), r = (int)(e % k);
-        const int p = tk.perm[r];
-        tk.US[e] = tk.wide ? tk.G[(int64_t)p * k + i] : tk.Sraw[p] * tk.QVt[(int64_t)p * len + i];
-    }
-    for (int64_t e = threadIdx.x; e < (int64_t)k * tk.N; e += kThreads) {
-        const int r = (int)(e / tk.N), c = (int)(e % tk.N);
-        const int p = tk.perm[r];
-        double v;
-        if (tk.wide) {
-            v = tk.QVt[(int64_t)p * len + c];
-        } else {
-            const double sp = tk.Sraw[p];
-            v = sp > 0.0 ? tk.G[(int64_t)p * k + c] / sp : 0.0;
-        }
-        tk.Vt[e] = v;
-    }
-    for (int r = threadIdx.x; r < k; r += kThreads) tk.S[r] = tk.Sraw[tk.perm[r]];
-    __syncthreads();
-    // sign: the largest |entry| of every row of Vt is positive
-    for (int r = warp; r < k; r += kWarps) {
-        double best = -1.0;
-        int bi = 0;
-        for (int c = lane; c < tk.N; c += 32) {
-            const double a = fabs(tk.Vt[(int64_t)r * tk.N + c]);
-            if (a > best) {
-                best = a;
-                bi = c;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        if (tk.Vt[(int64_t)r * tk.N + bi] < 0.0) {
-            for (int c = lane; c < tk.N; c += 32) tk.Vt[(int64_t)r * tk.N + c] = -tk.Vt[(int64_t)r * tk.N + c];
-            for (int i = lane; i < tk.M; i += 32) tk.US[(int64_t)i * k + r] = -tk.US[(int64_t)i * k + r];
-        }
-    }
+    dev::svd_assemble(tk.G, tk.QVt, tk.Sraw, tk.perm, tk.S, tk.US, tk.Vt, tk.M, tk.N, tk.k, tk.len, tk.wide);
 }
 
 __global__ void __launch_bounds__(kThreads) k_sumsq(const double* const* __restrict__ xs,

@@ -73,3 +73,69 @@ void launch_sumsq(Context* ctx, const std::vector<const double*>& xs, const std:
                   double* out_dev);
 
 }  // namespace bsm
+
+namespace bsm {
+
+// ---- fused per-site kernels of the truncation sweeps (csrc/sweep.cu) ----
+
+// Left sweep, one CTA per right sector m of bond t+1: gather the blocks of
+// core t that end in m (rows stacked in layout order, r0 = row offset) into
+// M x N, Householder QR (diag R >= 0), write Q's rows into the new core-t
+// blocks (rows x k) and R X into the new core-(t+1) blocks (k x cols).
+struct LeftSrc {
+    const double* src;
+    double* dst;
+    int rows, r0;
+};
+struct LeftX {
+    const double* X;
+    double* dst;
+    int cols;
+};
+struct LeftTask {
+    int M, N, k;
+    int s_beg, s_end, x_beg, x_end;
+};
+bool left_site_fits(int M, int N, int64_t rx_fma);
+void launch_left_site(Context* ctx, const std::vector<LeftTask>& tasks, const std::vector<LeftSrc>& srcs,
+                      const std::vector<LeftX>& xs);
+
+// Right sweep, one CTA per left sector n of bond t: gather [X_t(n,0) | X_t(n,1)]
+// (parts at column offsets), QR of it (tall) or of its transpose (wide), one-sided
+// Jacobi on the triangular factor, and the assembled S, U S, V^T (as SvdTask).
+struct SvdPart {
+    const double* src;
+    int cols, coff;
+};
+struct SvdSiteTask {
+    int M, N, k, len, wide;
+    int p_beg, p_end;
+    double* S;
+    double* US;
+    double* Vt;
+};
+bool svd_site_fits(int M, int N);
+void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const std::vector<SvdPart>& parts);
+
+// After the cut of bond t, one CTA per kept sector n: copy the kept V^T rows into
+// the new core-t blocks and multiply the core-(t-1) blocks ending in n by the
+// kept columns of U S (rows x K times K x keep, US row stride ldus).
+struct RCopy {
+    const double* src;
+    double* dst;
+    int rows, cols, src_ld;
+};
+struct RGemm {
+    const double* X;
+    const double* US;
+    double* dst;
+    int rows, K, keep, ldus;
+};
+struct RTask {
+    int c_beg, c_end, g_beg, g_end;
+};
+constexpr int64_t kFusedGemmMaxFma = 1 << 17;
+void launch_right_apply(Context* ctx, const std::vector<RTask>& tasks, const std::vector<RCopy>& copies,
+                        const std::vector<RGemm>& gemms);
+
+}  // namespace bsm

@@ -302,65 +302,102 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             stack[bk.ri].push_back({bi, Mrows[bk.ri]});
             Mrows[bk.ri] += bk.rows;
         }
-        std::vector<double*> Am(nm, nullptr), Qm(nm, nullptr), Rm(nm, nullptr);
-        std::vector<CopyTask> gather;
-        std::vector<QrTask> qr;
-        for (int mi = 0; mi < nm; ++mi) {
-            const int M = Mrows[mi], N = bm.dim[mi];
-            if (M == 0) continue;
-            const int k = std::min(M, N);
-            krank[mi] = k;
-            Am[mi] = s.dbl((size_t)M * N);
-            Qm[mi] = s.dbl((size_t)M * k);
-            Rm[mi] = s.dbl((size_t)k * N);
-            double* tau = s.dbl((size_t)k);
-            for (auto& pr : stack[mi]) {
-                const Block& bk = L.blocks[t][pr.first];
-                gather.push_back({cores[t] + bk.off, Am[mi] + pr.second, bk.rows, bk.cols, bk.cols, M,
-                                  0, 1, 0, 1.0});
-            }
-            qr.push_back({Am[mi], Qm[mi], Rm[mi], tau, M, N});
-        }
-        launch_copy(ctx, gather);
-        launch_qr(ctx, qr);
         Layout Ln = L;
         {
             Bond nb;
-            for (int mi = 0; mi < nm; ++mi)
+            for (int mi = 0; mi < nm; ++mi) {
+                if (Mrows[mi] > 0) krank[mi] = std::min(Mrows[mi], bm.dim[mi]);
                 if (krank[mi] > 0) {
                     nb.q.push_back(bm.q[mi]);
                     nb.dim.push_back(krank[mi]);
                 }
+            }
             Ln.bonds[t + 1] = nb;
             rebuild_site(Ln, t);
             rebuild_site(Ln, t + 1);
         }
         double* nt = alloc_core(Ln.core_size[t]);
         double* nt1 = alloc_core(Ln.core_size[t + 1]);
-        std::vector<CopyTask> qcopy;
-        for (const Block& nbk : Ln.blocks[t]) {
-            const int mi = bm.find(Ln.bonds[t + 1].q[nbk.ri]);
-            // row offset of this (li, sigma) block in the old stack
-            int r0 = -1;
-            for (auto& pr : stack[mi]) {
-                const Block& ob = L.blocks[t][pr.first];
-                if (ob.li == nbk.li && ob.sigma == nbk.sigma) r0 = pr.second;
-            }
-            qcopy.push_back({Qm[mi] + r0, nt + nbk.off, nbk.rows, nbk.cols, Mrows[mi], nbk.cols, 1, 0, 0,
-                             1.0});
-        }
-        launch_copy(ctx, qcopy);
-        std::vector<GemmOut> outs;
-        std::vector<GemmIn> ins;
         const std::vector<int> oldlook = block_lookup(L, t + 1);
-        for (const Block& nbk : Ln.blocks[t + 1]) {
-            const int mi = bm.find(Ln.bonds[t + 1].q[nbk.li]);
-            const Block& ob = L.blocks[t + 1][oldlook[mi * 2 + nbk.sigma]];
-            outs.push_back({nt1 + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
-                            (int)ins.size() + 1, 0.0});
-            ins.push_back({Rm[mi], cores[t + 1] + ob.off, ob.rows, bm.dim[mi], ob.cols, 0, 1.0});
+        const std::vector<int> newlook_t = block_lookup(Ln, t);
+        // fused path: one CTA per sector does gather, QR, Q scatter and R X
+        bool fused = true;
+        for (int mi = 0; mi < nm && fused; ++mi) {
+            if (Mrows[mi] == 0) continue;
+            int64_t rx = 0;
+            for (int sg = 0; sg < 2; ++sg) {
+                const int ob = oldlook[mi * 2 + sg];
+                if (ob >= 0) rx += (int64_t)krank[mi] * bm.dim[mi] * L.blocks[t + 1][ob].cols;
+            }
+            fused = left_site_fits(Mrows[mi], bm.dim[mi], rx);
         }
-        launch_gemm(ctx, outs, ins);
+        if (fused) {
+            std::vector<LeftTask> lt;
+            std::vector<LeftSrc> ls;
+            std::vector<LeftX> lx;
+            for (int mi = 0; mi < nm; ++mi) {
+                if (Mrows[mi] == 0) continue;
+                const int nmi = Ln.bonds[t + 1].find(bm.q[mi]);
+                LeftTask task{Mrows[mi], bm.dim[mi], krank[mi], (int)ls.size(), 0, (int)lx.size(), 0};
+                for (auto& pr : stack[mi]) {
+                    const Block& ob = L.blocks[t][pr.first];
+                    const Block& nbk = Ln.blocks[t][newlook_t[ob.li * 2 + ob.sigma]];
+                    ls.push_back({cores[t] + ob.off, nt + nbk.off, ob.rows, pr.second});
+                }
+                task.s_end = (int)ls.size();
+                for (const Block& nbk : Ln.blocks[t + 1]) {
+                    if (nbk.li != nmi) continue;
+                    const Block& ob = L.blocks[t + 1][oldlook[mi * 2 + nbk.sigma]];
+                    lx.push_back({cores[t + 1] + ob.off, nt1 + nbk.off, ob.cols});
+                }
+                task.x_end = (int)lx.size();
+                lt.push_back(task);
+            }
+            launch_left_site(ctx, lt, ls, lx);
+        } else {
+            std::vector<double*> Am(nm, nullptr), Qm(nm, nullptr), Rm(nm, nullptr);
+            std::vector<CopyTask> gather;
+            std::vector<QrTask> qr;
+            for (int mi = 0; mi < nm; ++mi) {
+                const int M = Mrows[mi], N = bm.dim[mi];
+                if (M == 0) continue;
+                const int k = krank[mi];
+                Am[mi] = s.dbl((size_t)M * N);
+                Qm[mi] = s.dbl((size_t)M * k);
+                Rm[mi] = s.dbl((size_t)k * N);
+                double* tau = s.dbl((size_t)k);
+                for (auto& pr : stack[mi]) {
+                    const Block& bk = L.blocks[t][pr.first];
+                    gather.push_back({cores[t] + bk.off, Am[mi] + pr.second, bk.rows, bk.cols, bk.cols, M,
+                                      0, 1, 0, 1.0});
+                }
+                qr.push_back({Am[mi], Qm[mi], Rm[mi], tau, M, N});
+            }
+            launch_copy(ctx, gather);
+            launch_qr(ctx, qr);
+            std::vector<CopyTask> qcopy;
+            for (const Block& nbk : Ln.blocks[t]) {
+                const int mi = bm.find(Ln.bonds[t + 1].q[nbk.ri]);
+                int r0 = -1;
+                for (auto& pr : stack[mi]) {
+                    const Block& ob = L.blocks[t][pr.first];
+                    if (ob.li == nbk.li && ob.sigma == nbk.sigma) r0 = pr.second;
+                }
+                qcopy.push_back({Qm[mi] + r0, nt + nbk.off, nbk.rows, nbk.cols, Mrows[mi], nbk.cols, 1, 0, 0,
+                                 1.0});
+            }
+            launch_copy(ctx, qcopy);
+            std::vector<GemmOut> outs;
+            std::vector<GemmIn> ins;
+            for (const Block& nbk : Ln.blocks[t + 1]) {
+                const int mi = bm.find(Ln.bonds[t + 1].q[nbk.li]);
+                const Block& ob = L.blocks[t + 1][oldlook[mi * 2 + nbk.sigma]];
+                outs.push_back({nt1 + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
+                                (int)ins.size() + 1, 0.0});
+                ins.push_back({Rm[mi], cores[t + 1] + ob.off, ob.rows, bm.dim[mi], ob.cols, 0, 1.0});
+            }
+            launch_gemm(ctx, outs, ins);
+        }
         release(t);
         release(t + 1);
         cores[t] = nt;
@@ -398,31 +435,56 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             stot += kk[ni];
         }
         double* S_all = s.dbl((size_t)std::max<int64_t>(stot, 1));
-        std::vector<CopyTask> gather;
-        std::vector<SvdTask> svd;
-        for (int ni = 0; ni < nn; ++ni) {
-            if (kk[ni] == 0) continue;
-            const int M = bn.dim[ni], N = c0[ni] + c1[ni], k = kk[ni];
-            const int wide = M < N ? 1 : 0;
-            double* G = s.dbl((size_t)M * N);
-            double* V = s.dbl((size_t)k * k);
-            US[ni] = s.dbl((size_t)M * k);
-            Vt[ni] = s.dbl((size_t)k * N);
-            for (int part = 0; part < 2; ++part) {
-                const int bi = part == 0 ? b0[ni] : b1[ni];
-                if (bi < 0) continue;
-                const Block& bk = L.blocks[t][bi];
-                const int coff = part == 0 ? 0 : c0[ni];
-                if (wide)
-                    gather.push_back({cores[t] + bk.off, G + coff, bk.rows, bk.cols, bk.cols, N, 0, 0, 0, 1.0});
-                else
-                    gather.push_back({cores[t] + bk.off, G + (int64_t)coff * M, bk.rows, bk.cols, bk.cols, M,
-                                      0, 1, 0, 1.0});
+        bool fused = true;
+        for (int ni = 0; ni < nn && fused; ++ni)
+            if (kk[ni] > 0) fused = svd_site_fits(bn.dim[ni], c0[ni] + c1[ni]);
+        if (fused) {
+            std::vector<SvdSiteTask> st;
+            std::vector<SvdPart> parts;
+            for (int ni = 0; ni < nn; ++ni) {
+                if (kk[ni] == 0) continue;
+                const int M = bn.dim[ni], N = c0[ni] + c1[ni], k = kk[ni];
+                US[ni] = s.dbl((size_t)M * k);
+                Vt[ni] = s.dbl((size_t)k * N);
+                SvdSiteTask task{M, N, k, std::max(M, N), M < N ? 1 : 0, (int)parts.size(), 0, S_all + soff[ni],
+                                 US[ni], Vt[ni]};
+                for (int part = 0; part < 2; ++part) {
+                    const int bi = part == 0 ? b0[ni] : b1[ni];
+                    if (bi < 0) continue;
+                    const Block& bk = L.blocks[t][bi];
+                    parts.push_back({cores[t] + bk.off, bk.cols, part == 0 ? 0 : c0[ni]});
+                }
+                task.p_end = (int)parts.size();
+                st.push_back(task);
             }
-            svd.push_back({G, V, S_all + soff[ni], US[ni], Vt[ni], M, N, wide});
+            launch_svd_site(ctx, st, parts);
+        } else {
+            std::vector<CopyTask> gather;
+            std::vector<SvdTask> svd;
+            for (int ni = 0; ni < nn; ++ni) {
+                if (kk[ni] == 0) continue;
+                const int M = bn.dim[ni], N = c0[ni] + c1[ni], k = kk[ni];
+                const int wide = M < N ? 1 : 0;
+                double* G = s.dbl((size_t)M * N);
+                double* V = s.dbl((size_t)k * k);
+                US[ni] = s.dbl((size_t)M * k);
+                Vt[ni] = s.dbl((size_t)k * N);
+                for (int part = 0; part < 2; ++part) {
+                    const int bi = part == 0 ? b0[ni] : b1[ni];
+                    if (bi < 0) continue;
+                    const Block& bk = L.blocks[t][bi];
+                    const int coff = part == 0 ? 0 : c0[ni];
+                    if (wide)
+                        gather.push_back({cores[t] + bk.off, G + coff, bk.rows, bk.cols, bk.cols, N, 0, 0, 0, 1.0});
+                    else
+                        gather.push_back({cores[t] + bk.off, G + (int64_t)coff * M, bk.rows, bk.cols, bk.cols, M,
+                                          0, 1, 0, 1.0});
+                }
+                svd.push_back({G, V, S_all + soff[ni], US[ni], Vt[ni], M, N, wide});
+            }
+            launch_copy(ctx, gather);
+            launch_svd(ctx, svd);
         }
-        launch_copy(ctx, gather);
-        launch_svd(ctx, svd);
         std::vector<double> S_h((size_t)stot);
         if (stot > 0) {
             BSM_CUDA(cudaMemcpyAsync(S_h.data(), S_all, (size_t)stot * sizeof(double),
@@ -447,25 +509,65 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         }
         double* nt = alloc_core(Ln.core_size[t]);
         double* ntm = alloc_core(Ln.core_size[t - 1]);
-        std::vector<CopyTask> vcopy;
-        for (const Block& nbk : Ln.blocks[t]) {
-            const int ni = bn.find(Ln.bonds[t].q[nbk.li]);
-            const int coff = nbk.sigma == 0 ? 0 : c0[ni];
-            const int N = c0[ni] + c1[ni];
-            vcopy.push_back({Vt[ni] + coff, nt + nbk.off, nbk.rows, nbk.cols, N, nbk.cols, 0, 0, 0, 1.0});
-        }
-        launch_copy(ctx, vcopy);
-        std::vector<GemmOut> outs;
-        std::vector<GemmIn> ins;
         const std::vector<int> oldlook = block_lookup(L, t - 1);
-        for (const Block& nbk : Ln.blocks[t - 1]) {
-            const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
-            const Block& ob = L.blocks[t - 1][oldlook[nbk.li * 2 + nbk.sigma]];
-            outs.push_back({ntm + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
-                            (int)ins.size() + 1, 0.0});
-            ins.push_back({cores[t - 1] + ob.off, US[ni], bn.dim[ni], ob.cols, kk[ni], 0, 1.0});
+        bool fused_apply = true;
+        {
+            std::vector<int64_t> fma(nn, 0);
+            for (const Block& nbk : Ln.blocks[t - 1]) {
+                const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
+                fma[ni] += (int64_t)nbk.rows * bn.dim[ni] * nbk.cols;
+            }
+            for (int ni = 0; ni < nn; ++ni)
+                if (fma[ni] > kFusedGemmMaxFma) fused_apply = false;
         }
-        launch_gemm(ctx, outs, ins);
+        if (fused_apply) {
+            std::vector<RTask> rt(nn);
+            std::vector<RCopy> rc;
+            std::vector<RGemm> rg;
+            std::vector<std::vector<RCopy>> cpn(nn);
+            std::vector<std::vector<RGemm>> gmn(nn);
+            for (const Block& nbk : Ln.blocks[t]) {
+                const int ni = bn.find(Ln.bonds[t].q[nbk.li]);
+                const int coff = nbk.sigma == 0 ? 0 : c0[ni];
+                cpn[ni].push_back({Vt[ni] + coff, nt + nbk.off, nbk.rows, nbk.cols, c0[ni] + c1[ni]});
+            }
+            for (const Block& nbk : Ln.blocks[t - 1]) {
+                const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
+                const Block& ob = L.blocks[t - 1][oldlook[nbk.li * 2 + nbk.sigma]];
+                gmn[ni].push_back({cores[t - 1] + ob.off, US[ni], ntm + nbk.off, nbk.rows, bn.dim[ni], nbk.cols,
+                                   kk[ni]});
+            }
+            std::vector<RTask> tasks;
+            for (int ni = 0; ni < nn; ++ni) {
+                if (cpn[ni].empty() && gmn[ni].empty()) continue;
+                RTask task{(int)rc.size(), 0, (int)rg.size(), 0};
+                rc.insert(rc.end(), cpn[ni].begin(), cpn[ni].end());
+                rg.insert(rg.end(), gmn[ni].begin(), gmn[ni].end());
+                task.c_end = (int)rc.size();
+                task.g_end = (int)rg.size();
+                tasks.push_back(task);
+            }
+            launch_right_apply(ctx, tasks, rc, rg);
+        } else {
+            std::vector<CopyTask> vcopy;
+            for (const Block& nbk : Ln.blocks[t]) {
+                const int ni = bn.find(Ln.bonds[t].q[nbk.li]);
+                const int coff = nbk.sigma == 0 ? 0 : c0[ni];
+                const int N = c0[ni] + c1[ni];
+                vcopy.push_back({Vt[ni] + coff, nt + nbk.off, nbk.rows, nbk.cols, N, nbk.cols, 0, 0, 0, 1.0});
+            }
+            launch_copy(ctx, vcopy);
+            std::vector<GemmOut> outs;
+            std::vector<GemmIn> ins;
+            for (const Block& nbk : Ln.blocks[t - 1]) {
+                const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
+                const Block& ob = L.blocks[t - 1][oldlook[nbk.li * 2 + nbk.sigma]];
+                outs.push_back({ntm + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
+                                (int)ins.size() + 1, 0.0});
+                ins.push_back({cores[t - 1] + ob.off, US[ni], bn.dim[ni], ob.cols, kk[ni], 0, 1.0});
+            }
+            launch_gemm(ctx, outs, ins);
+        }
         release(t);
         release(t - 1);
         cores[t] = nt;
