@@ -9,9 +9,14 @@
 namespace bsm {
 namespace dev {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;            // default block size of the batched kernels
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSweeps = 40;
+
+// The routines below work with any block size that is a multiple of 32
+// (callers size small problems down to fewer warps).
+__device__ __forceinline__ int nthreads() { return (int)blockDim.x; }
+__device__ __forceinline__ int nwarps() { return (int)(blockDim.x >> 5); }
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -43,7 +48,7 @@ __device__ __forceinline__ void householder(double* A, double* tau, int M, int N
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = 0; j < k; ++j) {
         double s = 0.0;
-        for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) {
+        for (int i = j + 1 + threadIdx.x; i < M; i += nthreads()) {
             const double v = A[(int64_t)j * M + i];
             s += v * v;
         }
@@ -65,9 +70,9 @@ __device__ __forceinline__ void householder(double* A, double* tau, int M, int N
         __syncthreads();
         const double tj = sh[0], scale = sh[1];
         if (tj != 0.0) {
-            for (int i = j + 1 + threadIdx.x; i < M; i += kThreads) A[(int64_t)j * M + i] *= scale;
+            for (int i = j + 1 + threadIdx.x; i < M; i += nthreads()) A[(int64_t)j * M + i] *= scale;
             __syncthreads();
-            for (int c = j + 1 + warp; c < N; c += kWarps) {
+            for (int c = j + 1 + warp; c < N; c += nwarps()) {
                 // read A(j, c) before the warp-synchronous reduction: lane 0 rewrites it after
                 const double a_jc = A[(int64_t)c * M + j];
                 double w = 0.0;
@@ -85,7 +90,7 @@ __device__ __forceinline__ void householder(double* A, double* tau, int M, int N
 // Q (M x k, column-major) = H_0 ... H_{k-1} applied to the first k columns of I.
 __device__ __forceinline__ void form_q(const double* A, const double* tau, double* Q, int M, int k) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += kThreads) {
+    for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += nthreads()) {
         const int i = (int)(e % M), c = (int)(e / M);
         Q[e] = i == c ? 1.0 : 0.0;
     }
@@ -93,7 +98,7 @@ __device__ __forceinline__ void form_q(const double* A, const double* tau, doubl
     for (int j = k - 1; j >= 0; --j) {
         const double tj = tau[j];
         if (tj == 0.0) continue;
-        for (int c = j + warp; c < k; c += kWarps) {
+        for (int c = j + warp; c < k; c += nwarps()) {
             const double q_jc = Q[(int64_t)c * M + j];
             double w = 0.0;
             for (int i = j + 1 + lane; i < M; i += 32) w += A[(int64_t)j * M + i] * Q[(int64_t)c * M + i];
@@ -119,7 +124,7 @@ __device__ __forceinline__ int rr_player(int pos, int round, int n2) {
 __device__ __forceinline__ void jacobi(double* G, double* V, double* Sraw, int k, double* red, int* s_rot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double f = 0.0;
-    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += kThreads) {
+    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += nthreads()) {
         const double v = G[e];
         f += v * v;
         V[e] = (e % k) == (e / k) ? 1.0 : 0.0;
@@ -132,7 +137,7 @@ __device__ __forceinline__ void jacobi(double* G, double* V, double* Sraw, int k
         if (threadIdx.x == 0) *s_rot = 0;
         __syncthreads();
         for (int round = 0; round < n2 - 1; ++round) {
-            for (int pi = warp; pi < n2 / 2; pi += kWarps) {
+            for (int pi = warp; pi < n2 / 2; pi += nwarps()) {
                 int p = rr_player(pi, round, n2), q = rr_player(n2 - 1 - pi, round, n2);
                 if (p >= k || q >= k) continue;
                 if (p > q) {
@@ -171,7 +176,7 @@ __device__ __forceinline__ void jacobi(double* G, double* V, double* Sraw, int k
         __syncthreads();
         if (!rot) break;
     }
-    for (int j = warp; j < k; j += kWarps) {
+    for (int j = warp; j < k; j += nwarps()) {
         double a = 0.0;
         for (int i = lane; i < k; i += 32) {
             const double x = G[(int64_t)j * k + i];
@@ -193,7 +198,7 @@ __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, 
                                              double* S, double* US, double* Vt, int M, int N, int k, int len,
                                              int wide) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < k; i += kThreads) {
+    for (int i = threadIdx.x; i < k; i += nthreads()) {
         const double si = Sraw[i];
         int rank = 0;
         for (int j = 0; j < k; ++j) {
@@ -203,12 +208,12 @@ __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, 
         perm[rank] = i;
     }
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += kThreads) {
+    for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += nthreads()) {
         const int i = (int)(e / k), r = (int)(e % k);
         const int p = perm[r];
         US[e] = wide ? G[(int64_t)p * k + i] : Sraw[p] * QV[(int64_t)p * len + i];
     }
-    for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += kThreads) {
+    for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += nthreads()) {
         const int r = (int)(e / N), c = (int)(e % N);
         const int p = perm[r];
         double v;
@@ -220,9 +225,9 @@ __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, 
         }
         Vt[e] = v;
     }
-    for (int r = threadIdx.x; r < k; r += kThreads) S[r] = Sraw[perm[r]];
+    for (int r = threadIdx.x; r < k; r += nthreads()) S[r] = Sraw[perm[r]];
     __syncthreads();
-    for (int r = warp; r < k; r += kWarps) {
+    for (int r = warp; r < k; r += nwarps()) {
         double best = -1.0;
         int bi = 0;
         for (int c = lane; c < N; c += 32) {

@@ -13,6 +13,8 @@ namespace {
 
 using dev::kThreads;
 using dev::kWarps;
+using dev::nthreads;
+using dev::nwarps;
 
 constexpr size_t kSweepSmem = 220 * 1024;
 
@@ -41,20 +43,20 @@ __global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restri
     double* R = tau + k;
     for (int s = tk.s_beg; s < tk.s_end; ++s) {
         const LeftSrc sr = srcs[s];
-        for (int64_t e = threadIdx.x; e < (int64_t)sr.rows * N; e += kThreads) {
+        for (int64_t e = threadIdx.x; e < (int64_t)sr.rows * N; e += nthreads()) {
             const int i = (int)(e / N), c = (int)(e % N);
             A[(int64_t)c * M + sr.r0 + i] = sr.src[e];
         }
     }
     __syncthreads();
     dev::householder(A, tau, M, N, red, sh);
-    for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += kThreads) {
+    for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += nthreads()) {
         const int r = (int)(e / N), c = (int)(e % N);
         R[e] = c >= r ? A[(int64_t)c * M + r] : 0.0;
     }
     dev::form_q(A, tau, Q, M, k);
     __syncthreads();
-    for (int j = warp; j < k; j += kWarps) {
+    for (int j = warp; j < k; j += nwarps()) {
         if (A[(int64_t)j * M + j] < 0.0) {
             for (int c = lane; c < N; c += 32) R[(int64_t)j * N + c] = -R[(int64_t)j * N + c];
             for (int i = lane; i < M; i += 32) Q[(int64_t)j * M + i] = -Q[(int64_t)j * M + i];
@@ -63,14 +65,14 @@ __global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restri
     __syncthreads();
     for (int s = tk.s_beg; s < tk.s_end; ++s) {
         const LeftSrc sr = srcs[s];
-        for (int64_t e = threadIdx.x; e < (int64_t)sr.rows * k; e += kThreads) {
+        for (int64_t e = threadIdx.x; e < (int64_t)sr.rows * k; e += nthreads()) {
             const int i = (int)(e / k), c = (int)(e % k);
             sr.dst[e] = Q[(int64_t)c * M + sr.r0 + i];
         }
     }
     for (int x = tk.x_beg; x < tk.x_end; ++x) {
         const LeftX lx = xs[x];
-        for (int64_t e = threadIdx.x; e < (int64_t)k * lx.cols; e += kThreads) {
+        for (int64_t e = threadIdx.x; e < (int64_t)k * lx.cols; e += nthreads()) {
             const int r = (int)(e / lx.cols), c = (int)(e % lx.cols);
             double acc = 0.0;
             for (int j = r; j < N; ++j) acc = fma(R[(int64_t)r * N + j], lx.X[(int64_t)j * lx.cols + c], acc);
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_site(const SvdSiteTask* __rest
     int* perm = (int*)(Sraw + k);
     for (int p = tk.p_beg; p < tk.p_end; ++p) {
         const SvdPart pt = parts[p];
-        for (int64_t e = threadIdx.x; e < (int64_t)M * pt.cols; e += kThreads) {
+        for (int64_t e = threadIdx.x; e < (int64_t)M * pt.cols; e += nthreads()) {
             const int i = (int)(e / pt.cols), c = pt.coff + (int)(e % pt.cols);
             if (tk.wide)
                 B[(int64_t)i * N + c] = pt.src[e];      // A^T column-major
@@ -107,14 +109,14 @@ __global__ void __launch_bounds__(kThreads) k_svd_site(const SvdSiteTask* __rest
     __syncthreads();
     dev::householder(B, tau, len, k, red, sh);
     // G = R^T (column-major): G(i, j) = R(j, i), nonzero for i >= j
-    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += kThreads) {
+    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += nthreads()) {
         const int j = (int)(e / k), i = (int)(e % k);
         G[e] = i >= j ? B[(int64_t)i * len + j] : 0.0;
     }
     dev::form_q(B, tau, Q, len, k);
     __syncthreads();
     dev::jacobi(G, V, Sraw, k, red, &s_rot);
-    for (int64_t e = threadIdx.x; e < (int64_t)len * k; e += kThreads) {
+    for (int64_t e = threadIdx.x; e < (int64_t)len * k; e += nthreads()) {
         const int p = (int)(e / len), i = (int)(e % len);
         double acc = 0.0;
         for (int j = 0; j < k; ++j) acc = fma(Q[(int64_t)j * len + i], V[(int64_t)p * k + j], acc);
@@ -130,14 +132,14 @@ __global__ void __launch_bounds__(kThreads) k_right_apply(const RTask* __restric
     const RTask tk = tasks[blockIdx.x];
     for (int c = tk.c_beg; c < tk.c_end; ++c) {
         const RCopy rc = copies[c];
-        for (int64_t e = threadIdx.x; e < (int64_t)rc.rows * rc.cols; e += kThreads) {
+        for (int64_t e = threadIdx.x; e < (int64_t)rc.rows * rc.cols; e += nthreads()) {
             const int i = (int)(e / rc.cols), j = (int)(e % rc.cols);
             rc.dst[e] = rc.src[(int64_t)i * rc.src_ld + j];
         }
     }
     for (int g = tk.g_beg; g < tk.g_end; ++g) {
         const RGemm rg = gemms[g];
-        for (int64_t e = threadIdx.x; e < (int64_t)rg.rows * rg.keep; e += kThreads) {
+        for (int64_t e = threadIdx.x; e < (int64_t)rg.rows * rg.keep; e += nthreads()) {
             const int i = (int)(e / rg.keep), j = (int)(e % rg.keep);
             double acc = 0.0;
             for (int q = 0; q < rg.K; ++q) acc = fma(rg.X[(int64_t)i * rg.K + q], rg.US[(int64_t)q * rg.ldus + j], acc);
@@ -162,6 +164,18 @@ unsigned char* upload_pack(Scratch& s, const Pack& p) {
     std::vector<unsigned char> h = p.host;
     if (h.empty()) h.push_back(0);
     return s.up(h);
+}
+
+// Warps per CTA: one per Jacobi pair of the largest problem, between 1 and 8.
+int block_for(int kmax) { return 32 * std::max(1, std::min(8, (kmax + 1) / 2)); }
+
+template <class F>
+void allow_smem(F* kern) {
+    static bool done = false;   // set once per process (the attribute is per function)
+    if (!done) {
+        BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem));
+        done = true;
+    }
 }
 
 void count_launch(Context* ctx) {
@@ -209,8 +223,10 @@ void launch_left_site(Context* ctx, const std::vector<LeftTask>& tasks, const st
     Scratch s(ctx);
     unsigned char* d = upload_pack(s, pk);
     Prof pr(ctx, KK_QR, fl, by);
-    BSM_CUDA(cudaFuncSetAttribute(k_left_site, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_left_site<<<(unsigned)tasks.size(), kThreads, smem, ctx->stream>>>((const LeftTask*)(d + ot),
+    allow_smem(k_left_site);
+    int kmax = 1;
+    for (const LeftTask& t : tasks) kmax = std::max(kmax, 2 * t.k);
+    k_left_site<<<(unsigned)tasks.size(), block_for(kmax), smem, ctx->stream>>>((const LeftTask*)(d + ot),
                                                                         (const LeftSrc*)(d + os),
                                                                         (const LeftX*)(d + ox));
     count_launch(ctx);
@@ -235,8 +251,10 @@ void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const 
     Scratch s(ctx);
     unsigned char* d = upload_pack(s, pk);
     Prof pr(ctx, KK_SVD, fl, by);
-    BSM_CUDA(cudaFuncSetAttribute(k_svd_site, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_svd_site<<<(unsigned)tasks.size(), kThreads, smem, ctx->stream>>>((const SvdSiteTask*)(d + ot),
+    allow_smem(k_svd_site);
+    int kmax = 1;
+    for (const SvdSiteTask& t : tasks) kmax = std::max(kmax, t.k);
+    k_svd_site<<<(unsigned)tasks.size(), block_for(kmax), smem, ctx->stream>>>((const SvdSiteTask*)(d + ot),
                                                                        (const SvdPart*)(d + op));
     count_launch(ctx);
     pr.done();
