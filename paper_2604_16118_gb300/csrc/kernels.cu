@@ -209,6 +209,21 @@ void check_launch(Context* ctx) {
     BSM_CUDA(cudaGetLastError());
 }
 
+// Every kernel of the library prefers the same L1/shared-memory split (maximum
+// shared memory), so consecutive launches never wait for the SM to re-partition.
+void configure_carveout() {
+    static bool done = false;
+    if (done) return;
+    const int carve = cudaSharedmemCarveoutMaxShared;
+    BSM_CUDA(cudaFuncSetAttribute(k_copy, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    BSM_CUDA(cudaFuncSetAttribute(k_gemm, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    BSM_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    BSM_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    BSM_CUDA(cudaFuncSetAttribute(k_svd_finalize, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    BSM_CUDA(cudaFuncSetAttribute(k_sumsq, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    done = true;
+}
+
 // RAII bracket of one launch for the optional profiler
 struct ProfScope {
     Context* ctx;
@@ -249,6 +264,7 @@ void Context::prof_end(int kind, double fl, double by, cudaEvent_t e0) {
 
 void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
     if (tasks.empty()) return;
+    configure_carveout();
     std::vector<CopyChunk> chunks;
     for (int i = 0; i < (int)tasks.size(); ++i) {
         const int64_t n = (int64_t)tasks[i].rows * tasks[i].cols;
@@ -268,6 +284,7 @@ void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
 
 void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins) {
     if (outs.empty()) return;
+    configure_carveout();
     std::vector<GemmTile> tiles;
     double fl = 0.0, by = 0.0;
     for (int o = 0; o < (int)outs.size(); ++o) {
@@ -296,6 +313,7 @@ constexpr size_t kSmemBudget = 220 * 1024;
 
 void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in) {
     if (tasks_in.empty()) return;
+    configure_carveout();
     double fl = 0.0, by = 0.0;
     std::vector<QrTask> small, large;
     size_t smem_max = 0;
@@ -334,6 +352,7 @@ void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in) {
 
 void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
     if (tasks.empty()) return;
+    configure_carveout();
     Scratch s(ctx);
     // 1. Householder QR of M (tall) or M^T (wide): Q is len x k, R is k x k
     std::vector<QrTask> qr;
@@ -413,6 +432,7 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
 void launch_sumsq(Context* ctx, const std::vector<const double*>& xs, const std::vector<int64_t>& ns,
                   double* out_dev) {
     if (xs.empty()) return;
+    configure_carveout();
     Scratch s(ctx);
     const double** d_x = s.up(xs);
     int64_t* d_n = s.up(ns);

@@ -171,9 +171,11 @@ int block_for(int kmax) { return 32 * std::max(1, std::min(8, (kmax + 1) / 2)); 
 
 template <class F>
 void allow_smem(F* kern) {
-    static bool done = false;   // set once per process (the attribute is per function)
+    static bool done = false;   // set once per process (the attributes are per function)
     if (!done) {
         BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem));
+        BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
         done = true;
     }
 }
@@ -275,6 +277,7 @@ void launch_right_apply(Context* ctx, const std::vector<RTask>& tasks, const std
     Scratch s(ctx);
     unsigned char* d = upload_pack(s, pk);
     Prof pr(ctx, KK_GEMM, fl, by);
+    allow_smem(k_right_apply);
     k_right_apply<<<(unsigned)tasks.size(), kThreads, 0, ctx->stream>>>(
         (const RTask*)(d + ot), (const RCopy*)(d + oc), (const RGemm*)(d + og));
     count_launch(ctx);
