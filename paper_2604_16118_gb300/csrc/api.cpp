@@ -29,6 +29,36 @@ void Context::free(void* p) {
     if (p) cudaFreeAsync(p, stream);
 }
 
+void* Context::upload_raw(const void* src, size_t bytes) {
+    void* d = alloc(bytes);
+    if (bytes > kRingSlotBytes) {
+        BSM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, stream));
+        return d;
+    }
+    if (!ring_host) {
+        BSM_CUDA(cudaMallocHost((void**)&ring_host, kRingSlots * kRingSlotBytes));
+        ring_ev.resize(kRingSlots);
+        ring_used.assign(kRingSlots, 0);
+        for (auto& e : ring_ev) BSM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const int slot = ring_next;
+    ring_next = (ring_next + 1) % kRingSlots;
+    if (ring_used[slot]) BSM_CUDA(cudaEventSynchronize(ring_ev[slot]));
+    unsigned char* h = ring_host + (size_t)slot * kRingSlotBytes;
+    std::memcpy(h, src, bytes);
+    BSM_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, stream));
+    BSM_CUDA(cudaEventRecord(ring_ev[slot], stream));
+    ring_used[slot] = 1;
+    return d;
+}
+
+void Context::release_ring() {
+    for (auto e : ring_ev) cudaEventDestroy(e);
+    ring_ev.clear();
+    if (ring_host) cudaFreeHost(ring_host);
+    ring_host = nullptr;
+}
+
 }  // namespace bsm
 
 namespace {
@@ -120,6 +150,7 @@ bsmps_status bsmps_ctx_destroy(bsmps_ctx ctx) {
             cudaEventDestroy(r.e1);
         }
         for (auto e : ctx->c.event_pool) cudaEventDestroy(e);
+        ctx->c.release_ring();
     });
     delete ctx;
     return s;

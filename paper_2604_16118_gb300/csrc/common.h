@@ -128,16 +128,24 @@ struct Context {
     cudaEvent_t take_event();
     void prof_begin(cudaEvent_t* e0);
     void prof_end(int kind, double flops, double bytes, cudaEvent_t e0);
+    // pinned staging ring for task uploads: a copy from pageable memory can make
+    // the host wait for the stream, so uploads go through page-locked slots
+    // whose reuse is gated by an event recorded after their copy
+    static constexpr int kRingSlots = 64;
+    static constexpr size_t kRingSlotBytes = 256 * 1024;
+    unsigned char* ring_host = nullptr;
+    std::vector<cudaEvent_t> ring_ev;
+    std::vector<char> ring_used;
+    int ring_next = 0;
+    void* upload_raw(const void* src, size_t bytes);
+    void release_ring();
     // scratch for task uploads and temporaries
     void* alloc(size_t bytes);
     void free(void* p);
     template <class T>
     T* upload(const std::vector<T>& v) {
         if (v.empty()) return nullptr;
-        T* d = (T*)alloc(v.size() * sizeof(T));
-        BSM_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
-                                 stream));
-        return d;
+        return (T*)upload_raw(v.data(), v.size() * sizeof(T));
     }
     void sync() { BSM_CUDA(cudaStreamSynchronize(stream)); }
 };

@@ -293,7 +293,7 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
     // ---- left-to-right QR sweep ----
     for (int t = 0; t + 1 < K; ++t) {
         Scratch s(ctx);
-        const Bond& bm = L.bonds[t + 1];
+        const Bond bm = L.bonds[t + 1];   // the old bond (L is updated in place below)
         const int nm = (int)bm.q.size();
         std::vector<int> Mrows(nm, 0), krank(nm, 0);
         std::vector<std::vector<std::pair<int, int>>> stack(nm);   // (block index, row offset)
@@ -302,7 +302,8 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             stack[bk.ri].push_back({bi, Mrows[bk.ri]});
             Mrows[bk.ri] += bk.rows;
         }
-        Layout Ln = L;
+        const std::vector<int> oldlook = block_lookup(L, t + 1);
+        const std::vector<Block> oldB_t = L.blocks[t], oldB_t1 = L.blocks[t + 1];
         {
             Bond nb;
             for (int mi = 0; mi < nm; ++mi) {
@@ -312,14 +313,13 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
                     nb.dim.push_back(krank[mi]);
                 }
             }
-            Ln.bonds[t + 1] = nb;
-            rebuild_site(Ln, t);
-            rebuild_site(Ln, t + 1);
+            L.bonds[t + 1] = nb;
+            rebuild_site(L, t);
+            rebuild_site(L, t + 1);
         }
-        double* nt = alloc_core(Ln.core_size[t]);
-        double* nt1 = alloc_core(Ln.core_size[t + 1]);
-        const std::vector<int> oldlook = block_lookup(L, t + 1);
-        const std::vector<int> newlook_t = block_lookup(Ln, t);
+        double* nt = alloc_core(L.core_size[t]);
+        double* nt1 = alloc_core(L.core_size[t + 1]);
+        const std::vector<int> newlook_t = block_lookup(L, t);
         // fused path: one CTA per sector does gather, QR, Q scatter and R X
         bool fused = true;
         for (int mi = 0; mi < nm && fused; ++mi) {
@@ -327,7 +327,7 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             int64_t rx = 0;
             for (int sg = 0; sg < 2; ++sg) {
                 const int ob = oldlook[mi * 2 + sg];
-                if (ob >= 0) rx += (int64_t)krank[mi] * bm.dim[mi] * L.blocks[t + 1][ob].cols;
+                if (ob >= 0) rx += (int64_t)krank[mi] * bm.dim[mi] * oldB_t1[ob].cols;
             }
             fused = left_site_fits(Mrows[mi], bm.dim[mi], rx);
         }
@@ -337,17 +337,17 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             std::vector<LeftX> lx;
             for (int mi = 0; mi < nm; ++mi) {
                 if (Mrows[mi] == 0) continue;
-                const int nmi = Ln.bonds[t + 1].find(bm.q[mi]);
+                const int nmi = L.bonds[t + 1].find(bm.q[mi]);
                 LeftTask task{Mrows[mi], bm.dim[mi], krank[mi], (int)ls.size(), 0, (int)lx.size(), 0};
                 for (auto& pr : stack[mi]) {
-                    const Block& ob = L.blocks[t][pr.first];
-                    const Block& nbk = Ln.blocks[t][newlook_t[ob.li * 2 + ob.sigma]];
+                    const Block& ob = oldB_t[pr.first];
+                    const Block& nbk = L.blocks[t][newlook_t[ob.li * 2 + ob.sigma]];
                     ls.push_back({cores[t] + ob.off, nt + nbk.off, ob.rows, pr.second});
                 }
                 task.s_end = (int)ls.size();
-                for (const Block& nbk : Ln.blocks[t + 1]) {
+                for (const Block& nbk : L.blocks[t + 1]) {
                     if (nbk.li != nmi) continue;
-                    const Block& ob = L.blocks[t + 1][oldlook[mi * 2 + nbk.sigma]];
+                    const Block& ob = oldB_t1[oldlook[mi * 2 + nbk.sigma]];
                     lx.push_back({cores[t + 1] + ob.off, nt1 + nbk.off, ob.cols});
                 }
                 task.x_end = (int)lx.size();
@@ -367,7 +367,7 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
                 Rm[mi] = s.dbl((size_t)k * N);
                 double* tau = s.dbl((size_t)k);
                 for (auto& pr : stack[mi]) {
-                    const Block& bk = L.blocks[t][pr.first];
+                    const Block& bk = oldB_t[pr.first];
                     gather.push_back({cores[t] + bk.off, Am[mi] + pr.second, bk.rows, bk.cols, bk.cols, M,
                                       0, 1, 0, 1.0});
                 }
@@ -376,11 +376,11 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             launch_copy(ctx, gather);
             launch_qr(ctx, qr);
             std::vector<CopyTask> qcopy;
-            for (const Block& nbk : Ln.blocks[t]) {
-                const int mi = bm.find(Ln.bonds[t + 1].q[nbk.ri]);
+            for (const Block& nbk : L.blocks[t]) {
+                const int mi = bm.find(L.bonds[t + 1].q[nbk.ri]);
                 int r0 = -1;
                 for (auto& pr : stack[mi]) {
-                    const Block& ob = L.blocks[t][pr.first];
+                    const Block& ob = oldB_t[pr.first];
                     if (ob.li == nbk.li && ob.sigma == nbk.sigma) r0 = pr.second;
                 }
                 qcopy.push_back({Qm[mi] + r0, nt + nbk.off, nbk.rows, nbk.cols, Mrows[mi], nbk.cols, 1, 0, 0,
@@ -389,9 +389,9 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             launch_copy(ctx, qcopy);
             std::vector<GemmOut> outs;
             std::vector<GemmIn> ins;
-            for (const Block& nbk : Ln.blocks[t + 1]) {
-                const int mi = bm.find(Ln.bonds[t + 1].q[nbk.li]);
-                const Block& ob = L.blocks[t + 1][oldlook[mi * 2 + nbk.sigma]];
+            for (const Block& nbk : L.blocks[t + 1]) {
+                const int mi = bm.find(L.bonds[t + 1].q[nbk.li]);
+                const Block& ob = oldB_t1[oldlook[mi * 2 + nbk.sigma]];
                 outs.push_back({nt1 + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
                                 (int)ins.size() + 1, 0.0});
                 ins.push_back({Rm[mi], cores[t + 1] + ob.off, ob.rows, bm.dim[mi], ob.cols, 0, 1.0});
@@ -404,7 +404,6 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         owned[t] = 1;
         cores[t + 1] = nt1;
         owned[t + 1] = 1;
-        L = Ln;
     }
 
     // ---- right-to-left SVD sweep ----
@@ -412,7 +411,7 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
     double td2 = 0.0, cd2 = 0.0;
     for (int t = K - 1; t >= 1; --t) {
         Scratch s(ctx);
-        const Bond& bn = L.bonds[t];
+        const Bond bn = L.bonds[t];   // the old bond (L is updated in place below)
         const int nn = (int)bn.q.size();
         std::vector<int> c0(nn, 0), c1(nn, 0), b0(nn, -1), b1(nn, -1), kk(nn, 0);
         for (int bi = 0; bi < (int)L.blocks[t].size(); ++bi) {
@@ -495,7 +494,8 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         for (int ni = 0; ni < nn; ++ni)
             for (int j = 0; j < kk[ni]; ++j) sv.push_back({S_h[soff[ni] + j], ni, j});
         const std::vector<int> keep = choose_cut(sv, nn, tol2, r_max, &td2, &cd2);
-        Layout Ln = L;
+        const std::vector<int> oldlook = block_lookup(L, t - 1);
+        const std::vector<Block> oldB_tm = L.blocks[t - 1];
         {
             Bond nb;
             for (int ni = 0; ni < nn; ++ni)
@@ -503,18 +503,17 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
                     nb.q.push_back(bn.q[ni]);
                     nb.dim.push_back(keep[ni]);
                 }
-            Ln.bonds[t] = nb;
-            rebuild_site(Ln, t - 1);
-            rebuild_site(Ln, t);
+            L.bonds[t] = nb;
+            rebuild_site(L, t - 1);
+            rebuild_site(L, t);
         }
-        double* nt = alloc_core(Ln.core_size[t]);
-        double* ntm = alloc_core(Ln.core_size[t - 1]);
-        const std::vector<int> oldlook = block_lookup(L, t - 1);
+        double* nt = alloc_core(L.core_size[t]);
+        double* ntm = alloc_core(L.core_size[t - 1]);
         bool fused_apply = true;
         {
             std::vector<int64_t> fma(nn, 0);
-            for (const Block& nbk : Ln.blocks[t - 1]) {
-                const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
+            for (const Block& nbk : L.blocks[t - 1]) {
+                const int ni = bn.find(L.bonds[t].q[nbk.ri]);
                 fma[ni] += (int64_t)nbk.rows * bn.dim[ni] * nbk.cols;
             }
             for (int ni = 0; ni < nn; ++ni)
@@ -526,14 +525,14 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             std::vector<RGemm> rg;
             std::vector<std::vector<RCopy>> cpn(nn);
             std::vector<std::vector<RGemm>> gmn(nn);
-            for (const Block& nbk : Ln.blocks[t]) {
-                const int ni = bn.find(Ln.bonds[t].q[nbk.li]);
+            for (const Block& nbk : L.blocks[t]) {
+                const int ni = bn.find(L.bonds[t].q[nbk.li]);
                 const int coff = nbk.sigma == 0 ? 0 : c0[ni];
                 cpn[ni].push_back({Vt[ni] + coff, nt + nbk.off, nbk.rows, nbk.cols, c0[ni] + c1[ni]});
             }
-            for (const Block& nbk : Ln.blocks[t - 1]) {
-                const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
-                const Block& ob = L.blocks[t - 1][oldlook[nbk.li * 2 + nbk.sigma]];
+            for (const Block& nbk : L.blocks[t - 1]) {
+                const int ni = bn.find(L.bonds[t].q[nbk.ri]);
+                const Block& ob = oldB_tm[oldlook[nbk.li * 2 + nbk.sigma]];
                 gmn[ni].push_back({cores[t - 1] + ob.off, US[ni], ntm + nbk.off, nbk.rows, bn.dim[ni], nbk.cols,
                                    kk[ni]});
             }
@@ -550,8 +549,8 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             launch_right_apply(ctx, tasks, rc, rg);
         } else {
             std::vector<CopyTask> vcopy;
-            for (const Block& nbk : Ln.blocks[t]) {
-                const int ni = bn.find(Ln.bonds[t].q[nbk.li]);
+            for (const Block& nbk : L.blocks[t]) {
+                const int ni = bn.find(L.bonds[t].q[nbk.li]);
                 const int coff = nbk.sigma == 0 ? 0 : c0[ni];
                 const int N = c0[ni] + c1[ni];
                 vcopy.push_back({Vt[ni] + coff, nt + nbk.off, nbk.rows, nbk.cols, N, nbk.cols, 0, 0, 0, 1.0});
@@ -559,9 +558,9 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
             launch_copy(ctx, vcopy);
             std::vector<GemmOut> outs;
             std::vector<GemmIn> ins;
-            for (const Block& nbk : Ln.blocks[t - 1]) {
-                const int ni = bn.find(Ln.bonds[t].q[nbk.ri]);
-                const Block& ob = L.blocks[t - 1][oldlook[nbk.li * 2 + nbk.sigma]];
+            for (const Block& nbk : L.blocks[t - 1]) {
+                const int ni = bn.find(L.bonds[t].q[nbk.ri]);
+                const Block& ob = oldB_tm[oldlook[nbk.li * 2 + nbk.sigma]];
                 outs.push_back({ntm + nbk.off, nbk.rows, nbk.cols, nbk.cols, (int)ins.size(),
                                 (int)ins.size() + 1, 0.0});
                 ins.push_back({cores[t - 1] + ob.off, US[ni], bn.dim[ni], ob.cols, kk[ni], 0, 1.0});
@@ -574,7 +573,6 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         owned[t] = 1;
         cores[t - 1] = ntm;
         owned[t - 1] = 1;
-        L = Ln;
     }
     if (disc_tol) *disc_tol = std::sqrt(td2);
     if (disc_cap) *disc_cap = std::sqrt(cd2);
