@@ -60,6 +60,7 @@ extern "C" {
 typedef struct bsmps_ctx_s* bsmps_ctx;
 typedef struct bsmps_mps_s* bsmps_mps;
 typedef struct bsmps_mpo_s* bsmps_mpo;
+typedef struct bsmps_mlp_s* bsmps_mlp;
 
 typedef enum {
     BSMPS_OK = 0,
@@ -300,6 +301,32 @@ BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const b
                                    const bsmps_solver_params* params,
                                    bsmps_solver_state* state, bsmps_mps* x,
                                    bsmps_step_info* info);
+
+/* ---- learned preconditioner network ------------------------------------- *
+ * A multilayer perceptron (no counterpart in the paper; it serves the learned
+ * preconditioner controller that predicts preconditioner parameters from the
+ * one-body spectrum and the residual history, with the paper's plain
+ * preconditioner as fallback).  Layers l = 0..n_layers-1 map widths[l] to
+ * widths[l+1]; hidden layers use ReLU, the last layer is linear.  The forward
+ * and backward products use BF16 copies of the weights with FP32 accumulation;
+ * the FP32 master parameters are updated by Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8) and re-rounded to BF16 (round to nearest even) after every update.
+ * Flat parameter layout: for each layer W (widths[l+1] x widths[l], row-major)
+ * then b (widths[l+1]).  Inputs/outputs are host float32 arrays, row-major
+ * (batch x width).  Loss: mean over batch and outputs of (y - t)^2. */
+BSMPS_API bsmps_status bsmps_mlp_create(bsmps_ctx ctx, int n_layers, const int* widths,
+                                        const float* params, int64_t n_params, bsmps_mlp* out);
+BSMPS_API bsmps_status bsmps_mlp_num_params(bsmps_mlp net, int64_t* n);
+BSMPS_API bsmps_status bsmps_mlp_get_params(bsmps_mlp net, float* params);
+BSMPS_API bsmps_status bsmps_mlp_forward(bsmps_mlp net, const float* x, int batch, float* y);
+/* loss and (when grad != NULL) the gradient of the loss w.r.t. the flat
+ * parameters, evaluated with the BF16 weights. */
+BSMPS_API bsmps_status bsmps_mlp_loss_grad(bsmps_mlp net, const float* x, const float* t, int batch,
+                                           float* loss, float* grad);
+/* one Adam step on a batch; *loss (may be NULL) is the loss before the step. */
+BSMPS_API bsmps_status bsmps_mlp_train_step(bsmps_mlp net, const float* x, const float* t, int batch,
+                                            float lr, float* loss);
+BSMPS_API bsmps_status bsmps_mlp_destroy(bsmps_mlp net);
 
 #ifdef __cplusplus
 }

@@ -18,6 +18,12 @@ struct bsmps_mpo_s {
 
 namespace bsm {
 
+Context* context_of(bsmps_ctx c) {
+    BSM_REQUIRE(c != nullptr, BSMPS_ERR_INVALID_ARG, "null context");
+    BSM_CUDA(cudaSetDevice(c->c.device));
+    return &c->c;
+}
+
 void* Context::alloc(size_t bytes) {
     if (bytes == 0) return nullptr;
     void* p = nullptr;

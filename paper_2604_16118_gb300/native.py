@@ -89,6 +89,15 @@ _SIGS = {
     "bsmps_precondition": (_i, [_vp, C.POINTER(Precond), _i, _vp, C.POINTER(_vp), _pi]),
     "bsmps_dot": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
     "bsmps_dot_noalloc": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
+    "bsmps_mlp_create": (_i, [_vp, _i, _pi, C.POINTER(C.c_float), _i64, C.POINTER(_vp)]),
+    "bsmps_mlp_num_params": (_i, [_vp, _pi64]),
+    "bsmps_mlp_get_params": (_i, [_vp, C.POINTER(C.c_float)]),
+    "bsmps_mlp_forward": (_i, [_vp, C.POINTER(C.c_float), _i, C.POINTER(C.c_float)]),
+    "bsmps_mlp_loss_grad": (_i, [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float), _i, C.POINTER(C.c_float),
+                                 C.POINTER(C.c_float)]),
+    "bsmps_mlp_train_step": (_i, [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float), _i, C.c_float,
+                                  C.POINTER(C.c_float)]),
+    "bsmps_mlp_destroy": (_i, [_vp]),
     "bsmps_eigensolve_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
                                    C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(StepInfo)]),
 }
@@ -382,3 +391,59 @@ def eigensolve_step(ctx, mpo, p, params, state, x):
     _check(ctx, code)
     x.h = None          # destroyed by the library
     return MPS(ctx, h), info.as_dict()
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class MLP:
+    """bsmps_mlp handle: BF16-weight MLP with FP32 accumulation and Adam training."""
+
+    def __init__(self, ctx, widths, params):
+        self.ctx = ctx
+        self.widths = [int(w) for w in widths]
+        w = np.ascontiguousarray(self.widths, dtype=np.int32)
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        h = _vp()
+        _check(ctx, lib().bsmps_mlp_create(ctx.h, len(w) - 1, _iptr(w), _fptr(p), len(p), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().bsmps_mlp_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def n_params(self):
+        n = C.c_int64()
+        _check(self.ctx, lib().bsmps_mlp_num_params(self.h, C.byref(n)))
+        return n.value
+
+    def params(self):
+        p = np.zeros(self.n_params(), dtype=np.float32)
+        _check(self.ctx, lib().bsmps_mlp_get_params(self.h, _fptr(p)))
+        return p
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros((x.shape[0], self.widths[-1]), dtype=np.float32)
+        _check(self.ctx, lib().bsmps_mlp_forward(self.h, _fptr(x), x.shape[0], _fptr(y)))
+        return y
+
+    def loss_grad(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(self.n_params(), dtype=np.float32)
+        loss = C.c_float()
+        _check(self.ctx, lib().bsmps_mlp_loss_grad(self.h, _fptr(x), _fptr(t), x.shape[0], C.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def train_step(self, x, t, lr):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = C.c_float()
+        _check(self.ctx, lib().bsmps_mlp_train_step(self.h, _fptr(x), _fptr(t), x.shape[0], lr, C.byref(loss)))
+        return loss.value

@@ -1,0 +1,90 @@
+"""Learned preconditioner controller: network kernels vs the FP64 reference, training,
+and what the trained controller gains over the plain preconditioner parameters."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as OMLP
+from synth import molecule_like, spinless_random_chain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2604_16118_gb300 import build, native
+    build.build()
+    return native
+
+
+@pytest.fixture(scope="module")
+def ctx(nat):
+    return nat.Context(0)
+
+
+def test_network_gradients_match_fp64_reference(nat, ctx):
+    widths = [128, 256, 256, 256, 2]
+    rng = np.random.default_rng(0)
+    p = OMLP.init_params(widths, 3)
+    x = rng.standard_normal((16, 128)).astype(np.float32)
+    t = rng.standard_normal((16, 2)).astype(np.float32)
+    net = nat.MLP(ctx, widths, p)
+    loss, g = net.loss_grad(x, t)
+    oloss, og = OMLP.loss_grad(p, widths, x.astype(np.float64), t.astype(np.float64))
+    # FP32 accumulation over <= 256 terms with identical bf16 weights
+    assert abs(loss - oloss) <= 1e-4 * abs(oloss)
+    assert np.abs(g - og).max() <= 1e-4 * np.abs(og).max()
+    y = net.forward(x)
+    assert np.abs(y - OMLP.forward(p, widths, x.astype(np.float64))[-1]).max() <= 1e-4 * np.abs(y).max()
+
+
+def test_training_reduces_the_loss(nat, ctx):
+    widths = [128, 256, 256, 256, 2]
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((64, 128)).astype(np.float32)
+    A = rng.standard_normal((128, 2)).astype(np.float32) / 12.0
+    t = np.tanh(x @ A)
+    net = nat.MLP(ctx, widths, OMLP.init_params(widths, 4))
+    l0 = net.loss_grad(x, t)[0]
+    for _ in range(200):
+        net.train_step(x, t, 1e-3)
+    assert net.loss_grad(x, t)[0] < 0.05 * l0
+    # the masters moved and the bf16 copies follow them
+    assert np.abs(net.params() - OMLP.init_params(widths, 4)).max() > 0.0
+
+
+def problems(seeds, kind):
+    out = []
+    for s in seeds:
+        if kind == 0:
+            out.append(molecule_like(L=3 + s % 2, n_up=1 + s % 2, n_dn=1 + (s // 2) % 2, seed=100 + s))
+        else:
+            K = 6 + 2 * (s % 2)
+            out.append(spinless_random_chain(K=K, N=K // 2, seed=200 + s))
+    return out
+
+
+def test_learned_controller_gain_over_plain_parameters(nat, ctx):
+    from paper_2604_16118_gb300 import learned as LP
+    train_p = problems(range(12), 0) + problems(range(12), 1)
+    test_p = problems(range(20, 24), 0) + problems(range(20, 24), 1)
+    X, Y, _ = LP.make_dataset(ctx, train_p)
+    net, losses = LP.train(ctx, X, Y, steps=300)
+    assert losses[-1] < losses[0]
+    gains = []
+    for wl in test_p:
+        sc = LP.grid_scores(ctx, wl)
+        sel = LP.choose(net, wl)
+        assert sel[0] in LP.C0_GRID and sel[1] in LP.MARGIN_GRID
+        plain = sc[LP.PLAIN]
+        assert math.isfinite(plain) and plain > 0
+        gains.append(sc[sel] / plain)
+    gain = float(np.exp(np.mean(np.log(np.maximum(gains, 1e-6)))))
+    print(f"\nheld-out energy decrease per GFLOP, learned / plain: per problem {np.round(gains, 3)}, "
+          f"geometric mean {gain:.3f}")
+    # the controller never runs worse than 1/2 of the plain parameters on average
+    assert gain >= 0.5
+    # run-time use: learned parameters or the plain fallback, energies decrease
+    E, F, used = LP.solve(ctx, net, test_p[0], 4)
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(E, E[1:]))
