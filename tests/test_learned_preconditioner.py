@@ -67,14 +67,14 @@ def problems(seeds, kind):
 
 def test_learned_controller_gain_over_plain_parameters(nat, ctx):
     from paper_2604_16118_gb300 import learned as LP
-    train_p = problems(range(12), 0) + problems(range(12), 1)
-    test_p = problems(range(20, 24), 0) + problems(range(20, 24), 1)
-    X, Y, _ = LP.make_dataset(ctx, train_p)
+    train_p = problems(range(6), 0) + problems(range(6), 1)
+    test_p = problems(range(20, 22), 0) + problems(range(20, 22), 1)
+    X, Y, _ = LP.make_dataset(ctx, train_p, n_steps=3)
     net, losses = LP.train(ctx, X, Y, steps=300)
     assert losses[-1] < losses[0]
     gains = []
     for wl in test_p:
-        sc = LP.grid_scores(ctx, wl)
+        sc = LP.grid_scores(ctx, wl, n_steps=3)
         sel = LP.choose(net, wl)
         assert sel[0] in LP.C0_GRID and sel[1] in LP.MARGIN_GRID
         plain = sc[LP.PLAIN]
@@ -83,8 +83,9 @@ def test_learned_controller_gain_over_plain_parameters(nat, ctx):
     gain = float(np.exp(np.mean(np.log(np.maximum(gains, 1e-6)))))
     print(f"\nheld-out energy decrease per GFLOP, learned / plain: per problem {np.round(gains, 3)}, "
           f"geometric mean {gain:.3f}")
-    # the controller never runs worse than 1/2 of the plain parameters on average
-    assert gain >= 0.5
+    # on these problems the grid's best points beat the plain parameters by 1.6-2.1x
+    # (probe over 8 problems); the trained controller must keep a clear gain
+    assert gain >= 1.2
     # run-time use: learned parameters or the plain fallback, energies decrease
     E, F, used = LP.solve(ctx, net, test_p[0], 4)
     assert all(b <= a + 1e-12 * abs(a) for a, b in zip(E, E[1:]))
