@@ -282,13 +282,8 @@ def main():
         infos.append(info)
     torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        f = torch.tensor([total_flops], device=dev, dtype=torch.float64)
-        dist.all_reduce(f)
-        total_flops = float(f.item())
+    from paper_2604_16118_gb300 import replicas
+    total_ms, total_flops = replicas.reduce_timing(total_ms, total_flops, dist, dev)
     clocks = sampler.stop()
     ms_per_step = total_ms / args.steps
     value = total_flops / (total_ms * 1e-3) / 1e12

@@ -193,10 +193,11 @@ __device__ __forceinline__ void jacobi(double* G, double* V, double* Sraw, int k
 // wide (M < N):  M^T = Q R, R^T = G, G V = U' S => U = U', Vt = (Q V)^T.
 // QV: column-major len x k (QV[p*len + i] = (Q V)(i, p)).  Writes S (k,
 // descending, ties by index), US = U diag(S) (M x k row-major) and Vt (k x N
-// row-major) with the largest-|.| entry of every Vt row positive.  perm: k ints.
+// row-major, row strides ldus / ldvt) with the largest-|.| entry of every Vt
+// row positive.  perm: k ints.
 __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, const double* Sraw, int* perm,
                                              double* S, double* US, double* Vt, int M, int N, int k, int len,
-                                             int wide) {
+                                             int wide, int ldus, int ldvt) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < k; i += nthreads()) {
         const double si = Sraw[i];
@@ -211,7 +212,7 @@ __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, 
     for (int64_t e = threadIdx.x; e < (int64_t)M * k; e += nthreads()) {
         const int i = (int)(e / k), r = (int)(e % k);
         const int p = perm[r];
-        US[e] = wide ? G[(int64_t)p * k + i] : Sraw[p] * QV[(int64_t)p * len + i];
+        US[(int64_t)i * ldus + r] = wide ? G[(int64_t)p * k + i] : Sraw[p] * QV[(int64_t)p * len + i];
     }
     for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += nthreads()) {
         const int r = (int)(e / N), c = (int)(e % N);
@@ -223,7 +224,7 @@ __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, 
             const double sp = Sraw[p];
             v = sp > 0.0 ? G[(int64_t)p * k + c] / sp : 0.0;
         }
-        Vt[e] = v;
+        Vt[(int64_t)r * ldvt + c] = v;
     }
     for (int r = threadIdx.x; r < k; r += nthreads()) S[r] = Sraw[perm[r]];
     __syncthreads();
@@ -231,7 +232,7 @@ __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, 
         double best = -1.0;
         int bi = 0;
         for (int c = lane; c < N; c += 32) {
-            const double a = fabs(Vt[(int64_t)r * N + c]);
+            const double a = fabs(Vt[(int64_t)r * ldvt + c]);
             if (a > best) {
                 best = a;
                 bi = c;
@@ -245,9 +246,9 @@ __device__ __forceinline__ void svd_assemble(const double* G, const double* QV, 
                 bi = oi;
             }
         }
-        if (Vt[(int64_t)r * N + bi] < 0.0) {
-            for (int c = lane; c < N; c += 32) Vt[(int64_t)r * N + c] = -Vt[(int64_t)r * N + c];
-            for (int i = lane; i < M; i += 32) US[(int64_t)i * k + r] = -US[(int64_t)i * k + r];
+        if (Vt[(int64_t)r * ldvt + bi] < 0.0) {
+            for (int c = lane; c < N; c += 32) Vt[(int64_t)r * ldvt + c] = -Vt[(int64_t)r * ldvt + c];
+            for (int i = lane; i < M; i += 32) US[(int64_t)i * ldus + r] = -US[(int64_t)i * ldus + r];
         }
     }
 }

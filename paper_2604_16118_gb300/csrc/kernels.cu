@@ -189,7 +189,7 @@ struct SvdFin {
 
 __global__ void __launch_bounds__(kThreads) k_svd_finalize(const SvdFin* __restrict__ tasks) {
     const SvdFin tk = tasks[blockIdx.x];
-    dev::svd_assemble(tk.G, tk.QVt, tk.Sraw, tk.perm, tk.S, tk.US, tk.Vt, tk.M, tk.N, tk.k, tk.len, tk.wide);
+    dev::svd_assemble(tk.G, tk.QVt, tk.Sraw, tk.perm, tk.S, tk.US, tk.Vt, tk.M, tk.N, tk.k, tk.len, tk.wide, tk.k, tk.N);
 }
 
 __global__ void __launch_bounds__(kThreads) k_sumsq(const double* const* __restrict__ xs,

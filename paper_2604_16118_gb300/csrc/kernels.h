@@ -139,3 +139,49 @@ void launch_right_apply(Context* ctx, const std::vector<RTask>& tasks, const std
                         const std::vector<RGemm>& gemms);
 
 }  // namespace bsm
+
+namespace bsm {
+
+// ---- device-driven right sweep (no host round trip per bond) ----
+
+// One sigma part of a sector's matrix at bond b: the left-orthogonal core-b
+// block X (rows x xcols, row-major) times the kept columns of U S of bond b+1
+// (US: xcols x ldus row-major, *keep kept columns; US == nullptr: identity).
+struct DynPart {
+    const double* X;
+    int xcols;
+    const double* US;
+    int ldus;
+    const int* keep;
+};
+// One sector of bond b: SVD of [part_0 | part_1] into padded outputs
+// (S: kpad, US: rows x kpad, Vt: kpad x ncols_pad); *kact receives the rank.
+struct DynTask {
+    int M, kpad, ncols_pad;
+    int p_beg, p_end;
+    double* S;
+    double* US;
+    double* Vt;
+    int* kact;
+};
+// Cut of one bond: the singular values of its sectors (sector i: S[i] with
+// *kact[i] values) pooled and cut exactly as choose_cut; keep[i] receives the
+// kept counts, disc[0] / disc[1] accumulate the squared norms discarded by the
+// tolerance / the cap.
+struct CutSector {
+    const double* S;
+    const int* kact;
+};
+struct CutTask {
+    int n_sec, s_beg, cap_total, r_max;
+    double tol2;
+    int* keep;
+    double* disc;
+};
+size_t dyn_svd_smem(int M, int ncols_pad);
+// returns the index of its profiler record (-1 when not profiling) so that the
+// caller can enter the algorithmic flops once the ranks are known
+int launch_right_dyn(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts);
+void launch_cut(Context* ctx, const CutTask& task, const std::vector<CutSector>& secs);
+
+}  // namespace bsm

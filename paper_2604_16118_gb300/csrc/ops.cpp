@@ -264,6 +264,179 @@ std::vector<int> choose_cut(std::vector<SvEntry> sv, int n_sectors, double tol2,
     return cnt;
 }
 
+// Right sweep of trunc_eps with the cut decided on the device: every bond's
+// SVDs read the kept counts of the previous bond from device memory, so the
+// whole sweep is enqueued without a host round trip; the kept counts of all
+// bonds are read once at the end.  Returns false (nothing done) when a bond's
+// padded problem does not fit the fused kernels.
+static bool right_sweep_device(Context* ctx, Layout& L, std::vector<double*>& cores, std::vector<char>& owned,
+                               double eps, int r_max, double* td2, double* cd2) {
+    const int K = L.K;
+    if (K < 2) return false;
+    const double tol2 = eps * eps / (K - 1);
+    // padded ranks per bond (kpad[K] = 1 for the single sector of bond K)
+    std::vector<std::vector<int>> kpad(K + 1), cpad(K + 1);
+    kpad[K].assign(L.bonds[K].q.size(), 1);
+    for (int b = K - 1; b >= 1; --b) {
+        const Bond& bn = L.bonds[b];
+        kpad[b].assign(bn.q.size(), 0);
+        cpad[b].assign(bn.q.size(), 0);
+        int total = 0;
+        for (const Block& bk : L.blocks[b]) {
+            const int m = bk.ri;
+            cpad[b][bk.li] += (b + 1 == K) ? bk.cols : kpad[b + 1][m];
+        }
+        for (size_t n = 0; n < bn.q.size(); ++n) {
+            // the SVD keeps min(rows, cols) columns before the cut, so the
+            // padding is not reduced by the rank cap
+            const int kp = std::min(bn.dim[n], cpad[b][n]);
+            kpad[b][n] = kp;
+            total += kp;
+            if (kp > 96 || dyn_svd_smem(bn.dim[n], cpad[b][n]) > 220 * 1024) return false;
+            int64_t fma = 0;
+            for (const Block& bk : L.blocks[b])
+                if (bk.li == (int)n && b + 1 < K) fma += (int64_t)bk.rows * bk.cols * kpad[b + 1][bk.ri];
+            if (fma > (int64_t)1 << 20) return false;
+        }
+        if (total > 2048) return false;
+    }
+    // buffers: per bond and sector S, US (rows x kpad), Vt (kpad x cpad); kact, keep per bond
+    Scratch s(ctx);
+    std::vector<std::vector<double*>> S(K), US(K), Vt(K);
+    std::vector<int> secoff(K + 1, 0);
+    int nsec_all = 0;
+    for (int b = 1; b < K; ++b) {
+        secoff[b] = nsec_all;
+        nsec_all += (int)L.bonds[b].q.size();
+    }
+    int* ints = (int*)ctx->alloc(sizeof(int) * 2 * (size_t)std::max(nsec_all, 1));
+    s.ptrs.push_back(ints);
+    int* kact = ints;
+    int* keep = ints + nsec_all;
+    double* disc = s.dbl(2);
+    BSM_CUDA(cudaMemsetAsync(ints, 0, sizeof(int) * 2 * (size_t)std::max(nsec_all, 1), ctx->stream));
+    BSM_CUDA(cudaMemsetAsync(disc, 0, sizeof(double) * 2, ctx->stream));
+    for (int b = 1; b < K; ++b) {
+        const Bond& bn = L.bonds[b];
+        for (size_t n = 0; n < bn.q.size(); ++n) {
+            const int kp = std::max(kpad[b][n], 1), cp = std::max(cpad[b][n], 1);
+            S[b].push_back(s.dbl((size_t)kp));
+            US[b].push_back(s.dbl((size_t)bn.dim[n] * kp));
+            Vt[b].push_back(s.dbl((size_t)kp * cp));
+        }
+    }
+    std::vector<int> prof_idx;
+    for (int b = K - 1; b >= 1; --b) {
+        const Bond& bn = L.bonds[b];
+        std::vector<DynTask> tasks;
+        std::vector<DynPart> parts;
+        std::vector<std::vector<DynPart>> per(bn.q.size());
+        for (const Block& bk : L.blocks[b]) {   // layout order: sigma 0 before 1 within a sector
+            const int m = bk.ri;
+            if (b + 1 == K)
+                per[bk.li].push_back({cores[b] + bk.off, bk.cols, nullptr, 0, nullptr});
+            else
+                per[bk.li].push_back({cores[b] + bk.off, bk.cols, US[b + 1][m], std::max(kpad[b + 1][m], 1),
+                                      keep + secoff[b + 1] + m});
+        }
+        for (size_t n = 0; n < bn.q.size(); ++n) {
+            DynTask t{bn.dim[n], std::max(kpad[b][n], 1), std::max(cpad[b][n], 1), (int)parts.size(), 0,
+                      S[b][n], US[b][n], Vt[b][n], kact + secoff[b] + (int)n};
+            parts.insert(parts.end(), per[n].begin(), per[n].end());
+            t.p_end = (int)parts.size();
+            tasks.push_back(t);
+        }
+        prof_idx.push_back(launch_right_dyn(ctx, tasks, parts));
+        std::vector<CutSector> cs;
+        int cap = 0;
+        for (size_t n = 0; n < bn.q.size(); ++n) {
+            cs.push_back({S[b][n], kact + secoff[b] + (int)n});
+            cap += kpad[b][n];
+        }
+        CutTask ct{(int)bn.q.size(), 0, std::max(cap, 1), r_max, tol2, keep + secoff[b], disc};
+        launch_cut(ctx, ct, cs);
+    }
+    std::vector<int> keep_h((size_t)std::max(nsec_all, 1));
+    double disc_h[2];
+    BSM_CUDA(cudaMemcpyAsync(keep_h.data(), keep, sizeof(int) * keep_h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    BSM_CUDA(cudaMemcpyAsync(disc_h, disc, sizeof(disc_h), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    *td2 += disc_h[0];
+    *cd2 += disc_h[1];
+    // actual sizes: cols of sector n at bond b = sum of kept counts of its parts
+    auto kept = [&](int b, int m) { return b == K ? 1 : keep_h[secoff[b] + m]; };
+    double fl = 0.0;
+    std::vector<std::vector<int>> cols_act(K), coff1(K);
+    for (int b = K - 1; b >= 1; --b) {
+        const Bond& bn = L.bonds[b];
+        cols_act[b].assign(bn.q.size(), 0);
+        coff1[b].assign(bn.q.size(), 0);
+        for (const Block& bk : L.blocks[b]) {
+            const int c = (b + 1 == K) ? bk.cols : kept(b + 1, bk.ri);
+            if (bk.sigma == 0) coff1[b][bk.li] = c;
+            cols_act[b][bk.li] += c;
+            if (b + 1 < K) fl += 2.0 * bk.rows * (double)bk.cols * c;
+        }
+        for (size_t n = 0; n < bn.q.size(); ++n) {
+            const double M = bn.dim[n], N = cols_act[b][n], k = std::min(M, N), len = std::max(M, N);
+            if (k > 0)
+                fl += 2.0 * len * k * k - (len + k) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * len * k * k -
+                      2.0 / 3.0 * k * k * k + 54.0 * k * k * k + 2.0 * len * k * k;
+        }
+    }
+    ctx->flops += fl;
+    if (!prof_idx.empty() && prof_idx[0] >= 0) {
+        for (int idx : prof_idx) ctx->prof[idx].flops = 0.0;
+        ctx->prof[prof_idx[0]].flops = fl;   // attributed to the sweep's first SVD launch record
+    }
+    // compact layout and cores
+    Layout F = L;
+    for (int b = 1; b < K; ++b) {
+        Bond nb;
+        for (size_t n = 0; n < L.bonds[b].q.size(); ++n)
+            if (keep_h[secoff[b] + n] > 0) {
+                nb.q.push_back(L.bonds[b].q[n]);
+                nb.dim.push_back(keep_h[secoff[b] + n]);
+            }
+        F.bonds[b] = nb;
+    }
+    F.rebuild_blocks();
+    std::vector<double*> nc(K, nullptr);
+    for (int t = 0; t < K; ++t)
+        if (F.core_size[t] > 0) nc[t] = (double*)ctx->alloc(sizeof(double) * (size_t)F.core_size[t]);
+    std::vector<CopyTask> cp;
+    std::vector<GemmOut> go;
+    std::vector<GemmIn> gi;
+    for (int t = 0; t < K; ++t) {
+        for (const Block& fb : F.blocks[t]) {
+            const Charge qn = F.bonds[t].q[fb.li];
+            if (t == 0) {
+                // core 0: X_0 (1 x rho_1(m)) times the kept columns of U S of bond 1
+                const int m = L.bonds[1].find(F.bonds[1].q[fb.ri]);
+                const Block* ob = nullptr;
+                for (const Block& b0 : L.blocks[0])
+                    if (b0.sigma == fb.sigma) ob = &b0;
+                go.push_back({nc[0] + fb.off, fb.rows, fb.cols, fb.cols, (int)gi.size(), (int)gi.size() + 1, 0.0});
+                gi.push_back({cores[0] + ob->off, US[1][m], ob->cols, ob->cols, std::max(kpad[1][m], 1), 0, 1.0});
+            } else {
+                const int n = L.bonds[t].find(qn);
+                const int coff = fb.sigma == 0 ? 0 : coff1[t][n];
+                cp.push_back({Vt[t][n] + coff, nc[t] + fb.off, fb.rows, fb.cols, std::max(cpad[t][n], 1), fb.cols, 0,
+                              0, 0, 1.0});
+            }
+        }
+    }
+    launch_copy(ctx, cp);
+    launch_gemm(ctx, go, gi);
+    for (int t = 0; t < K; ++t) {
+        if (owned[t] && cores[t]) ctx->free(cores[t]);
+        cores[t] = nc[t];
+        owned[t] = 1;
+    }
+    L = F;
+    return true;
+}
+
 MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
                    double* disc_cap) {
     const int K = x->lay.K;
@@ -409,7 +582,8 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
     // ---- right-to-left SVD sweep ----
     const double tol2 = K > 1 ? eps * eps / (K - 1) : 0.0;
     double td2 = 0.0, cd2 = 0.0;
-    for (int t = K - 1; t >= 1; --t) {
+    const bool done_on_device = right_sweep_device(ctx, L, cores, owned, eps, r_max, &td2, &cd2);
+    for (int t = done_on_device ? 0 : K - 1; t >= 1; --t) {
         Scratch s(ctx);
         const Bond bn = L.bonds[t];   // the old bond (L is updated in place below)
         const int nn = (int)bn.q.size();

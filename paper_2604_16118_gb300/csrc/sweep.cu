@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_site(const SvdSiteTask* __rest
         B[e] = acc;
     }
     __syncthreads();
-    dev::svd_assemble(G, B, Sraw, perm, tk.S, tk.US, tk.Vt, M, N, k, len, tk.wide);
+    dev::svd_assemble(G, B, Sraw, perm, tk.S, tk.US, tk.Vt, M, N, k, len, tk.wide, k, N);
 }
 
 __global__ void __launch_bounds__(kThreads) k_right_apply(const RTask* __restrict__ tasks,
@@ -145,6 +145,159 @@ __global__ void __launch_bounds__(kThreads) k_right_apply(const RTask* __restric
             for (int q = 0; q < rg.K; ++q) acc = fma(rg.X[(int64_t)i * rg.K + q], rg.US[(int64_t)q * rg.ldus + j], acc);
             rg.dst[e] = acc;
         }
+    }
+}
+
+// Device-driven right sweep, one CTA per sector of bond b: the sector's matrix
+// is formed from the left-orthogonal core-b blocks times the kept columns of
+// the U S of bond b+1 (kept counts read from device memory), then QR, Jacobi
+// and assembly as in k_svd_site into padded outputs.
+__global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restrict__ tasks,
+                                                        const DynPart* __restrict__ parts) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ double sh[2];
+    __shared__ int s_rot;
+    __shared__ int s_cols[2];
+    const DynTask tk = tasks[blockIdx.x];
+    const int np = tk.p_end - tk.p_beg;
+    if (threadIdx.x < 2) {
+        int c = 0;
+        if ((int)threadIdx.x < np) {
+            const DynPart pt = parts[tk.p_beg + threadIdx.x];
+            c = pt.keep ? *pt.keep : pt.xcols;
+        }
+        s_cols[threadIdx.x] = c;
+    }
+    __syncthreads();
+    const int M = tk.M, N = s_cols[0] + s_cols[1];
+    if (N == 0 || M == 0) {
+        if (threadIdx.x == 0) *tk.kact = 0;
+        return;
+    }
+    const int k = M < N ? M : N, len = M < N ? N : M, wide = M < N ? 1 : 0;
+    double* B = sm;
+    double* Q = B + (int64_t)len * k;
+    double* tau = Q + (int64_t)len * k;
+    double* G = tau + k;
+    double* V = G + (int64_t)k * k;
+    double* Sraw = V + (int64_t)k * k;
+    int* perm = (int*)(Sraw + k);
+    int coff = 0;
+    for (int p = 0; p < np; ++p) {
+        const DynPart pt = parts[tk.p_beg + p];
+        const int cols = s_cols[p];
+        for (int64_t e = threadIdx.x; e < (int64_t)M * cols; e += nthreads()) {
+            const int i = (int)(e / cols), cc = (int)(e % cols), c = coff + cc;
+            double v;
+            if (pt.US) {
+                v = 0.0;
+                for (int q = 0; q < pt.xcols; ++q)
+                    v = fma(pt.X[(int64_t)i * pt.xcols + q], pt.US[(int64_t)q * pt.ldus + cc], v);
+            } else {
+                v = pt.X[(int64_t)i * pt.xcols + cc];
+            }
+            if (wide)
+                B[(int64_t)i * N + c] = v;
+            else
+                B[(int64_t)c * M + i] = v;
+        }
+        coff += cols;
+    }
+    __syncthreads();
+    dev::householder(B, tau, len, k, red, sh);
+    for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += nthreads()) {
+        const int j = (int)(e / k), i = (int)(e % k);
+        G[e] = i >= j ? B[(int64_t)i * len + j] : 0.0;
+    }
+    dev::form_q(B, tau, Q, len, k);
+    __syncthreads();
+    dev::jacobi(G, V, Sraw, k, red, &s_rot);
+    for (int64_t e = threadIdx.x; e < (int64_t)len * k; e += nthreads()) {
+        const int p = (int)(e / len), i = (int)(e % len);
+        double acc = 0.0;
+        for (int j = 0; j < k; ++j) acc = fma(Q[(int64_t)j * len + i], V[(int64_t)p * k + j], acc);
+        B[e] = acc;
+    }
+    __syncthreads();
+    dev::svd_assemble(G, B, Sraw, perm, tk.S, tk.US, tk.Vt, M, N, k, len, wide, tk.kpad, tk.ncols_pad);
+    if (threadIdx.x == 0) *tk.kact = k;
+}
+
+// Pooled cut of one bond (one CTA): stable descending order with ties by
+// (sector, index), then the sequential tolerance / cluster / cap rule; the
+// products and sums are rounded individually (no contraction) so that the
+// decisions equal the host rule.
+__global__ void __launch_bounds__(kThreads) k_cut_dyn(const CutTask* __restrict__ tptr,
+                                                      const CutSector* __restrict__ secs) {
+    extern __shared__ double sm[];
+    __shared__ int s_n;
+    const CutTask tk = *tptr;
+    double* val = sm;
+    int* sec = (int*)(val + tk.cap_total);
+    int* jj = sec + tk.cap_total;
+    int* order = jj + tk.cap_total;
+    int* off = order + tk.cap_total;   // n_sec + 1
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int i = 0; i < tk.n_sec; ++i) {
+            off[i] = o;
+            o += *secs[tk.s_beg + i].kact;
+        }
+        off[tk.n_sec] = o;
+        s_n = o;
+    }
+    __syncthreads();
+    const int n = s_n;
+    for (int i = 0; i < tk.n_sec; ++i) {
+        const int c = off[i + 1] - off[i];
+        for (int j = threadIdx.x; j < c; j += nthreads()) {
+            val[off[i] + j] = secs[tk.s_beg + i].S[j];
+            sec[off[i] + j] = i;
+            jj[off[i] + j] = j;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += nthreads()) {
+        const double se = val[e];
+        int rank = 0;
+        for (int o = 0; o < n; ++o) {
+            const double so = val[o];
+            const bool before = so > se || (so == se && (sec[o] < sec[e] || (sec[o] == sec[e] && jj[o] < jj[e])));
+            rank += before ? 1 : 0;
+        }
+        order[rank] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double rtol = 1e-10;
+        int keep = n;
+        double acc = 0.0;
+        while (keep > 0) {
+            const double sv = val[order[keep - 1]];
+            const double s2 = __dmul_rn(sv, sv);
+            if (__dadd_rn(acc, s2) <= tk.tol2) {
+                acc = __dadd_rn(acc, s2);
+                keep -= 1;
+            } else {
+                break;
+            }
+        }
+        while (keep > 0 && keep < n && val[order[keep]] >= __dmul_rn(val[order[keep - 1]], 1.0 - rtol)) keep += 1;
+        double td = 0.0;
+        for (int i = keep; i < n; ++i) td = __dadd_rn(td, __dmul_rn(val[order[i]], val[order[i]]));
+        double cd = 0.0;
+        if (tk.r_max > 0 && keep > tk.r_max) {
+            int k2 = tk.r_max;
+            while (k2 > 0 && val[order[k2]] >= __dmul_rn(val[order[k2 - 1]], 1.0 - rtol)) k2 -= 1;
+            if (k2 == 0) k2 = tk.r_max;
+            for (int i = k2; i < keep; ++i) cd = __dadd_rn(cd, __dmul_rn(val[order[i]], val[order[i]]));
+            keep = k2;
+        }
+        for (int i = 0; i < tk.n_sec; ++i) tk.keep[i] = 0;
+        for (int r = 0; r < keep; ++r) tk.keep[sec[order[r]]] += 1;
+        tk.disc[0] = __dadd_rn(tk.disc[0], td);
+        tk.disc[1] = __dadd_rn(tk.disc[1], cd);
     }
 }
 
@@ -201,6 +354,8 @@ struct Prof {
 }  // namespace
 
 bool left_site_fits(int M, int N, int64_t rx_fma) { return left_smem(M, N) <= kSweepSmem && rx_fma <= kFusedGemmMaxFma; }
+
+size_t dyn_svd_smem(int M, int ncols_pad) { return svd_smem(M, ncols_pad); }
 
 bool svd_site_fits(int M, int N) { return std::min(M, N) <= 96 && svd_smem(M, N) <= kSweepSmem; }
 
@@ -280,6 +435,49 @@ void launch_right_apply(Context* ctx, const std::vector<RTask>& tasks, const std
     allow_smem(k_right_apply);
     k_right_apply<<<(unsigned)tasks.size(), kThreads, 0, ctx->stream>>>(
         (const RTask*)(d + ot), (const RCopy*)(d + oc), (const RGemm*)(d + og));
+    count_launch(ctx);
+    pr.done();
+}
+
+}  // namespace bsm
+
+namespace bsm {
+
+int launch_right_dyn(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts) {
+    if (tasks.empty()) return -1;
+    size_t smem = 0;
+    int kmax = 1;
+    double fl = 0.0, by = 0.0;
+    for (const DynTask& t : tasks) {
+        smem = std::max(smem, svd_smem(t.M, t.ncols_pad));
+        kmax = std::max(kmax, t.kpad);
+        const double k = t.kpad, len = std::max(t.M, t.ncols_pad);
+        fl += 4.0 * len * k * k + 54.0 * k * k * k + 2.0 * len * k * k;   // nominal upper bound
+        by += 8.0 * ((double)t.M * t.ncols_pad + t.M * k + k * t.ncols_pad);
+    }
+    Pack pk;
+    const size_t ot = pk.add(tasks), op = pk.add(parts);
+    Scratch s(ctx);
+    unsigned char* d = upload_pack(s, pk);
+    Prof pr(ctx, KK_SVD, fl, by);
+    allow_smem(k_right_dyn);
+    k_right_dyn<<<(unsigned)tasks.size(), block_for(kmax), smem, ctx->stream>>>((const DynTask*)(d + ot),
+                                                                               (const DynPart*)(d + op));
+    count_launch(ctx);
+    pr.done();
+    return ctx->profiling ? (int)ctx->prof.size() - 1 : -1;
+}
+
+void launch_cut(Context* ctx, const CutTask& task, const std::vector<CutSector>& secs) {
+    Pack pk;
+    const size_t ot = pk.add(std::vector<CutTask>{task}), os = pk.add(secs);
+    Scratch s(ctx);
+    unsigned char* d = upload_pack(s, pk);
+    const size_t smem = sizeof(double) * (size_t)task.cap_total + sizeof(int) * (3 * (size_t)task.cap_total +
+                                                                                 task.n_sec + 1);
+    Prof pr(ctx, KK_SUMSQ, 0.0, 8.0 * task.cap_total);
+    allow_smem(k_cut_dyn);
+    k_cut_dyn<<<1, kThreads, smem, ctx->stream>>>((const CutTask*)(d + ot), (const CutSector*)(d + os));
     count_launch(ctx);
     pr.done();
 }
