@@ -43,6 +43,7 @@ struct GemmTile {
 };
 
 constexpr int kTile = 32;
+constexpr int kSmallGemmThreads = 128;
 
 // 32 x 32 output tile per CTA; thread (ty, tx) owns rows ty + 8 r (r < 4), column tx.
 __global__ void __launch_bounds__(kThreads) k_gemm(const GemmOut* __restrict__ outs,
@@ -78,11 +79,14 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmOut* __restrict__ o
                 Bs[kk][nn] = (gk < in.K && gn < o.N) ? in.B[(int64_t)gk * in.ldb + gn] : 0.0;
             }
             __syncthreads();
-#pragma unroll 8
-            for (int kk = 0; kk < kTile; ++kk) {
+            // only the valid part of the K chunk and the warps that own rows
+            // below M issue FP64 instructions
+            const int kk_end = min(kTile, in.K - k0);
+            for (int kk = 0; kk < kk_end; ++kk) {
                 const double b = Bs[kk][tx];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r] = fma(As[kk][ty + 8 * r], b, acc[r]);
+                for (int r = 0; r < 4; ++r)
+                    if (tl.m0 + ty + 8 * r < o.M) acc[r] = fma(As[kk][ty + 8 * r], b, acc[r]);
             }
             __syncthreads();
         }
@@ -96,6 +100,34 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmOut* __restrict__ o
             double* cp = o.C + (int64_t)gm * o.ldc + gn;
             *cp = o.beta == 0.0 ? acc[r] : o.beta * (*cp) + acc[r];
         }
+    }
+}
+
+// Small outputs (M, N <= 32): one CTA per output, one thread per output
+// element, the K loop reading A and B directly, so that no FP64 instruction is
+// spent on tile padding.
+__global__ void __launch_bounds__(kSmallGemmThreads) k_gemm_small(const GemmOut* __restrict__ outs,
+                                                                  const GemmIn* __restrict__ ins,
+                                                                  const int* __restrict__ ids) {
+    const GemmOut o = outs[ids[blockIdx.x]];
+    const int n_el = o.M * o.N;
+    for (int e = threadIdx.x; e < n_el; e += kSmallGemmThreads) {
+        const int m = e / o.N, n = e % o.N;
+        double acc = 0.0;
+        for (int c = o.beg; c < o.end; ++c) {
+            const GemmIn in = ins[c];
+            double part = 0.0;
+            if (in.transA) {
+                for (int k = 0; k < in.K; ++k)
+                    part = fma(in.A[(int64_t)k * in.lda + m], in.B[(int64_t)k * in.ldb + n], part);
+            } else {
+                for (int k = 0; k < in.K; ++k)
+                    part = fma(in.A[(int64_t)m * in.lda + k], in.B[(int64_t)k * in.ldb + n], part);
+            }
+            acc = fma(in.alpha, part, acc);
+        }
+        double* cp = o.C + (int64_t)m * o.ldc + n;
+        *cp = o.beta == 0.0 ? acc : o.beta * (*cp) + acc;
     }
 }
 
@@ -286,26 +318,38 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
     if (outs.empty()) return;
     configure_carveout();
     std::vector<GemmTile> tiles;
+    std::vector<int> small;
     double fl = 0.0, by = 0.0;
     for (int o = 0; o < (int)outs.size(); ++o) {
         const GemmOut& g = outs[o];
-        for (int m0 = 0; m0 < g.M; m0 += kTile)
-            for (int n0 = 0; n0 < g.N; n0 += kTile) tiles.push_back({o, m0, n0});
+        if (g.M <= kTile && g.N <= kTile) {
+            if (g.M > 0 && g.N > 0) small.push_back(o);
+        } else {
+            for (int m0 = 0; m0 < g.M; m0 += kTile)
+                for (int n0 = 0; n0 < g.N; n0 += kTile) tiles.push_back({o, m0, n0});
+        }
         for (int c = g.beg; c < g.end; ++c) {
             fl += 2.0 * g.M * g.N * (double)ins[c].K;
             by += 8.0 * ((double)g.M * ins[c].K + (double)ins[c].K * g.N);
         }
         by += 8.0 * g.M * (double)g.N * (g.beta == 0.0 ? 1.0 : 2.0);
     }
-    if (tiles.empty()) return;
+    if (tiles.empty() && small.empty()) return;
     ctx->flops += fl;
     Scratch s(ctx);
     GemmOut* d_o = s.up(outs);
     GemmIn* d_i = s.up(ins);
-    GemmTile* d_t = s.up(tiles);
     ProfScope ps(ctx, KK_GEMM, fl, by);
-    k_gemm<<<(unsigned)tiles.size(), kThreads, 0, ctx->stream>>>(d_o, d_i, d_t);
-    check_launch(ctx);
+    if (!small.empty()) {
+        int* d_s = s.up(small);
+        k_gemm_small<<<(unsigned)small.size(), kSmallGemmThreads, 0, ctx->stream>>>(d_o, d_i, d_s);
+        check_launch(ctx);
+    }
+    if (!tiles.empty()) {
+        GemmTile* d_t = s.up(tiles);
+        k_gemm<<<(unsigned)tiles.size(), kThreads, 0, ctx->stream>>>(d_o, d_i, d_t);
+        check_launch(ctx);
+    }
     ps.done();
 }
 

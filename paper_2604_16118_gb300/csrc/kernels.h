@@ -184,4 +184,24 @@ size_t dyn_svd_smem(int M, int ncols_pad);
 int launch_right_dyn(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts);
 void launch_cut(Context* ctx, const CutTask& task, const std::vector<CutSector>& secs);
 
+// ---- persistent sweeps (one cooperative launch per sweep) ----
+
+// Phase bookkeeping of one persistent launch (16 bytes, zeroed before the
+// launch).  err != 0 after the launch: a bounded wait gave up and the sweep's
+// outputs are invalid.
+struct GridSync {
+    unsigned int arrive, release;
+    int err, pad;
+};
+// Left sweep: phase p runs tasks[phase_beg[p] .. phase_beg[p+1]) (site p);
+// the sources of phase p > 0 are the R X outputs of phase p-1.  Returns false
+// (nothing launched) when the grid cannot be co-resident.
+bool launch_left_sweep(Context* ctx, const std::vector<LeftTask>& tasks, const std::vector<LeftSrc>& srcs,
+                       const std::vector<LeftX>& xs, const std::vector<int>& phase_beg, GridSync* gs);
+// Right sweep: phase p runs its SVD tasks, then cuts[p] on the last CTA to
+// arrive.  *prof_idx: the profiler record (-1 when not profiling).
+bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts,
+                        const std::vector<int>& phase_beg, const std::vector<CutTask>& cuts,
+                        const std::vector<CutSector>& secs, GridSync* gs, int* prof_idx);
+
 }  // namespace bsm

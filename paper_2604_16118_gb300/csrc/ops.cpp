@@ -264,13 +264,108 @@ std::vector<int> choose_cut(std::vector<SvEntry> sv, int n_sectors, double tol2,
     return cnt;
 }
 
+// Left-to-right QR sweep as one persistent launch: the new layout of every
+// site follows on the host from the sector row counts alone (rank = min(rows,
+// cols)), so all sites' tasks are planned first and the sites run as phases
+// of one cooperative kernel.  Returns false (L, cores and owned untouched)
+// when a site does not fit the fused kernel or the grid cannot be resident.
+static bool left_sweep_persistent(Context* ctx, Layout& L, std::vector<double*>& cores, std::vector<char>& owned,
+                                  GridSync* gs) {
+    const int K = L.K;
+    if (K < 2) return false;
+    Layout P = L;
+    std::vector<double*> pc = cores;
+    std::vector<char> po = owned;
+    std::vector<double*> fresh, deferred;
+    std::vector<LeftTask> lt;
+    std::vector<LeftSrc> ls;
+    std::vector<LeftX> lx;
+    std::vector<int> phase_beg{0};
+    auto abandon = [&]() {
+        for (double* q : fresh) ctx->free(q);
+        return false;
+    };
+    for (int t = 0; t + 1 < K; ++t) {
+        const Bond bm = P.bonds[t + 1];
+        const int nm = (int)bm.q.size();
+        std::vector<int> Mrows(nm, 0), krank(nm, 0);
+        std::vector<std::vector<std::pair<int, int>>> stack(nm);
+        for (int bi = 0; bi < (int)P.blocks[t].size(); ++bi) {
+            const Block& bk = P.blocks[t][bi];
+            stack[bk.ri].push_back({bi, Mrows[bk.ri]});
+            Mrows[bk.ri] += bk.rows;
+        }
+        const std::vector<int> oldlook = block_lookup(P, t + 1);
+        const std::vector<Block> oldB_t = P.blocks[t], oldB_t1 = P.blocks[t + 1];
+        Bond nb;
+        for (int mi = 0; mi < nm; ++mi) {
+            if (Mrows[mi] > 0) krank[mi] = std::min(Mrows[mi], bm.dim[mi]);
+            if (krank[mi] > 0) {
+                nb.q.push_back(bm.q[mi]);
+                nb.dim.push_back(krank[mi]);
+            }
+        }
+        for (int mi = 0; mi < nm; ++mi) {
+            if (Mrows[mi] == 0) continue;
+            int64_t rx = 0;
+            for (int sg = 0; sg < 2; ++sg) {
+                const int ob = oldlook[mi * 2 + sg];
+                if (ob >= 0) rx += (int64_t)krank[mi] * bm.dim[mi] * oldB_t1[ob].cols;
+            }
+            if (!left_site_fits(Mrows[mi], bm.dim[mi], rx)) return abandon();
+        }
+        P.bonds[t + 1] = nb;
+        rebuild_site(P, t);
+        rebuild_site(P, t + 1);
+        double* nt = P.core_size[t] > 0 ? (double*)ctx->alloc(sizeof(double) * (size_t)P.core_size[t]) : nullptr;
+        double* nt1 =
+            P.core_size[t + 1] > 0 ? (double*)ctx->alloc(sizeof(double) * (size_t)P.core_size[t + 1]) : nullptr;
+        if (nt) fresh.push_back(nt);
+        if (nt1) fresh.push_back(nt1);
+        const std::vector<int> newlook_t = block_lookup(P, t);
+        for (int mi = 0; mi < nm; ++mi) {
+            if (Mrows[mi] == 0) continue;
+            const int nmi = P.bonds[t + 1].find(bm.q[mi]);
+            LeftTask task{Mrows[mi], bm.dim[mi], krank[mi], (int)ls.size(), 0, (int)lx.size(), 0};
+            for (auto& pr : stack[mi]) {
+                const Block& ob = oldB_t[pr.first];
+                const Block& nbk = P.blocks[t][newlook_t[ob.li * 2 + ob.sigma]];
+                ls.push_back({pc[t] + ob.off, nt + nbk.off, ob.rows, pr.second});
+            }
+            task.s_end = (int)ls.size();
+            for (const Block& nbk : P.blocks[t + 1]) {
+                if (nbk.li != nmi) continue;
+                const Block& ob = oldB_t1[oldlook[mi * 2 + nbk.sigma]];
+                lx.push_back({pc[t + 1] + ob.off, nt1 + nbk.off, ob.cols});
+            }
+            task.x_end = (int)lx.size();
+            lt.push_back(task);
+        }
+        phase_beg.push_back((int)lt.size());
+        for (int u : {t, t + 1}) {
+            if (po[u] && pc[u]) deferred.push_back(pc[u]);
+        }
+        pc[t] = nt;
+        po[t] = 1;
+        pc[t + 1] = nt1;
+        po[t + 1] = 1;
+    }
+    if (!launch_left_sweep(ctx, lt, ls, lx, phase_beg, gs)) return abandon();
+    // the intermediate R X cores and the replaced cores are released behind the launch
+    for (double* q : deferred) ctx->free(q);
+    L = P;
+    cores = pc;
+    owned = po;
+    return true;
+}
+
 // Right sweep of trunc_eps with the cut decided on the device: every bond's
 // SVDs read the kept counts of the previous bond from device memory, so the
 // whole sweep is enqueued without a host round trip; the kept counts of all
 // bonds are read once at the end.  Returns false (nothing done) when a bond's
 // padded problem does not fit the fused kernels.
 static bool right_sweep_device(Context* ctx, Layout& L, std::vector<double*>& cores, std::vector<char>& owned,
-                               double eps, int r_max, double* td2, double* cd2) {
+                               double eps, int r_max, double* td2, double* cd2, GridSync* gs, bool* gs_checked) {
     const int K = L.K;
     if (K < 2) return false;
     const double tol2 = eps * eps / (K - 1);
@@ -325,11 +420,14 @@ static bool right_sweep_device(Context* ctx, Layout& L, std::vector<double*>& co
             Vt[b].push_back(s.dbl((size_t)kp * cp));
         }
     }
-    std::vector<int> prof_idx;
+    // all bonds' tasks in sweep order (phase p = bond K-1-p)
+    std::vector<DynTask> tasks;
+    std::vector<DynPart> parts;
+    std::vector<CutTask> cuts;
+    std::vector<CutSector> secs;
+    std::vector<int> phase_beg{0};
     for (int b = K - 1; b >= 1; --b) {
         const Bond& bn = L.bonds[b];
-        std::vector<DynTask> tasks;
-        std::vector<DynPart> parts;
         std::vector<std::vector<DynPart>> per(bn.q.size());
         for (const Block& bk : L.blocks[b]) {   // layout order: sigma 0 before 1 within a sector
             const int m = bk.ri;
@@ -346,21 +444,35 @@ static bool right_sweep_device(Context* ctx, Layout& L, std::vector<double*>& co
             t.p_end = (int)parts.size();
             tasks.push_back(t);
         }
-        prof_idx.push_back(launch_right_dyn(ctx, tasks, parts));
-        std::vector<CutSector> cs;
+        phase_beg.push_back((int)tasks.size());
+        const int s_beg = (int)secs.size();
         int cap = 0;
         for (size_t n = 0; n < bn.q.size(); ++n) {
-            cs.push_back({S[b][n], kact + secoff[b] + (int)n});
+            secs.push_back({S[b][n], kact + secoff[b] + (int)n});
             cap += kpad[b][n];
         }
-        CutTask ct{(int)bn.q.size(), 0, std::max(cap, 1), r_max, tol2, keep + secoff[b], disc};
-        launch_cut(ctx, ct, cs);
+        cuts.push_back({(int)bn.q.size(), s_beg, std::max(cap, 1), r_max, tol2, keep + secoff[b], disc});
+    }
+    std::vector<int> prof_idx(1, -1);
+    if (!launch_right_sweep(ctx, tasks, parts, phase_beg, cuts, secs, gs + 1, &prof_idx[0])) {
+        // grid not co-resident: one SVD launch and one cut launch per bond
+        prof_idx.clear();
+        for (size_t p = 0; p + 1 < phase_beg.size(); ++p) {
+            std::vector<DynTask> tp(tasks.begin() + phase_beg[p], tasks.begin() + phase_beg[p + 1]);
+            prof_idx.push_back(launch_right_dyn(ctx, tp, parts));
+            launch_cut(ctx, cuts[p], secs);
+        }
     }
     std::vector<int> keep_h((size_t)std::max(nsec_all, 1));
     double disc_h[2];
+    GridSync gs_h[2];
     BSM_CUDA(cudaMemcpyAsync(keep_h.data(), keep, sizeof(int) * keep_h.size(), cudaMemcpyDeviceToHost, ctx->stream));
     BSM_CUDA(cudaMemcpyAsync(disc_h, disc, sizeof(disc_h), cudaMemcpyDeviceToHost, ctx->stream));
+    BSM_CUDA(cudaMemcpyAsync(gs_h, gs, sizeof(gs_h), cudaMemcpyDeviceToHost, ctx->stream));
     ctx->sync();
+    BSM_REQUIRE(gs_h[0].err == 0 && gs_h[1].err == 0, BSMPS_ERR_TIMEOUT,
+                "truncation sweep: a grid-wide wait gave up");
+    *gs_checked = true;
     *td2 += disc_h[0];
     *cd2 += disc_h[1];
     // actual sizes: cols of sector n at bond b = sum of kept counts of its parts
@@ -463,8 +575,17 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         return n > 0 ? (double*)ctx->alloc((size_t)n * sizeof(double)) : nullptr;
     };
 
+    // phase bookkeeping of the two persistent sweeps; err is read back with
+    // the right sweep's cut results (or at the end when that path is not taken)
+    Scratch gs_scratch(ctx);
+    GridSync* gs = (GridSync*)ctx->alloc(2 * sizeof(GridSync));
+    gs_scratch.ptrs.push_back(gs);
+    BSM_CUDA(cudaMemsetAsync(gs, 0, 2 * sizeof(GridSync), ctx->stream));
+    bool gs_checked = false;
+
     // ---- left-to-right QR sweep ----
-    for (int t = 0; t + 1 < K; ++t) {
+    const bool left_done = left_sweep_persistent(ctx, L, cores, owned, gs);
+    for (int t = left_done ? K : 0; t + 1 < K; ++t) {
         Scratch s(ctx);
         const Bond bm = L.bonds[t + 1];   // the old bond (L is updated in place below)
         const int nm = (int)bm.q.size();
@@ -582,7 +703,7 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
     // ---- right-to-left SVD sweep ----
     const double tol2 = K > 1 ? eps * eps / (K - 1) : 0.0;
     double td2 = 0.0, cd2 = 0.0;
-    const bool done_on_device = right_sweep_device(ctx, L, cores, owned, eps, r_max, &td2, &cd2);
+    const bool done_on_device = right_sweep_device(ctx, L, cores, owned, eps, r_max, &td2, &cd2, gs, &gs_checked);
     for (int t = done_on_device ? 0 : K - 1; t >= 1; --t) {
         Scratch s(ctx);
         const Bond bn = L.bonds[t];   // the old bond (L is updated in place below)
@@ -747,6 +868,12 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         owned[t] = 1;
         cores[t - 1] = ntm;
         owned[t - 1] = 1;
+    }
+    if (left_done && !gs_checked) {
+        GridSync h;
+        BSM_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->sync();
+        BSM_REQUIRE(h.err == 0, BSMPS_ERR_TIMEOUT, "left truncation sweep: a grid-wide wait gave up");
     }
     if (disc_tol) *disc_tol = std::sqrt(td2);
     if (disc_cap) *disc_cap = std::sqrt(cd2);

@@ -4,6 +4,7 @@
 // around the host's cut decision (right sweep).
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "dense_dev.cuh"
 #include "kernels.h"
@@ -28,13 +29,62 @@ size_t svd_smem(int M, int N) {
     return sizeof(double) * (2 * len * k + 2 * k * k + 3 * k);
 }
 
-__global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restrict__ tasks,
-                                                        const LeftSrc* __restrict__ srcs,
-                                                        const LeftX* __restrict__ xs) {
-    extern __shared__ double sm[];
-    __shared__ double red[33];
-    __shared__ double sh[2];
-    const LeftTask tk = tasks[blockIdx.x];
+// Global loads of data that other CTAs of the same launch may have written
+// (persistent sweeps) go through L2; the per-site kernels use plain loads.
+template <bool CG>
+__device__ __forceinline__ double ldd(const double* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+template <bool CG>
+__device__ __forceinline__ int ldi(const int* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// One sector stack of a left-sweep site: gather, Householder QR with
+// diag(R) >= 0, Q scattered to the new core t, R X written to the new core t+1.
+// Rank-1 sector stack of the left sweep (A: M x N column-major, min(M, N) = 1)
+// in closed form, diag(R) >= 0 as in the general path: a column x gives
+// Q = x / ||x||, R = ||x|| (Q = e_0, R = 0 for x = 0); a row x gives Q = [sgn],
+// R = sgn x with sgn = -1 exactly when x_0 < 0.
+template <bool CG>
+__device__ void left_rank1(const LeftTask& tk, const LeftSrc* __restrict__ srcs, const LeftX* __restrict__ xs,
+                           const double* A, double* red) {
+    const int M = tk.M, N = tk.N;
+    if (N == 1) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < M; i += nthreads()) s = fma(A[i], A[i], s);
+        s = dev::block_sum(s, red);
+        const double r = sqrt(s);
+        const double f = r > 0.0 ? 1.0 / r : 0.0;
+        for (int si = tk.s_beg; si < tk.s_end; ++si) {
+            const LeftSrc sr = srcs[si];
+            for (int i = threadIdx.x; i < sr.rows; i += nthreads())
+                sr.dst[i] = r > 0.0 ? A[sr.r0 + i] * f : (sr.r0 + i == 0 ? 1.0 : 0.0);
+        }
+        for (int x = tk.x_beg; x < tk.x_end; ++x) {
+            const LeftX lx = xs[x];
+            for (int c = threadIdx.x; c < lx.cols; c += nthreads()) lx.dst[c] = r * ldd<CG>(lx.X + c);
+        }
+        return;
+    }
+    // M == 1: one row of N entries
+    const double sgn = A[0] < 0.0 ? -1.0 : 1.0;
+    if (threadIdx.x == 0) srcs[tk.s_beg].dst[0] = sgn;
+    for (int x = tk.x_beg; x < tk.x_end; ++x) {
+        const LeftX lx = xs[x];
+        for (int c = threadIdx.x; c < lx.cols; c += nthreads()) {
+            double acc = 0.0;
+            for (int j = 0; j < N; ++j) acc = fma(sgn * A[(int64_t)j], ldd<CG>(lx.X + (int64_t)j * lx.cols + c), acc);
+            lx.dst[c] = acc;
+        }
+    }
+}
+
+template <bool CG>
+__device__ void left_body(const LeftTask& tk, const LeftSrc* __restrict__ srcs, const LeftX* __restrict__ xs,
+                          double* sm, double* red, double* sh) {
     const int M = tk.M, N = tk.N, k = tk.k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* A = sm;
@@ -45,10 +95,14 @@ __global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restri
         const LeftSrc sr = srcs[s];
         for (int64_t e = threadIdx.x; e < (int64_t)sr.rows * N; e += nthreads()) {
             const int i = (int)(e / N), c = (int)(e % N);
-            A[(int64_t)c * M + sr.r0 + i] = sr.src[e];
+            A[(int64_t)c * M + sr.r0 + i] = ldd<CG>(sr.src + e);
         }
     }
     __syncthreads();
+    if (k == 1) {
+        left_rank1<CG>(tk, srcs, xs, A, red);
+        return;
+    }
     dev::householder(A, tau, M, N, red, sh);
     for (int64_t e = threadIdx.x; e < (int64_t)k * N; e += nthreads()) {
         const int r = (int)(e / N), c = (int)(e % N);
@@ -75,10 +129,19 @@ __global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restri
         for (int64_t e = threadIdx.x; e < (int64_t)k * lx.cols; e += nthreads()) {
             const int r = (int)(e / lx.cols), c = (int)(e % lx.cols);
             double acc = 0.0;
-            for (int j = r; j < N; ++j) acc = fma(R[(int64_t)r * N + j], lx.X[(int64_t)j * lx.cols + c], acc);
+            for (int j = r; j < N; ++j) acc = fma(R[(int64_t)r * N + j], ldd<CG>(lx.X + (int64_t)j * lx.cols + c), acc);
             lx.dst[e] = acc;
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restrict__ tasks,
+                                                        const LeftSrc* __restrict__ srcs,
+                                                        const LeftX* __restrict__ xs) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ double sh[2];
+    left_body<false>(tasks[blockIdx.x], srcs, xs, sm, red, sh);
 }
 
 __global__ void __launch_bounds__(kThreads) k_svd_site(const SvdSiteTask* __restrict__ tasks,
@@ -152,20 +215,88 @@ __global__ void __launch_bounds__(kThreads) k_right_apply(const RTask* __restric
 // is formed from the left-orthogonal core-b blocks times the kept columns of
 // the U S of bond b+1 (kept counts read from device memory), then QR, Jacobi
 // and assembly as in k_svd_site into padded outputs.
-__global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restrict__ tasks,
-                                                        const DynPart* __restrict__ parts) {
-    extern __shared__ double sm[];
-    __shared__ double red[33];
-    __shared__ double sh[2];
-    __shared__ int s_rot;
-    __shared__ int s_cols[2];
-    const DynTask tk = tasks[blockIdx.x];
+// Index of the largest |v[c]|, c < n (ties: the smallest index), known to
+// every thread.  red: 33 shared doubles.
+__device__ __forceinline__ int block_argmax_abs(const double* v, int n, double* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double best = -1.0;
+    int bi = 0;
+    for (int c = threadIdx.x; c < n; c += nthreads()) {
+        const double a = fabs(v[c]);
+        if (a > best) {
+            best = a;
+            bi = c;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        red[w] = best;
+        red[16 + w] = (double)bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = red[0];
+        int i = (int)red[16];
+        for (int u = 1; u < nwarps(); ++u) {
+            const int ui = (int)red[16 + u];
+            if (red[u] > b || (red[u] == b && ui < i)) {
+                b = red[u];
+                i = ui;
+            }
+        }
+        red[32] = (double)i;
+    }
+    __syncthreads();
+    return (int)red[32];
+}
+
+// Rank-1 sector of the right sweep (a single row or column v, length len):
+// the SVD in closed form with the conventions of the general path.  A column
+// (M x 1) gives US = v, Vt = [1]; a row (1 x N) gives Vt = sgn v / sigma and
+// US = sgn sigma, sgn making the largest |entry| of the Vt row positive.  A
+// zero vector gives S = 0 (a value every cut discards).
+__device__ void right_rank1(const DynTask& tk, const double* v, int len, int wide, double* red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += nthreads()) s = fma(v[i], v[i], s);
+    s = dev::block_sum(s, red);
+    const double sigma = sqrt(s);
+    if (!wide) {
+        for (int i = threadIdx.x; i < len; i += nthreads()) tk.US[(int64_t)i * tk.kpad] = sigma > 0.0 ? v[i] : 0.0;
+        if (threadIdx.x == 0) {
+            tk.Vt[0] = sigma > 0.0 ? 1.0 : 0.0;
+            tk.S[0] = sigma;
+            *tk.kact = 1;
+        }
+        return;
+    }
+    const int im = block_argmax_abs(v, len, red);
+    const double sgn = v[im] < 0.0 ? -1.0 : 1.0;
+    const double f = sigma > 0.0 ? sgn / sigma : 0.0;
+    for (int c = threadIdx.x; c < len; c += nthreads()) tk.Vt[c] = sigma > 0.0 ? v[c] * f : (c == 0 ? 1.0 : 0.0);
+    if (threadIdx.x == 0) {
+        tk.US[0] = sgn * sigma;
+        tk.S[0] = sigma;
+        *tk.kact = 1;
+    }
+}
+
+template <bool CG>
+__device__ void right_body(const DynTask& tk, const DynPart* __restrict__ parts, double* sm, double* red,
+                           double* sh, int* s_rot, int* s_cols) {
     const int np = tk.p_end - tk.p_beg;
     if (threadIdx.x < 2) {
         int c = 0;
         if ((int)threadIdx.x < np) {
             const DynPart pt = parts[tk.p_beg + threadIdx.x];
-            c = pt.keep ? *pt.keep : pt.xcols;
+            c = pt.keep ? ldi<CG>(pt.keep) : pt.xcols;
         }
         s_cols[threadIdx.x] = c;
     }
@@ -193,9 +324,9 @@ __global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restric
             if (pt.US) {
                 v = 0.0;
                 for (int q = 0; q < pt.xcols; ++q)
-                    v = fma(pt.X[(int64_t)i * pt.xcols + q], pt.US[(int64_t)q * pt.ldus + cc], v);
+                    v = fma(ldd<CG>(pt.X + (int64_t)i * pt.xcols + q), ldd<CG>(pt.US + (int64_t)q * pt.ldus + cc), v);
             } else {
-                v = pt.X[(int64_t)i * pt.xcols + cc];
+                v = ldd<CG>(pt.X + (int64_t)i * pt.xcols + cc);
             }
             if (wide)
                 B[(int64_t)i * N + c] = v;
@@ -205,6 +336,23 @@ __global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restric
         coff += cols;
     }
     __syncthreads();
+    if (k == 1) {
+        right_rank1(tk, B, len, wide, red);
+        return;
+    }
+    if (len <= 32 && k <= 16) {
+        // small sector: one-sided Jacobi directly on B (no QR step)
+        double* Vd = B + (int64_t)len * k;
+        double* Sr = Vd + (int64_t)k * k;
+        double* rinv = Sr + k;
+        int* prm = (int*)(rinv + k);
+        dev::jacobi_direct(B, Vd, Sr, len, k, red, s_rot);
+        dev::svd_assemble_direct(B, Vd, Sr, rinv, prm, tk.S, tk.US, tk.Vt, M, N, k, len, wide, tk.kpad,
+                                 tk.ncols_pad);
+        __syncthreads();
+        if (threadIdx.x == 0) *tk.kact = k;
+        return;
+    }
     dev::householder(B, tau, len, k, red, sh);
     for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += nthreads()) {
         const int j = (int)(e / k), i = (int)(e % k);
@@ -212,7 +360,7 @@ __global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restric
     }
     dev::form_q(B, tau, Q, len, k);
     __syncthreads();
-    dev::jacobi(G, V, Sraw, k, red, &s_rot);
+    dev::jacobi(G, V, Sraw, k, red, s_rot);
     for (int64_t e = threadIdx.x; e < (int64_t)len * k; e += nthreads()) {
         const int p = (int)(e / len), i = (int)(e % len);
         double acc = 0.0;
@@ -224,15 +372,23 @@ __global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restric
     if (threadIdx.x == 0) *tk.kact = k;
 }
 
+__global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restrict__ tasks,
+                                                        const DynPart* __restrict__ parts) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ double sh[2];
+    __shared__ int s_rot;
+    __shared__ int s_cols[2];
+    right_body<false>(tasks[blockIdx.x], parts, sm, red, sh, &s_rot, s_cols);
+}
+
 // Pooled cut of one bond (one CTA): stable descending order with ties by
 // (sector, index), then the sequential tolerance / cluster / cap rule; the
 // products and sums are rounded individually (no contraction) so that the
 // decisions equal the host rule.
-__global__ void __launch_bounds__(kThreads) k_cut_dyn(const CutTask* __restrict__ tptr,
-                                                      const CutSector* __restrict__ secs) {
-    extern __shared__ double sm[];
-    __shared__ int s_n;
-    const CutTask tk = *tptr;
+template <bool CG>
+__device__ void cut_body(const CutTask& tk, const CutSector* __restrict__ secs, double* sm, int* s_n_ptr) {
+    int& s_n = *s_n_ptr;
     double* val = sm;
     int* sec = (int*)(val + tk.cap_total);
     int* jj = sec + tk.cap_total;
@@ -242,7 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_cut_dyn(const CutTask* __restrict_
         int o = 0;
         for (int i = 0; i < tk.n_sec; ++i) {
             off[i] = o;
-            o += *secs[tk.s_beg + i].kact;
+            o += ldi<CG>(secs[tk.s_beg + i].kact);
         }
         off[tk.n_sec] = o;
         s_n = o;
@@ -252,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_cut_dyn(const CutTask* __restrict_
     for (int i = 0; i < tk.n_sec; ++i) {
         const int c = off[i + 1] - off[i];
         for (int j = threadIdx.x; j < c; j += nthreads()) {
-            val[off[i] + j] = secs[tk.s_beg + i].S[j];
+            val[off[i] + j] = ldd<CG>(secs[tk.s_beg + i].S + j);
             sec[off[i] + j] = i;
             jj[off[i] + j] = j;
         }
@@ -299,6 +455,115 @@ __global__ void __launch_bounds__(kThreads) k_cut_dyn(const CutTask* __restrict_
         tk.disc[0] = __dadd_rn(tk.disc[0], td);
         tk.disc[1] = __dadd_rn(tk.disc[1], cd);
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_cut_dyn(const CutTask* __restrict__ tptr,
+                                                      const CutSector* __restrict__ secs) {
+    extern __shared__ double sm[];
+    __shared__ int s_n;
+    cut_body<false>(*tptr, secs, sm, &s_n);
+}
+
+// ---- persistent sweeps: one cooperative launch per sweep ----
+//
+// Every CTA of the grid is resident (cooperative launch), the sites are
+// phases, and a phase ends when all CTAs have arrived; the last CTA to arrive
+// runs the phase's serial tail (the pooled cut of the right sweep) before it
+// releases the others.  Waits are bounded by the global timer: a CTA that
+// waits longer than kWaitLimitNs sets gs->err and every CTA returns.
+
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Phase p ends; `tail` runs on the last CTA to arrive.  False: give up.
+template <class F>
+__device__ bool phase_end(GridSync* gs, unsigned int p, int* s_flag, F&& tail) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int t = atomicAdd(&gs->arrive, 1u);
+        *s_flag = (t == (p + 1) * gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*s_flag == 1) {
+        __threadfence();
+        tail();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(&gs->release, p + 1);
+        }
+        __syncthreads();
+        return true;
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = global_ns();
+        int ok = 1;
+        for (;;) {
+            if (*(volatile unsigned int*)&gs->release >= p + 1) break;
+            if (*(volatile int*)&gs->err) {
+                ok = 0;
+                break;
+            }
+            if (global_ns() - t0 > kWaitLimitNs) {
+                atomicExch(&gs->err, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(40);
+        }
+        __threadfence();
+        *s_flag = ok ? 2 : 3;
+    }
+    __syncthreads();
+    return *s_flag == 2;
+}
+
+__global__ void __launch_bounds__(kThreads) k_left_sweep(const LeftTask* __restrict__ tasks,
+                                                         const LeftSrc* __restrict__ srcs,
+                                                         const LeftX* __restrict__ xs,
+                                                         const int* __restrict__ phase_beg, int n_phase,
+                                                         GridSync* gs) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ double sh[2];
+    __shared__ int s_flag;
+    for (int p = 0; p < n_phase; ++p) {
+        for (int ti = phase_beg[p] + (int)blockIdx.x; ti < phase_beg[p + 1]; ti += (int)gridDim.x) {
+            __syncthreads();
+            left_body<true>(tasks[ti], srcs, xs, sm, red, sh);
+        }
+        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag, [] {})) return;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_right_sweep(const DynTask* __restrict__ tasks,
+                                                          const DynPart* __restrict__ parts,
+                                                          const int* __restrict__ phase_beg,
+                                                          const CutTask* __restrict__ cuts,
+                                                          const CutSector* __restrict__ secs, int n_phase,
+                                                          GridSync* gs) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ double sh[2];
+    __shared__ int s_rot;
+    __shared__ int s_cols[2];
+    __shared__ int s_n;
+    __shared__ int s_flag;
+    for (int p = 0; p < n_phase; ++p) {
+        for (int ti = phase_beg[p] + (int)blockIdx.x; ti < phase_beg[p + 1]; ti += (int)gridDim.x) {
+            __syncthreads();
+            right_body<true>(tasks[ti], parts, sm, red, sh, &s_rot, s_cols);
+        }
+        const CutTask ct = cuts[p];
+        if (!phase_end(gs, (unsigned)p, &s_flag, [&] { cut_body<true>(ct, secs, sm, &s_n); })) return;
+    }
 }
 
 // All task arrays of one launch in one upload.
@@ -322,15 +587,27 @@ unsigned char* upload_pack(Scratch& s, const Pack& p) {
 // Warps per CTA: one per Jacobi pair of the largest problem, between 1 and 8.
 int block_for(int kmax) { return 32 * std::max(1, std::min(8, (kmax + 1) / 2)); }
 
+// The attributes are per function and per process: set them once per kernel.
 template <class F>
 void allow_smem(F* kern) {
-    static bool done = false;   // set once per process (the attributes are per function)
-    if (!done) {
-        BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem));
-        BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared));
-        done = true;
-    }
+    static std::mutex mu;
+    static std::vector<const void*> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), (const void*)kern) != done.end()) return;
+    BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmem));
+    BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
+    done.push_back((const void*)kern);
+}
+
+// Largest grid of `kern` whose CTAs are all resident at once (0: none).
+template <class F>
+int coresident_ctas(F* kern, int threads, size_t smem) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    BSM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    BSM_CUDA(cudaGetDevice(&dev));
+    BSM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    return per_sm * nsm;
 }
 
 void count_launch(Context* ctx) {
@@ -480,6 +757,95 @@ void launch_cut(Context* ctx, const CutTask& task, const std::vector<CutSector>&
     k_cut_dyn<<<1, kThreads, smem, ctx->stream>>>((const CutTask*)(d + ot), (const CutSector*)(d + os));
     count_launch(ctx);
     pr.done();
+}
+
+bool launch_left_sweep(Context* ctx, const std::vector<LeftTask>& tasks, const std::vector<LeftSrc>& srcs,
+                       const std::vector<LeftX>& xs, const std::vector<int>& phase_beg, GridSync* gs) {
+    const int n_phase = (int)phase_beg.size() - 1;
+    if (n_phase <= 0 || tasks.empty()) return false;
+    size_t smem = 0;
+    int kmax = 1, maxt = 1;
+    double fl = 0.0, by = 0.0;
+    for (const LeftTask& t : tasks) {
+        smem = std::max(smem, left_smem(t.M, t.N));
+        kmax = std::max(kmax, 2 * t.k);
+        const double m = t.M, n = t.N, k = t.k;
+        fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;
+        by += 8.0 * (m * n + m * k);
+        for (int x = t.x_beg; x < t.x_end; ++x) {
+            fl += 2.0 * k * n * xs[x].cols;
+            by += 8.0 * (n + k) * xs[x].cols;
+        }
+    }
+    for (int p = 0; p < n_phase; ++p) maxt = std::max(maxt, phase_beg[p + 1] - phase_beg[p]);
+    const int threads = block_for(kmax);
+    allow_smem(k_left_sweep);
+    const int cap = coresident_ctas(k_left_sweep, threads, smem);
+    if (cap <= 0) return false;
+    const int grid = std::min(maxt, cap);
+    ctx->flops += fl;
+    Pack pk;
+    const size_t ot = pk.add(tasks), os = pk.add(srcs), ox = pk.add(xs), op = pk.add(phase_beg);
+    Scratch s(ctx);
+    unsigned char* d = upload_pack(s, pk);
+    const LeftTask* a0 = (const LeftTask*)(d + ot);
+    const LeftSrc* a1 = (const LeftSrc*)(d + os);
+    const LeftX* a2 = (const LeftX*)(d + ox);
+    const int* a3 = (const int*)(d + op);
+    int a4 = n_phase;
+    GridSync* a5 = gs;
+    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5};
+    Prof pr(ctx, KK_QR, fl, by);
+    BSM_CUDA(cudaLaunchCooperativeKernel((const void*)k_left_sweep, dim3(grid), dim3(threads), args, smem,
+                                         ctx->stream));
+    count_launch(ctx);
+    pr.done();
+    return true;
+}
+
+bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts,
+                        const std::vector<int>& phase_beg, const std::vector<CutTask>& cuts,
+                        const std::vector<CutSector>& secs, GridSync* gs, int* prof_idx) {
+    *prof_idx = -1;
+    const int n_phase = (int)phase_beg.size() - 1;
+    if (n_phase <= 0 || (int)cuts.size() != n_phase) return false;
+    size_t smem = 0;
+    int kmax = 1, maxt = 1;
+    double by = 0.0;
+    for (const DynTask& t : tasks) {
+        smem = std::max(smem, svd_smem(t.M, t.ncols_pad));
+        kmax = std::max(kmax, t.kpad);
+        by += 8.0 * ((double)t.M * t.ncols_pad + (double)t.M * t.kpad + (double)t.kpad * t.ncols_pad);
+    }
+    for (const CutTask& c : cuts)
+        smem = std::max(smem, sizeof(double) * (size_t)c.cap_total +
+                                  sizeof(int) * (3 * (size_t)c.cap_total + c.n_sec + 1));
+    for (int p = 0; p < n_phase; ++p) maxt = std::max(maxt, phase_beg[p + 1] - phase_beg[p]);
+    const int threads = block_for(kmax);
+    allow_smem(k_right_sweep);
+    const int cap = coresident_ctas(k_right_sweep, threads, smem);
+    if (cap <= 0) return false;
+    const int grid = std::min(maxt, cap);
+    Pack pk;
+    const size_t ot = pk.add(tasks), opa = pk.add(parts), oph = pk.add(phase_beg), oc = pk.add(cuts),
+                 os = pk.add(secs);
+    Scratch s(ctx);
+    unsigned char* d = upload_pack(s, pk);
+    const DynTask* a0 = (const DynTask*)(d + ot);
+    const DynPart* a1 = (const DynPart*)(d + opa);
+    const int* a2 = (const int*)(d + oph);
+    const CutTask* a3 = (const CutTask*)(d + oc);
+    const CutSector* a4 = (const CutSector*)(d + os);
+    int a5 = n_phase;
+    GridSync* a6 = gs;
+    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+    Prof pr(ctx, KK_SVD, 0.0, by);   // flops entered by the caller once the ranks are known
+    BSM_CUDA(cudaLaunchCooperativeKernel((const void*)k_right_sweep, dim3(grid), dim3(threads), args, smem,
+                                         ctx->stream));
+    count_launch(ctx);
+    pr.done();
+    if (ctx->profiling) *prof_idx = (int)ctx->prof.size() - 1;
+    return true;
 }
 
 }  // namespace bsm
