@@ -214,8 +214,20 @@ __device__ __forceinline__ void form_q(const double* A, const double* tau, doubl
 }
 
 __device__ __forceinline__ int rr_player(int pos, int round, int n2) {
-    return pos == 0 ? 0 : ((pos - 1 + round) % (n2 - 1)) + 1;
+    if (pos == 0) return 0;
+    int v = pos - 1 + round;   // < 2 (n2 - 1) for round < n2 - 1
+    if (v >= n2 - 1) v -= n2 - 1;
+    return v + 1;
 }
+
+// Order of non-negative doubles through their bit patterns (integer compares
+// instead of FP64 ones).
+__device__ __forceinline__ long long nonneg_key(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long abs_key(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+
+// sqrt(x) for x >= 0 from one reciprocal square root (about 2/3 of the cost of
+// an FP64 square root here); 1 ulp-level accuracy.
+__device__ __forceinline__ double sqrt_via_rsqrt(double x) { return x > 0.0 ? x * rsqrt(x) : 0.0; }
 
 // Rotation (c, s) that makes the columns with squared norms a, b and inner
 // product g orthogonal: with d = b - a, t = sign(zeta) 2|g| / (|d| + sqrt(d^2
@@ -230,12 +242,11 @@ __device__ __forceinline__ void jacobi_rotation(double a, double b, double g, do
     *s = *c * t;
 }
 
-// jacobi_rotation() with the angle taken in FP32 and (c, s) made orthonormal
-// in FP64: d = b - a and 2g are scaled by a power of two (the larger magnitude
-// into [1, 2)), t is formed in FP32, and two Newton steps h = (3 - (c^2 +
-// s^2))/2, (c, s) <- h (c, s) bring c^2 + s^2 to 1 within FP64 rounding.  The
-// rotation is then exactly orthogonal in FP64 and only its angle carries the
-// FP32 error, which leaves |g'| ~ 1e-7 |g| for the next sweep to remove.
+// jacobi_rotation() with the angle taken in FP32: d = b - a and 2g are
+// brought into FP32 range (scaled by a power of two when needed), t is formed
+// in FP32, and c = rsqrt(1 + t^2), s = c t in FP64, so that c^2 + s^2 = 1
+// within FP64 rounding.  The rotation is orthogonal in FP64 and only its angle
+// carries the FP32 error, which leaves |g'| ~ 1e-7 |g| for the next sweep.
 __device__ __forceinline__ void jacobi_rotation_fast(double a, double b, double g, double* c, double* s) {
     const double d = b - a, g2 = g + g;
     const int ed = (__double2hiint(d) >> 20) & 0x7ff, eg = (__double2hiint(g2) >> 20) & 0x7ff;
@@ -244,21 +255,21 @@ __device__ __forceinline__ void jacobi_rotation_fast(double a, double b, double 
         jacobi_rotation(a, b, g, c, s);
         return;
     }
-    const double sc = __hiloint2double((2046 - e) << 20, 0);   // 2^(1023 - e)
-    const float df = __double2float_rn(d * sc), gf = __double2float_rn(g2 * sc);
+    float df, gf;
+    if (e >= 1023 - 60 && e <= 1023 + 60) {   // squares stay normal in FP32
+        df = __double2float_rn(d);
+        gf = __double2float_rn(g2);
+    } else {
+        const double sc = __hiloint2double((2046 - e) << 20, 0);   // 2^(1023 - e)
+        df = __double2float_rn(d * sc);
+        gf = __double2float_rn(g2 * sc);
+    }
     const float r = sqrtf(fmaf(df, df, gf * gf));
     const float sz = (df == 0.0f || ((df > 0.0f) == (gf > 0.0f))) ? 1.0f : -1.0f;
-    const float t = sz * fabsf(gf) / (fabsf(df) + r);
-    const float cf = rsqrtf(fmaf(t, t, 1.0f));
-    double cd = (double)cf, sd = (double)(cf * t);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double h = fma(-0.5, fma(cd, cd, sd * sd), 1.5);
-        cd *= h;
-        sd *= h;
-    }
+    const double t = (double)(sz * fabsf(gf) / (fabsf(df) + r));
+    const double cd = rsqrt(fma(t, t, 1.0));
     *c = cd;
-    *s = sd;
+    *s = cd * t;
 }
 
 // jacobi() for k <= 16: one round-robin pair per warp; the pair's three inner
@@ -310,7 +321,8 @@ __device__ __forceinline__ void jacobi_small(double* G, double* V, double* Sraw,
                     b = __shfl_sync(0xffffffffu, ab, 16);
                     g = __shfl_sync(0xffffffffu, pg, 0);
                 }
-                if (g != 0.0 && g * g > tol2 * a * b && fmin(a, b) > tiny2) {
+                if (g * g > tol2 * (a * b) && nonneg_key(a) > nonneg_key(tiny2) &&
+                    nonneg_key(b) > nonneg_key(tiny2)) {
                     double c, s;
                     jacobi_rotation_fast(a, b, g, &c, &s);
                     if (lane < 2 * S && i < k) {
@@ -334,7 +346,7 @@ __device__ __forceinline__ void jacobi_small(double* G, double* V, double* Sraw,
         const int j = j0 + sg;
         const double x = (j < k && i < k) ? G[(int64_t)j * k + i] : 0.0;
         const double a = seg_sum(x * x, S);
-        if (j < k && i == 0) Sraw[j] = sqrt(a);
+        if (j < k && i == 0) Sraw[j] = sqrt_via_rsqrt(a);
     }
     __syncthreads();
 }
@@ -393,7 +405,8 @@ __device__ __forceinline__ void jacobi_direct(double* B, double* V, double* Sraw
                     b = warp_sum(xq * xq);
                     g = warp_sum(xp * xq);
                 }
-                if (g != 0.0 && g * g > tol2 * a * b && fmin(a, b) > tiny2) {
+                if (g * g > tol2 * (a * b) && nonneg_key(a) > nonneg_key(tiny2) &&
+                    nonneg_key(b) > nonneg_key(tiny2)) {
                     double c, s;
                     jacobi_rotation_fast(a, b, g, &c, &s);
                     if (S <= 16) {
@@ -431,7 +444,7 @@ __device__ __forceinline__ void jacobi_direct(double* B, double* V, double* Sraw
         const int j = j0 + sg;
         const double x = (j < k && i < rows) ? B[(int64_t)j * rows + i] : 0.0;
         const double a = seg_sum(x * x, S);
-        if (j < k && i == 0) Sraw[j] = sqrt(a);
+        if (j < k && i == 0) Sraw[j] = sqrt_via_rsqrt(a);
     }
     __syncthreads();
 }
@@ -446,10 +459,11 @@ __device__ __forceinline__ void svd_assemble_direct(const double* B, const doubl
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < k; i += nthreads()) {
         const double si = Sraw[i];
+        const long long ki = nonneg_key(si);
         int rank = 0;
         for (int j = 0; j < k; ++j) {
-            const double sj = Sraw[j];
-            rank += (sj > si || (sj == si && j < i)) ? 1 : 0;
+            const long long kj = nonneg_key(Sraw[j]);
+            rank += (kj > ki || (kj == ki && j < i)) ? 1 : 0;
         }
         perm[rank] = i;
         if (wide) {
@@ -471,17 +485,17 @@ __device__ __forceinline__ void svd_assemble_direct(const double* B, const doubl
     for (int r = threadIdx.x; r < k; r += nthreads()) S[r] = Sraw[perm[r]];
     __syncthreads();
     for (int r = warp; r < k; r += nwarps()) {
-        double best = -1.0;
+        long long best = -1;
         int bi = 0;
         for (int c = lane; c < N; c += 32) {
-            const double a = fabs(Vt[(int64_t)r * ldvt + c]);
+            const long long a = abs_key(Vt[(int64_t)r * ldvt + c]);
             if (a > best) {
                 best = a;
                 bi = c;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) {
                 best = ob;

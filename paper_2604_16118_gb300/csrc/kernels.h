@@ -163,6 +163,7 @@ struct DynTask {
     double* US;
     double* Vt;
     int* kact;
+    int cut;   // index of the cut of this task's truncation and bond
 };
 // Cut of one bond: the singular values of its sectors (sector i: S[i] with
 // *kact[i] values) pooled and cut exactly as choose_cut; keep[i] receives the
@@ -177,6 +178,8 @@ struct CutTask {
     double tol2;
     int* keep;
     double* disc;
+    int n_tasks;   // SVD tasks of this truncation and bond (persistent sweep)
+    int* done;     // their completion counter (zeroed before the launch)
 };
 size_t dyn_svd_smem(int M, int ncols_pad);
 // returns the index of its profiler record (-1 when not profiling) so that the
@@ -198,8 +201,9 @@ struct GridSync {
 // (nothing launched) when the grid cannot be co-resident.
 bool launch_left_sweep(Context* ctx, const std::vector<LeftTask>& tasks, const std::vector<LeftSrc>& srcs,
                        const std::vector<LeftX>& xs, const std::vector<int>& phase_beg, GridSync* gs);
-// Right sweep: phase p runs its SVD tasks, then cuts[p] on the last CTA to
-// arrive.  *prof_idx: the profiler record (-1 when not profiling).
+// Right sweep: phase p runs its SVD tasks; the CTA that completes the last
+// task of a truncation in the phase runs that truncation's cut (tasks[i].cut).
+// *prof_idx: the profiler record (-1 when not profiling).
 bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts,
                         const std::vector<int>& phase_beg, const std::vector<CutTask>& cuts,
                         const std::vector<CutSector>& secs, GridSync* gs, int* prof_idx);

@@ -247,8 +247,8 @@ std::vector<int> choose_cut(std::vector<SvEntry> sv, int n_sectors, double tol2,
         }
     }
     while (keep > 0 && keep < n && sv[keep].s >= sv[keep - 1].s * (1.0 - rtol)) keep += 1;
-    double td = 0.0;
-    for (int i = keep; i < n; ++i) td += sv[i].s * sv[i].s;
+    double td = 0.0;   // discarded squares, summed from the smallest
+    for (int i = n - 1; i >= keep; --i) td += sv[i].s * sv[i].s;
     double cd = 0.0;
     if (r_max > 0 && keep > r_max) {
         int k2 = r_max;
@@ -264,328 +264,62 @@ std::vector<int> choose_cut(std::vector<SvEntry> sv, int n_sectors, double tol2,
     return cnt;
 }
 
-// Left-to-right QR sweep as one persistent launch: the new layout of every
-// site follows on the host from the sector row counts alone (rank = min(rows,
-// cols)), so all sites' tasks are planned first and the sites run as phases
-// of one cooperative kernel.  Returns false (L, cores and owned untouched)
-// when a site does not fit the fused kernel or the grid cannot be resident.
-static bool left_sweep_persistent(Context* ctx, Layout& L, std::vector<double*>& cores, std::vector<char>& owned,
-                                  GridSync* gs) {
-    const int K = L.K;
-    if (K < 2) return false;
-    Layout P = L;
-    std::vector<double*> pc = cores;
-    std::vector<char> po = owned;
-    std::vector<double*> fresh, deferred;
-    std::vector<LeftTask> lt;
-    std::vector<LeftSrc> ls;
-    std::vector<LeftX> lx;
-    std::vector<int> phase_beg{0};
-    auto abandon = [&]() {
-        for (double* q : fresh) ctx->free(q);
-        return false;
-    };
-    for (int t = 0; t + 1 < K; ++t) {
-        const Bond bm = P.bonds[t + 1];
-        const int nm = (int)bm.q.size();
-        std::vector<int> Mrows(nm, 0), krank(nm, 0);
-        std::vector<std::vector<std::pair<int, int>>> stack(nm);
-        for (int bi = 0; bi < (int)P.blocks[t].size(); ++bi) {
-            const Block& bk = P.blocks[t][bi];
-            stack[bk.ri].push_back({bi, Mrows[bk.ri]});
-            Mrows[bk.ri] += bk.rows;
-        }
-        const std::vector<int> oldlook = block_lookup(P, t + 1);
-        const std::vector<Block> oldB_t = P.blocks[t], oldB_t1 = P.blocks[t + 1];
-        Bond nb;
-        for (int mi = 0; mi < nm; ++mi) {
-            if (Mrows[mi] > 0) krank[mi] = std::min(Mrows[mi], bm.dim[mi]);
-            if (krank[mi] > 0) {
-                nb.q.push_back(bm.q[mi]);
-                nb.dim.push_back(krank[mi]);
-            }
-        }
-        for (int mi = 0; mi < nm; ++mi) {
-            if (Mrows[mi] == 0) continue;
-            int64_t rx = 0;
-            for (int sg = 0; sg < 2; ++sg) {
-                const int ob = oldlook[mi * 2 + sg];
-                if (ob >= 0) rx += (int64_t)krank[mi] * bm.dim[mi] * oldB_t1[ob].cols;
-            }
-            if (!left_site_fits(Mrows[mi], bm.dim[mi], rx)) return abandon();
-        }
-        P.bonds[t + 1] = nb;
-        rebuild_site(P, t);
-        rebuild_site(P, t + 1);
-        double* nt = P.core_size[t] > 0 ? (double*)ctx->alloc(sizeof(double) * (size_t)P.core_size[t]) : nullptr;
-        double* nt1 =
-            P.core_size[t + 1] > 0 ? (double*)ctx->alloc(sizeof(double) * (size_t)P.core_size[t + 1]) : nullptr;
-        if (nt) fresh.push_back(nt);
-        if (nt1) fresh.push_back(nt1);
-        const std::vector<int> newlook_t = block_lookup(P, t);
-        for (int mi = 0; mi < nm; ++mi) {
-            if (Mrows[mi] == 0) continue;
-            const int nmi = P.bonds[t + 1].find(bm.q[mi]);
-            LeftTask task{Mrows[mi], bm.dim[mi], krank[mi], (int)ls.size(), 0, (int)lx.size(), 0};
-            for (auto& pr : stack[mi]) {
-                const Block& ob = oldB_t[pr.first];
-                const Block& nbk = P.blocks[t][newlook_t[ob.li * 2 + ob.sigma]];
-                ls.push_back({pc[t] + ob.off, nt + nbk.off, ob.rows, pr.second});
-            }
-            task.s_end = (int)ls.size();
-            for (const Block& nbk : P.blocks[t + 1]) {
-                if (nbk.li != nmi) continue;
-                const Block& ob = oldB_t1[oldlook[mi * 2 + nbk.sigma]];
-                lx.push_back({pc[t + 1] + ob.off, nt1 + nbk.off, ob.cols});
-            }
-            task.x_end = (int)lx.size();
-            lt.push_back(task);
-        }
-        phase_beg.push_back((int)lt.size());
-        for (int u : {t, t + 1}) {
-            if (po[u] && pc[u]) deferred.push_back(pc[u]);
-        }
-        pc[t] = nt;
-        po[t] = 1;
-        pc[t + 1] = nt1;
-        po[t + 1] = 1;
-    }
-    if (!launch_left_sweep(ctx, lt, ls, lx, phase_beg, gs)) return abandon();
-    // the intermediate R X cores and the replaced cores are released behind the launch
-    for (double* q : deferred) ctx->free(q);
-    L = P;
-    cores = pc;
-    owned = po;
-    return true;
-}
+namespace {
 
-// Right sweep of trunc_eps with the cut decided on the device: every bond's
-// SVDs read the kept counts of the previous bond from device memory, so the
-// whole sweep is enqueued without a host round trip; the kept counts of all
-// bonds are read once at the end.  Returns false (nothing done) when a bond's
-// padded problem does not fit the fused kernels.
-static bool right_sweep_device(Context* ctx, Layout& L, std::vector<double*>& cores, std::vector<char>& owned,
-                               double eps, int r_max, double* td2, double* cd2, GridSync* gs, bool* gs_checked) {
-    const int K = L.K;
-    if (K < 2) return false;
-    const double tol2 = eps * eps / (K - 1);
-    // padded ranks per bond (kpad[K] = 1 for the single sector of bond K)
-    std::vector<std::vector<int>> kpad(K + 1), cpad(K + 1);
-    kpad[K].assign(L.bonds[K].q.size(), 1);
-    for (int b = K - 1; b >= 1; --b) {
-        const Bond& bn = L.bonds[b];
-        kpad[b].assign(bn.q.size(), 0);
-        cpad[b].assign(bn.q.size(), 0);
-        int total = 0;
-        for (const Block& bk : L.blocks[b]) {
-            const int m = bk.ri;
-            cpad[b][bk.li] += (b + 1 == K) ? bk.cols : kpad[b + 1][m];
-        }
-        for (size_t n = 0; n < bn.q.size(); ++n) {
-            // the SVD keeps min(rows, cols) columns before the cut, so the
-            // padding is not reduced by the rank cap
-            const int kp = std::min(bn.dim[n], cpad[b][n]);
-            kpad[b][n] = kp;
-            total += kp;
-            if (kp > 96 || dyn_svd_smem(bn.dim[n], cpad[b][n]) > 220 * 1024) return false;
-            int64_t fma = 0;
-            for (const Block& bk : L.blocks[b])
-                if (bk.li == (int)n && b + 1 < K) fma += (int64_t)bk.rows * bk.cols * kpad[b + 1][bk.ri];
-            if (fma > (int64_t)1 << 20) return false;
-        }
-        if (total > 2048) return false;
+// One truncation in flight: the sweeps update its layout and cores in place.
+// Cores it owns (allocated by a sweep) are freed on destruction unless they
+// were handed to the result.
+struct TruncJob {
+    Context* ctx;
+    Layout L;
+    std::vector<double*> cores;
+    std::vector<char> owned;
+    double eps;
+    int r_max;
+    double td2 = 0.0, cd2 = 0.0;
+    TruncJob(Context* c, const Mps* x, double e, int r)
+        : ctx(c), L(x->lay), cores(x->core), owned(x->lay.K, 0), eps(e), r_max(r) {}
+    TruncJob(const TruncJob&) = delete;
+    TruncJob& operator=(const TruncJob&) = delete;
+    ~TruncJob() {
+        for (size_t t = 0; t < cores.size(); ++t)
+            if (owned[t] && cores[t]) ctx->free(cores[t]);
     }
-    // buffers: per bond and sector S, US (rows x kpad), Vt (kpad x cpad); kact, keep per bond
-    Scratch s(ctx);
-    std::vector<std::vector<double*>> S(K), US(K), Vt(K);
-    std::vector<int> secoff(K + 1, 0);
-    int nsec_all = 0;
-    for (int b = 1; b < K; ++b) {
-        secoff[b] = nsec_all;
-        nsec_all += (int)L.bonds[b].q.size();
-    }
-    int* ints = (int*)ctx->alloc(sizeof(int) * 2 * (size_t)std::max(nsec_all, 1));
-    s.ptrs.push_back(ints);
-    int* kact = ints;
-    int* keep = ints + nsec_all;
-    double* disc = s.dbl(2);
-    BSM_CUDA(cudaMemsetAsync(ints, 0, sizeof(int) * 2 * (size_t)std::max(nsec_all, 1), ctx->stream));
-    BSM_CUDA(cudaMemsetAsync(disc, 0, sizeof(double) * 2, ctx->stream));
-    for (int b = 1; b < K; ++b) {
-        const Bond& bn = L.bonds[b];
-        for (size_t n = 0; n < bn.q.size(); ++n) {
-            const int kp = std::max(kpad[b][n], 1), cp = std::max(cpad[b][n], 1);
-            S[b].push_back(s.dbl((size_t)kp));
-            US[b].push_back(s.dbl((size_t)bn.dim[n] * kp));
-            Vt[b].push_back(s.dbl((size_t)kp * cp));
-        }
-    }
-    // all bonds' tasks in sweep order (phase p = bond K-1-p)
-    std::vector<DynTask> tasks;
-    std::vector<DynPart> parts;
-    std::vector<CutTask> cuts;
-    std::vector<CutSector> secs;
-    std::vector<int> phase_beg{0};
-    for (int b = K - 1; b >= 1; --b) {
-        const Bond& bn = L.bonds[b];
-        std::vector<std::vector<DynPart>> per(bn.q.size());
-        for (const Block& bk : L.blocks[b]) {   // layout order: sigma 0 before 1 within a sector
-            const int m = bk.ri;
-            if (b + 1 == K)
-                per[bk.li].push_back({cores[b] + bk.off, bk.cols, nullptr, 0, nullptr});
-            else
-                per[bk.li].push_back({cores[b] + bk.off, bk.cols, US[b + 1][m], std::max(kpad[b + 1][m], 1),
-                                      keep + secoff[b + 1] + m});
-        }
-        for (size_t n = 0; n < bn.q.size(); ++n) {
-            DynTask t{bn.dim[n], std::max(kpad[b][n], 1), std::max(cpad[b][n], 1), (int)parts.size(), 0,
-                      S[b][n], US[b][n], Vt[b][n], kact + secoff[b] + (int)n};
-            parts.insert(parts.end(), per[n].begin(), per[n].end());
-            t.p_end = (int)parts.size();
-            tasks.push_back(t);
-        }
-        phase_beg.push_back((int)tasks.size());
-        const int s_beg = (int)secs.size();
-        int cap = 0;
-        for (size_t n = 0; n < bn.q.size(); ++n) {
-            secs.push_back({S[b][n], kact + secoff[b] + (int)n});
-            cap += kpad[b][n];
-        }
-        cuts.push_back({(int)bn.q.size(), s_beg, std::max(cap, 1), r_max, tol2, keep + secoff[b], disc});
-    }
-    std::vector<int> prof_idx(1, -1);
-    if (!launch_right_sweep(ctx, tasks, parts, phase_beg, cuts, secs, gs + 1, &prof_idx[0])) {
-        // grid not co-resident: one SVD launch and one cut launch per bond
-        prof_idx.clear();
-        for (size_t p = 0; p + 1 < phase_beg.size(); ++p) {
-            std::vector<DynTask> tp(tasks.begin() + phase_beg[p], tasks.begin() + phase_beg[p + 1]);
-            prof_idx.push_back(launch_right_dyn(ctx, tp, parts));
-            launch_cut(ctx, cuts[p], secs);
-        }
-    }
-    std::vector<int> keep_h((size_t)std::max(nsec_all, 1));
-    double disc_h[2];
-    GridSync gs_h[2];
-    BSM_CUDA(cudaMemcpyAsync(keep_h.data(), keep, sizeof(int) * keep_h.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    BSM_CUDA(cudaMemcpyAsync(disc_h, disc, sizeof(disc_h), cudaMemcpyDeviceToHost, ctx->stream));
-    BSM_CUDA(cudaMemcpyAsync(gs_h, gs, sizeof(gs_h), cudaMemcpyDeviceToHost, ctx->stream));
-    ctx->sync();
-    BSM_REQUIRE(gs_h[0].err == 0 && gs_h[1].err == 0, BSMPS_ERR_TIMEOUT,
-                "truncation sweep: a grid-wide wait gave up");
-    *gs_checked = true;
-    *td2 += disc_h[0];
-    *cd2 += disc_h[1];
-    // actual sizes: cols of sector n at bond b = sum of kept counts of its parts
-    auto kept = [&](int b, int m) { return b == K ? 1 : keep_h[secoff[b] + m]; };
-    double fl = 0.0;
-    std::vector<std::vector<int>> cols_act(K), coff1(K);
-    for (int b = K - 1; b >= 1; --b) {
-        const Bond& bn = L.bonds[b];
-        cols_act[b].assign(bn.q.size(), 0);
-        coff1[b].assign(bn.q.size(), 0);
-        for (const Block& bk : L.blocks[b]) {
-            const int c = (b + 1 == K) ? bk.cols : kept(b + 1, bk.ri);
-            if (bk.sigma == 0) coff1[b][bk.li] = c;
-            cols_act[b][bk.li] += c;
-            if (b + 1 < K) fl += 2.0 * bk.rows * (double)bk.cols * c;
-        }
-        for (size_t n = 0; n < bn.q.size(); ++n) {
-            const double M = bn.dim[n], N = cols_act[b][n], k = std::min(M, N), len = std::max(M, N);
-            if (k > 0)
-                fl += 2.0 * len * k * k - (len + k) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * len * k * k -
-                      2.0 / 3.0 * k * k * k + 54.0 * k * k * k + 2.0 * len * k * k;
-        }
-    }
-    ctx->flops += fl;
-    if (!prof_idx.empty() && prof_idx[0] >= 0) {
-        for (int idx : prof_idx) ctx->prof[idx].flops = 0.0;
-        ctx->prof[prof_idx[0]].flops = fl;   // attributed to the sweep's first SVD launch record
-    }
-    // compact layout and cores
-    Layout F = L;
-    for (int b = 1; b < K; ++b) {
-        Bond nb;
-        for (size_t n = 0; n < L.bonds[b].q.size(); ++n)
-            if (keep_h[secoff[b] + n] > 0) {
-                nb.q.push_back(L.bonds[b].q[n]);
-                nb.dim.push_back(keep_h[secoff[b] + n]);
-            }
-        F.bonds[b] = nb;
-    }
-    F.rebuild_blocks();
-    std::vector<double*> nc(K, nullptr);
-    for (int t = 0; t < K; ++t)
-        if (F.core_size[t] > 0) nc[t] = (double*)ctx->alloc(sizeof(double) * (size_t)F.core_size[t]);
-    std::vector<CopyTask> cp;
-    std::vector<GemmOut> go;
-    std::vector<GemmIn> gi;
-    for (int t = 0; t < K; ++t) {
-        for (const Block& fb : F.blocks[t]) {
-            const Charge qn = F.bonds[t].q[fb.li];
-            if (t == 0) {
-                // core 0: X_0 (1 x rho_1(m)) times the kept columns of U S of bond 1
-                const int m = L.bonds[1].find(F.bonds[1].q[fb.ri]);
-                const Block* ob = nullptr;
-                for (const Block& b0 : L.blocks[0])
-                    if (b0.sigma == fb.sigma) ob = &b0;
-                go.push_back({nc[0] + fb.off, fb.rows, fb.cols, fb.cols, (int)gi.size(), (int)gi.size() + 1, 0.0});
-                gi.push_back({cores[0] + ob->off, US[1][m], ob->cols, ob->cols, std::max(kpad[1][m], 1), 0, 1.0});
-            } else {
-                const int n = L.bonds[t].find(qn);
-                const int coff = fb.sigma == 0 ? 0 : coff1[t][n];
-                cp.push_back({Vt[t][n] + coff, nc[t] + fb.off, fb.rows, fb.cols, std::max(cpad[t][n], 1), fb.cols, 0,
-                              0, 0, 1.0});
-            }
-        }
-    }
-    launch_copy(ctx, cp);
-    launch_gemm(ctx, go, gi);
-    for (int t = 0; t < K; ++t) {
-        if (owned[t] && cores[t]) ctx->free(cores[t]);
-        cores[t] = nc[t];
-        owned[t] = 1;
-    }
-    L = F;
-    return true;
-}
-
-MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
-                   double* disc_cap) {
-    const int K = x->lay.K;
-    Layout L = x->lay;
-    std::vector<double*> cores = x->core;
-    std::vector<char> owned(K, 0);
-    auto release = [&](int t) {
+    void release(int t) {
         if (owned[t] && cores[t]) ctx->free(cores[t]);
         cores[t] = nullptr;
         owned[t] = 0;
-    };
-    struct Guard {
-        std::vector<double*>* c;
-        std::vector<char>* o;
-        Context* ctx;
-        bool active = true;
-        ~Guard() {
-            if (!active) return;
-            for (size_t t = 0; t < c->size(); ++t)
-                if ((*o)[t] && (*c)[t]) ctx->free((*c)[t]);
+    }
+    double* alloc_core(int64_t n) { return n > 0 ? (double*)ctx->alloc((size_t)n * sizeof(double)) : nullptr; }
+    MpsPtr finish() {
+        const int K = L.K;
+        MpsPtr y(new Mps);
+        y->ctx = ctx;
+        y->lay = L;
+        y->core.assign(K, nullptr);
+        for (int t = 0; t < K; ++t) {
+            if (owned[t]) {
+                y->core[t] = cores[t];
+            } else if (L.core_size[t] > 0) {   // untouched core (K == 1): copy
+                y->core[t] = alloc_core(L.core_size[t]);
+                BSM_CUDA(cudaMemcpyAsync(y->core[t], cores[t], (size_t)L.core_size[t] * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, ctx->stream));
+            }
+            owned[t] = 0;
         }
-    } guard{&cores, &owned, ctx};
-    auto alloc_core = [&](int64_t n) -> double* {
-        return n > 0 ? (double*)ctx->alloc((size_t)n * sizeof(double)) : nullptr;
-    };
+        return y;
+    }
+};
 
-    // phase bookkeeping of the two persistent sweeps; err is read back with
-    // the right sweep's cut results (or at the end when that path is not taken)
-    Scratch gs_scratch(ctx);
-    GridSync* gs = (GridSync*)ctx->alloc(2 * sizeof(GridSync));
-    gs_scratch.ptrs.push_back(gs);
-    BSM_CUDA(cudaMemsetAsync(gs, 0, 2 * sizeof(GridSync), ctx->stream));
-    bool gs_checked = false;
-
-    // ---- left-to-right QR sweep ----
-    const bool left_done = left_sweep_persistent(ctx, L, cores, owned, gs);
-    for (int t = left_done ? K : 0; t + 1 < K; ++t) {
+// ---- left-to-right QR sweep, one launch per site ----
+void left_sweep_sitewise(Context* ctx, TruncJob& J) {
+    const int K = J.L.K;
+    Layout& L = J.L;
+    std::vector<double*>& cores = J.cores;
+    std::vector<char>& owned = J.owned;
+    auto release = [&](int t) { J.release(t); };
+    auto alloc_core = [&](int64_t n) { return J.alloc_core(n); };
+    for (int t = 0; t + 1 < K; ++t) {
         Scratch s(ctx);
         const Bond bm = L.bonds[t + 1];   // the old bond (L is updated in place below)
         const int nm = (int)bm.q.size();
@@ -700,11 +434,21 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         owned[t + 1] = 1;
     }
 
-    // ---- right-to-left SVD sweep ----
-    const double tol2 = K > 1 ? eps * eps / (K - 1) : 0.0;
-    double td2 = 0.0, cd2 = 0.0;
-    const bool done_on_device = right_sweep_device(ctx, L, cores, owned, eps, r_max, &td2, &cd2, gs, &gs_checked);
-    for (int t = done_on_device ? 0 : K - 1; t >= 1; --t) {
+}
+
+// ---- right-to-left SVD sweep, one launch per site and a host cut ----
+void right_sweep_sitewise(Context* ctx, TruncJob& J) {
+    const int K = J.L.K;
+    Layout& L = J.L;
+    std::vector<double*>& cores = J.cores;
+    std::vector<char>& owned = J.owned;
+    const int r_max = J.r_max;
+    double& td2 = J.td2;
+    double& cd2 = J.cd2;
+    auto release = [&](int t) { J.release(t); };
+    auto alloc_core = [&](int64_t n) { return J.alloc_core(n); };
+    const double tol2 = K > 1 ? J.eps * J.eps / (K - 1) : 0.0;
+    for (int t = K - 1; t >= 1; --t) {
         Scratch s(ctx);
         const Bond bn = L.bonds[t];   // the old bond (L is updated in place below)
         const int nn = (int)bn.q.size();
@@ -869,31 +613,465 @@ MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* di
         cores[t - 1] = ntm;
         owned[t - 1] = 1;
     }
+}
+
+// Planned left sweep of one job: the new layout of every site follows on the
+// host from the sector row counts alone (rank = min(rows, cols)).
+struct LeftPlan {
+    Layout P;
+    std::vector<double*> pc;
+    std::vector<char> po;
+    std::vector<double*> fresh, deferred;
+    std::vector<std::vector<LeftTask>> tasks;   // per site
+    std::vector<LeftSrc> srcs;
+    std::vector<LeftX> xs;
+};
+
+// False (nothing allocated) when a site does not fit the fused kernel.
+bool plan_left(Context* ctx, const TruncJob& J, LeftPlan& pl) {
+    const int K = J.L.K;
+    pl.P = J.L;
+    pl.pc = J.cores;
+    pl.po = J.owned;
+    pl.tasks.assign(K - 1, {});
+    auto abandon = [&]() {
+        for (double* q : pl.fresh) ctx->free(q);
+        pl.fresh.clear();
+        return false;
+    };
+    Layout& P = pl.P;
+    for (int t = 0; t + 1 < K; ++t) {
+        const Bond bm = P.bonds[t + 1];
+        const int nm = (int)bm.q.size();
+        std::vector<int> Mrows(nm, 0), krank(nm, 0);
+        std::vector<std::vector<std::pair<int, int>>> stack(nm);
+        for (int bi = 0; bi < (int)P.blocks[t].size(); ++bi) {
+            const Block& bk = P.blocks[t][bi];
+            stack[bk.ri].push_back({bi, Mrows[bk.ri]});
+            Mrows[bk.ri] += bk.rows;
+        }
+        const std::vector<int> oldlook = block_lookup(P, t + 1);
+        const std::vector<Block> oldB_t = P.blocks[t], oldB_t1 = P.blocks[t + 1];
+        Bond nb;
+        for (int mi = 0; mi < nm; ++mi) {
+            if (Mrows[mi] > 0) krank[mi] = std::min(Mrows[mi], bm.dim[mi]);
+            if (krank[mi] > 0) {
+                nb.q.push_back(bm.q[mi]);
+                nb.dim.push_back(krank[mi]);
+            }
+        }
+        for (int mi = 0; mi < nm; ++mi) {
+            if (Mrows[mi] == 0) continue;
+            int64_t rx = 0;
+            for (int sg = 0; sg < 2; ++sg) {
+                const int ob = oldlook[mi * 2 + sg];
+                if (ob >= 0) rx += (int64_t)krank[mi] * bm.dim[mi] * oldB_t1[ob].cols;
+            }
+            if (!left_site_fits(Mrows[mi], bm.dim[mi], rx)) return abandon();
+        }
+        P.bonds[t + 1] = nb;
+        rebuild_site(P, t);
+        rebuild_site(P, t + 1);
+        double* nt = P.core_size[t] > 0 ? (double*)ctx->alloc(sizeof(double) * (size_t)P.core_size[t]) : nullptr;
+        double* nt1 =
+            P.core_size[t + 1] > 0 ? (double*)ctx->alloc(sizeof(double) * (size_t)P.core_size[t + 1]) : nullptr;
+        if (nt) pl.fresh.push_back(nt);
+        if (nt1) pl.fresh.push_back(nt1);
+        const std::vector<int> newlook_t = block_lookup(P, t);
+        for (int mi = 0; mi < nm; ++mi) {
+            if (Mrows[mi] == 0) continue;
+            const int nmi = P.bonds[t + 1].find(bm.q[mi]);
+            LeftTask task{Mrows[mi], bm.dim[mi], krank[mi], (int)pl.srcs.size(), 0, (int)pl.xs.size(), 0};
+            for (auto& pr : stack[mi]) {
+                const Block& ob = oldB_t[pr.first];
+                const Block& nbk = P.blocks[t][newlook_t[ob.li * 2 + ob.sigma]];
+                pl.srcs.push_back({pl.pc[t] + ob.off, nt + nbk.off, ob.rows, pr.second});
+            }
+            task.s_end = (int)pl.srcs.size();
+            for (const Block& nbk : P.blocks[t + 1]) {
+                if (nbk.li != nmi) continue;
+                const Block& ob = oldB_t1[oldlook[mi * 2 + nbk.sigma]];
+                pl.xs.push_back({pl.pc[t + 1] + ob.off, nt1 + nbk.off, ob.cols});
+            }
+            task.x_end = (int)pl.xs.size();
+            pl.tasks[t].push_back(task);
+        }
+        for (int u : {t, t + 1})
+            if (pl.po[u] && pl.pc[u]) pl.deferred.push_back(pl.pc[u]);
+        pl.pc[t] = nt;
+        pl.po[t] = 1;
+        pl.pc[t + 1] = nt1;
+        pl.po[t + 1] = 1;
+    }
+    return true;
+}
+
+// Left sweeps of several truncations as one persistent launch (site t of
+// every job is phase t).  Jobs whose sites do not fit are returned in `rest`.
+bool left_sweep_batch(Context* ctx, const std::vector<TruncJob*>& jobs, GridSync* gs,
+                      std::vector<TruncJob*>* rest) {
+    std::vector<TruncJob*> in;
+    std::vector<LeftPlan> plans;
+    plans.reserve(jobs.size());
+    for (TruncJob* J : jobs) {
+        if (J->L.K < 2) {
+            rest->push_back(J);
+            continue;
+        }
+        plans.emplace_back();
+        if (plan_left(ctx, *J, plans.back())) {
+            in.push_back(J);
+        } else {
+            plans.pop_back();
+            rest->push_back(J);
+        }
+    }
+    if (in.empty()) return false;
+    const int K = in[0]->L.K;
+    std::vector<LeftTask> lt;
+    std::vector<LeftSrc> ls;
+    std::vector<LeftX> lx;
+    std::vector<int> phase_beg{0};
+    std::vector<int> soff(plans.size()), xoff(plans.size());
+    for (size_t j = 0; j < plans.size(); ++j) {
+        soff[j] = (int)ls.size();
+        xoff[j] = (int)lx.size();
+        ls.insert(ls.end(), plans[j].srcs.begin(), plans[j].srcs.end());
+        lx.insert(lx.end(), plans[j].xs.begin(), plans[j].xs.end());
+    }
+    for (int t = 0; t + 1 < K; ++t) {
+        for (size_t j = 0; j < plans.size(); ++j)
+            for (LeftTask task : plans[j].tasks[t]) {
+                task.s_beg += soff[j];
+                task.s_end += soff[j];
+                task.x_beg += xoff[j];
+                task.x_end += xoff[j];
+                lt.push_back(task);
+            }
+        phase_beg.push_back((int)lt.size());
+    }
+    if (!launch_left_sweep(ctx, lt, ls, lx, phase_beg, gs)) {
+        for (LeftPlan& pl : plans)
+            for (double* q : pl.fresh) ctx->free(q);
+        rest->insert(rest->end(), in.begin(), in.end());
+        return false;
+    }
+    // the intermediate R X cores and the replaced cores are released behind the launch
+    for (size_t j = 0; j < plans.size(); ++j) {
+        for (double* q : plans[j].deferred) ctx->free(q);
+        in[j]->L = plans[j].P;
+        in[j]->cores = plans[j].pc;
+        in[j]->owned = plans[j].po;
+    }
+    return true;
+}
+
+// Sizes of one job's device-driven right sweep: padded ranks per bond
+// (kpad[K] = 1 for the single sector of bond K) and padded column counts.
+struct RightPlan {
+    TruncJob* J;
+    std::vector<std::vector<int>> kpad, cpad;
+    std::vector<int> secoff;   // first sector of bond b in the job's keep / kact arrays
+    int nsec = 0;
+    std::vector<std::vector<double*>> S, US, Vt;
+    int* kact = nullptr;
+    int* keep = nullptr;
+    double* disc = nullptr;
+};
+
+bool plan_right_sizes(const TruncJob& J, RightPlan& rp) {
+    const Layout& L = J.L;
+    const int K = L.K;
+    if (K < 2) return false;
+    rp.kpad.assign(K + 1, {});
+    rp.cpad.assign(K + 1, {});
+    rp.kpad[K].assign(L.bonds[K].q.size(), 1);
+    for (int b = K - 1; b >= 1; --b) {
+        const Bond& bn = L.bonds[b];
+        rp.kpad[b].assign(bn.q.size(), 0);
+        rp.cpad[b].assign(bn.q.size(), 0);
+        int total = 0;
+        for (const Block& bk : L.blocks[b]) rp.cpad[b][bk.li] += (b + 1 == K) ? bk.cols : rp.kpad[b + 1][bk.ri];
+        for (size_t n = 0; n < bn.q.size(); ++n) {
+            // the SVD keeps min(rows, cols) columns before the cut, so the
+            // padding is not reduced by the rank cap
+            const int kp = std::min(bn.dim[n], rp.cpad[b][n]);
+            rp.kpad[b][n] = kp;
+            total += kp;
+            if (kp > 96 || dyn_svd_smem(bn.dim[n], rp.cpad[b][n]) > 220 * 1024) return false;
+            int64_t fma = 0;
+            for (const Block& bk : L.blocks[b])
+                if (bk.li == (int)n && b + 1 < K) fma += (int64_t)bk.rows * bk.cols * rp.kpad[b + 1][bk.ri];
+            if (fma > (int64_t)1 << 20) return false;
+        }
+        if (total > 2048) return false;
+    }
+    rp.secoff.assign(K + 1, 0);
+    rp.nsec = 0;
+    for (int b = 1; b < K; ++b) {
+        rp.secoff[b] = rp.nsec;
+        rp.nsec += (int)L.bonds[b].q.size();
+    }
+    return true;
+}
+
+// Right sweeps with the cut decided on the device, several truncations in one
+// persistent launch (bond K-1-p of every job is phase p).  Every bond's SVDs
+// read the kept counts of the previous bond from device memory; the last task
+// of a job in a phase runs that job's pooled cut.  The kept counts of all
+// bonds are read once at the end.  Jobs that do not fit are returned in `rest`.
+bool right_sweep_batch(Context* ctx, const std::vector<TruncJob*>& jobs, GridSync* gs, bool* gs_checked,
+                       std::vector<TruncJob*>* rest) {
+    std::vector<RightPlan> plans;
+    for (TruncJob* J : jobs) {
+        RightPlan rp;
+        rp.J = J;
+        if (plan_right_sizes(*J, rp))
+            plans.push_back(std::move(rp));
+        else
+            rest->push_back(J);
+    }
+    if (plans.empty()) return false;
+    const int K = plans[0].J->L.K;
+    const int nj = (int)plans.size();
+    // buffers
+    Scratch s(ctx);
+    int nsec_tot = 0;
+    for (RightPlan& rp : plans) nsec_tot += rp.nsec;
+    const int n_phase = K - 1;
+    const size_t n_ints = 2 * (size_t)std::max(nsec_tot, 1) + (size_t)n_phase * nj;
+    int* ints = (int*)ctx->alloc(sizeof(int) * n_ints);
+    s.ptrs.push_back(ints);
+    double* disc = s.dbl(2 * (size_t)nj);
+    BSM_CUDA(cudaMemsetAsync(ints, 0, sizeof(int) * n_ints, ctx->stream));
+    BSM_CUDA(cudaMemsetAsync(disc, 0, sizeof(double) * 2 * nj, ctx->stream));
+    int* done = ints + 2 * (size_t)std::max(nsec_tot, 1);
+    {
+        int o = 0;
+        for (int j = 0; j < nj; ++j) {
+            RightPlan& rp = plans[j];
+            rp.kact = ints + o;
+            rp.keep = ints + std::max(nsec_tot, 1) + o;
+            rp.disc = disc + 2 * j;
+            o += rp.nsec;
+            const Layout& L = rp.J->L;
+            rp.S.assign(K, {});
+            rp.US.assign(K, {});
+            rp.Vt.assign(K, {});
+            for (int b = 1; b < K; ++b) {
+                const Bond& bn = L.bonds[b];
+                for (size_t n = 0; n < bn.q.size(); ++n) {
+                    const int kp = std::max(rp.kpad[b][n], 1), cp = std::max(rp.cpad[b][n], 1);
+                    rp.S[b].push_back(s.dbl((size_t)kp));
+                    rp.US[b].push_back(s.dbl((size_t)bn.dim[n] * kp));
+                    rp.Vt[b].push_back(s.dbl((size_t)kp * cp));
+                }
+            }
+        }
+    }
+    // tasks in sweep order
+    std::vector<DynTask> tasks;
+    std::vector<DynPart> parts;
+    std::vector<CutTask> cuts;
+    std::vector<CutSector> secs;
+    std::vector<int> phase_beg{0};
+    for (int b = K - 1; b >= 1; --b) {
+        for (int j = 0; j < nj; ++j) {
+            RightPlan& rp = plans[j];
+            const Layout& L = rp.J->L;
+            const std::vector<double*>& cores = rp.J->cores;
+            const Bond& bn = L.bonds[b];
+            const int cut_idx = (int)cuts.size();
+            std::vector<std::vector<DynPart>> per(bn.q.size());
+            for (const Block& bk : L.blocks[b]) {   // layout order: sigma 0 before 1 within a sector
+                const int m = bk.ri;
+                if (b + 1 == K)
+                    per[bk.li].push_back({cores[b] + bk.off, bk.cols, nullptr, 0, nullptr});
+                else
+                    per[bk.li].push_back({cores[b] + bk.off, bk.cols, rp.US[b + 1][m],
+                                          std::max(rp.kpad[b + 1][m], 1), rp.keep + rp.secoff[b + 1] + m});
+            }
+            for (size_t n = 0; n < bn.q.size(); ++n) {
+                DynTask t{bn.dim[n],       std::max(rp.kpad[b][n], 1), std::max(rp.cpad[b][n], 1),
+                          (int)parts.size(), 0, rp.S[b][n], rp.US[b][n], rp.Vt[b][n],
+                          rp.kact + rp.secoff[b] + (int)n, cut_idx};
+                parts.insert(parts.end(), per[n].begin(), per[n].end());
+                t.p_end = (int)parts.size();
+                tasks.push_back(t);
+            }
+            const int s_beg = (int)secs.size();
+            int cap = 0;
+            for (size_t n = 0; n < bn.q.size(); ++n) {
+                secs.push_back({rp.S[b][n], rp.kact + rp.secoff[b] + (int)n});
+                cap += rp.kpad[b][n];
+            }
+            const double tol2 = rp.J->eps * rp.J->eps / (K - 1);
+            cuts.push_back({(int)bn.q.size(), s_beg, std::max(cap, 1), rp.J->r_max, tol2, rp.keep + rp.secoff[b],
+                            rp.disc, (int)bn.q.size(), done + cut_idx});
+        }
+        phase_beg.push_back((int)tasks.size());
+    }
+    std::vector<int> prof_idx(1, -1);
+    if (!launch_right_sweep(ctx, tasks, parts, phase_beg, cuts, secs, gs + 1, &prof_idx[0])) {
+        // grid not co-resident: one SVD launch per bond and one cut launch per job
+        prof_idx.clear();
+        for (int p = 0; p < n_phase; ++p) {
+            std::vector<DynTask> tp(tasks.begin() + phase_beg[p], tasks.begin() + phase_beg[p + 1]);
+            prof_idx.push_back(launch_right_dyn(ctx, tp, parts));
+            for (int j = 0; j < nj; ++j) launch_cut(ctx, cuts[(size_t)p * nj + j], secs);
+        }
+    }
+    std::vector<int> ints_h(2 * (size_t)std::max(nsec_tot, 1));
+    std::vector<double> disc_h(2 * (size_t)nj);
+    GridSync gs_h[2];
+    BSM_CUDA(cudaMemcpyAsync(ints_h.data(), ints, sizeof(int) * ints_h.size(), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    BSM_CUDA(cudaMemcpyAsync(disc_h.data(), disc, sizeof(double) * disc_h.size(), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    BSM_CUDA(cudaMemcpyAsync(gs_h, gs, sizeof(gs_h), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    BSM_REQUIRE(gs_h[0].err == 0 && gs_h[1].err == 0, BSMPS_ERR_TIMEOUT,
+                "truncation sweep: a grid-wide wait gave up");
+    *gs_checked = true;
+    // compaction of every job: kept rows of Vt into cores 1..K-1, X_0 U S into core 0
+    double fl = 0.0;
+    std::vector<CopyTask> cp;
+    std::vector<GemmOut> go;
+    std::vector<GemmIn> gi;
+    std::vector<std::vector<double*>> new_cores(nj);
+    std::vector<Layout> new_lay(nj);
+    for (int j = 0; j < nj; ++j) {
+        RightPlan& rp = plans[j];
+        TruncJob& J = *rp.J;
+        const Layout& L = J.L;
+        J.td2 += disc_h[2 * j];
+        J.cd2 += disc_h[2 * j + 1];
+        const int* keep_h = ints_h.data() + std::max(nsec_tot, 1) + (rp.keep - (ints + std::max(nsec_tot, 1)));
+        auto kept = [&](int b, int m) { return b == K ? 1 : keep_h[rp.secoff[b] + m]; };
+        std::vector<std::vector<int>> coff1(K);
+        for (int b = K - 1; b >= 1; --b) {
+            const Bond& bn = L.bonds[b];
+            std::vector<int> cols_act(bn.q.size(), 0);
+            coff1[b].assign(bn.q.size(), 0);
+            for (const Block& bk : L.blocks[b]) {
+                const int c = (b + 1 == K) ? bk.cols : kept(b + 1, bk.ri);
+                if (bk.sigma == 0) coff1[b][bk.li] = c;
+                cols_act[bk.li] += c;
+                if (b + 1 < K) fl += 2.0 * bk.rows * (double)bk.cols * c;
+            }
+            for (size_t n = 0; n < bn.q.size(); ++n) {
+                const double M = bn.dim[n], N = cols_act[n], k = std::min(M, N), len = std::max(M, N);
+                if (k > 0)
+                    fl += 2.0 * len * k * k - (len + k) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * len * k * k -
+                          2.0 / 3.0 * k * k * k + 54.0 * k * k * k + 2.0 * len * k * k;
+            }
+        }
+        Layout F = L;
+        for (int b = 1; b < K; ++b) {
+            Bond nb;
+            for (size_t n = 0; n < L.bonds[b].q.size(); ++n)
+                if (keep_h[rp.secoff[b] + n] > 0) {
+                    nb.q.push_back(L.bonds[b].q[n]);
+                    nb.dim.push_back(keep_h[rp.secoff[b] + n]);
+                }
+            F.bonds[b] = nb;
+        }
+        F.rebuild_blocks();
+        std::vector<double*>& nc = new_cores[j];
+        nc.assign(K, nullptr);
+        for (int t = 0; t < K; ++t)
+            if (F.core_size[t] > 0) nc[t] = (double*)ctx->alloc(sizeof(double) * (size_t)F.core_size[t]);
+        for (int t = 0; t < K; ++t) {
+            for (const Block& fb : F.blocks[t]) {
+                const Charge qn = F.bonds[t].q[fb.li];
+                if (t == 0) {
+                    const int m = L.bonds[1].find(F.bonds[1].q[fb.ri]);
+                    const Block* ob = nullptr;
+                    for (const Block& b0 : L.blocks[0])
+                        if (b0.sigma == fb.sigma) ob = &b0;
+                    go.push_back({nc[0] + fb.off, fb.rows, fb.cols, fb.cols, (int)gi.size(), (int)gi.size() + 1, 0.0});
+                    gi.push_back({J.cores[0] + ob->off, rp.US[1][m], ob->cols, ob->cols,
+                                  std::max(rp.kpad[1][m], 1), 0, 1.0});
+                } else {
+                    const int n = L.bonds[t].find(qn);
+                    const int coff = fb.sigma == 0 ? 0 : coff1[t][n];
+                    cp.push_back({rp.Vt[t][n] + coff, nc[t] + fb.off, fb.rows, fb.cols,
+                                  std::max(rp.cpad[t][n], 1), fb.cols, 0, 0, 0, 1.0});
+                }
+            }
+        }
+        new_lay[j] = F;
+    }
+    ctx->flops += fl;
+    if (!prof_idx.empty() && prof_idx[0] >= 0) {
+        for (int idx : prof_idx) ctx->prof[idx].flops = 0.0;
+        ctx->prof[prof_idx[0]].flops = fl;   // attributed to the sweep's first SVD launch record
+    }
+    launch_copy(ctx, cp);
+    launch_gemm(ctx, go, gi);
+    for (int j = 0; j < nj; ++j) {
+        TruncJob& J = *plans[j].J;
+        for (int t = 0; t < K; ++t) {
+            if (J.owned[t] && J.cores[t]) ctx->free(J.cores[t]);
+            J.cores[t] = new_cores[j][t];
+            J.owned[t] = 1;
+        }
+        J.L = new_lay[j];
+    }
+    return true;
+}
+
+// trunc_eps of several MPS of the same sites (Sec. 2.2): the fused sweeps of
+// all of them share launches.
+std::vector<MpsPtr> truncate_jobs(Context* ctx, std::vector<std::unique_ptr<TruncJob>>& jobs) {
+    std::vector<TruncJob*> all;
+    for (auto& j : jobs) all.push_back(j.get());
+    // phase bookkeeping of the two persistent sweeps; err is read back with
+    // the right sweep's cut results (or at the end when that path is not taken)
+    Scratch gs_scratch(ctx);
+    GridSync* gs = (GridSync*)ctx->alloc(2 * sizeof(GridSync));
+    gs_scratch.ptrs.push_back(gs);
+    BSM_CUDA(cudaMemsetAsync(gs, 0, 2 * sizeof(GridSync), ctx->stream));
+    bool gs_checked = false;
+    std::vector<TruncJob*> left_rest;
+    const bool left_done = left_sweep_batch(ctx, all, gs, &left_rest);
+    for (TruncJob* J : left_rest) left_sweep_sitewise(ctx, *J);
+    std::vector<TruncJob*> right_rest;
+    right_sweep_batch(ctx, all, gs, &gs_checked, &right_rest);
+    for (TruncJob* J : right_rest) right_sweep_sitewise(ctx, *J);
     if (left_done && !gs_checked) {
         GridSync h;
         BSM_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
         ctx->sync();
         BSM_REQUIRE(h.err == 0, BSMPS_ERR_TIMEOUT, "left truncation sweep: a grid-wide wait gave up");
     }
-    if (disc_tol) *disc_tol = std::sqrt(td2);
-    if (disc_cap) *disc_cap = std::sqrt(cd2);
+    std::vector<MpsPtr> out;
+    for (TruncJob* J : all) out.push_back(J->finish());
+    return out;
+}
 
-    MpsPtr y(new Mps);
-    y->ctx = ctx;
-    y->lay = L;
-    y->core.assign(K, nullptr);
-    for (int t = 0; t < K; ++t) {
-        if (owned[t]) {
-            y->core[t] = cores[t];
-        } else if (L.core_size[t] > 0) {   // untouched core (K == 1): copy
-            y->core[t] = alloc_core(L.core_size[t]);
-            BSM_CUDA(cudaMemcpyAsync(y->core[t], cores[t], (size_t)L.core_size[t] * sizeof(double),
-                                     cudaMemcpyDeviceToDevice, ctx->stream));
-        }
-        owned[t] = 0;
+}  // namespace
+
+MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol, double* disc_cap) {
+    std::vector<std::unique_ptr<TruncJob>> jobs;
+    jobs.emplace_back(new TruncJob(ctx, x, eps, r_max));
+    std::vector<MpsPtr> out = truncate_jobs(ctx, jobs);
+    if (disc_tol) *disc_tol = std::sqrt(jobs[0]->td2);
+    if (disc_cap) *disc_cap = std::sqrt(jobs[0]->cd2);
+    return std::move(out[0]);
+}
+
+std::vector<MpsPtr> op_truncate_batch(Context* ctx, const std::vector<const Mps*>& xs, const std::vector<double>& eps,
+                                      int r_max) {
+    BSM_REQUIRE(xs.size() == eps.size(), BSMPS_ERR_INVALID_ARG, "one tolerance per MPS");
+    if (xs.empty()) return {};
+    std::vector<std::unique_ptr<TruncJob>> jobs;
+    for (size_t i = 0; i < xs.size(); ++i) {
+        BSM_REQUIRE(same_space(xs[i]->lay, xs[0]->lay), BSMPS_ERR_INVALID_ARG,
+                    "batched truncation of MPS on different sites");
+        jobs.emplace_back(new TruncJob(ctx, xs[i], eps[i], r_max));
     }
-    guard.active = false;
-    return y;
+    return truncate_jobs(ctx, jobs);
 }
 
 namespace {

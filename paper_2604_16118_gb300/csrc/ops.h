@@ -33,6 +33,11 @@ MpsPtr op_apply_exact(Context* ctx, const Mpo& W, const Mps* x, double shift);
 MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
                    double* disc_cap);
 
+// trunc_eps of several MPS on the same sites, eps[i] for xs[i]; the sweeps of
+// all of them share launches.
+std::vector<MpsPtr> op_truncate_batch(Context* ctx, const std::vector<const Mps*>& xs,
+                                      const std::vector<double>& eps, int r_max);
+
 // Which pooled singular values of one bond survive (Sec. 2.2); entries
 // (sigma, sector, j).  Returns kept counts per sector.
 struct SvEntry {

@@ -157,9 +157,14 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
         std::vector<EnvProblem> up;
         for (int kp = 0; kp < nt; ++kp) up.push_back({u[kp].get(), u[kp].get(), nullptr, 0.0});
         const std::vector<double> un2 = op_dot_batch(ctx, up);
-        for (int kp = 0; kp < nt; ++kp)
-            u[kp] = op_truncate(ctx, u[kp].get(), prm.u_rel * std::sqrt(std::max(un2[kp], 0.0)), 0, nullptr,
-                                nullptr);
+        std::vector<const Mps*> ux;
+        std::vector<double> ueps;
+        for (int kp = 0; kp < nt; ++kp) {
+            ux.push_back(u[kp].get());
+            ueps.push_back(prm.u_rel * std::sqrt(std::max(un2[kp], 0.0)));
+        }
+        std::vector<MpsPtr> uc = op_truncate_batch(ctx, ux, ueps, 0);
+        for (int kp = 0; kp < nt; ++kp) u[kp] = std::move(uc[kp]);
     }
     std::vector<EnvProblem> nprobs;
     for (int kp = 0; kp < nt; ++kp)

@@ -24,6 +24,11 @@ size_t left_smem(int M, int N) {
     return sizeof(double) * ((size_t)M * N + (size_t)M * k + k + k * (size_t)N);
 }
 
+// values, their squares, sector ids, order, and n_sec + 1 offsets
+size_t cut_smem(const CutTask& c) {
+    return sizeof(double) * 2 * (size_t)c.cap_total + sizeof(int) * (2 * (size_t)c.cap_total + c.n_sec + 1);
+}
+
 size_t svd_smem(int M, int N) {
     const size_t k = (size_t)std::min(M, N), len = (size_t)std::max(M, N);
     return sizeof(double) * (2 * len * k + 2 * k * k + 3 * k);
@@ -56,8 +61,8 @@ __device__ void left_rank1(const LeftTask& tk, const LeftSrc* __restrict__ srcs,
         double s = 0.0;
         for (int i = threadIdx.x; i < M; i += nthreads()) s = fma(A[i], A[i], s);
         s = dev::block_sum(s, red);
-        const double r = sqrt(s);
-        const double f = r > 0.0 ? 1.0 / r : 0.0;
+        const double f = s > 0.0 ? rsqrt(s) : 0.0;   // 1/r
+        const double r = s * f;
         for (int si = tk.s_beg; si < tk.s_end; ++si) {
             const LeftSrc sr = srcs[si];
             for (int i = threadIdx.x; i < sr.rows; i += nthreads())
@@ -219,43 +224,44 @@ __global__ void __launch_bounds__(kThreads) k_right_apply(const RTask* __restric
 // every thread.  red: 33 shared doubles.
 __device__ __forceinline__ int block_argmax_abs(const double* v, int n, double* red) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double best = -1.0;
+    long long best = -1;
     int bi = 0;
     for (int c = threadIdx.x; c < n; c += nthreads()) {
-        const double a = fabs(v[c]);
+        const long long a = dev::abs_key(v[c]);
         if (a > best) {
             best = a;
             bi = c;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) {
             best = ob;
             bi = oi;
         }
     }
+    if (nwarps() == 1) return __shfl_sync(0xffffffffu, bi, 0);
+    long long* rk = (long long*)red;   // 8 keys, then 8 indices
     __syncthreads();
     if (lane == 0) {
-        red[w] = best;
-        red[16 + w] = (double)bi;
+        rk[w] = best;
+        rk[16 + w] = bi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = red[0];
-        int i = (int)red[16];
+        long long b = rk[0];
+        long long i = rk[16];
         for (int u = 1; u < nwarps(); ++u) {
-            const int ui = (int)red[16 + u];
-            if (red[u] > b || (red[u] == b && ui < i)) {
-                b = red[u];
-                i = ui;
+            if (rk[u] > b || (rk[u] == b && rk[16 + u] < i)) {
+                b = rk[u];
+                i = rk[16 + u];
             }
         }
-        red[32] = (double)i;
+        rk[32] = i;
     }
     __syncthreads();
-    return (int)red[32];
+    return (int)rk[32];
 }
 
 // Rank-1 sector of the right sweep (a single row or column v, length len):
@@ -267,7 +273,8 @@ __device__ void right_rank1(const DynTask& tk, const double* v, int len, int wid
     double s = 0.0;
     for (int i = threadIdx.x; i < len; i += nthreads()) s = fma(v[i], v[i], s);
     s = dev::block_sum(s, red);
-    const double sigma = sqrt(s);
+    const double rs = s > 0.0 ? rsqrt(s) : 0.0;   // 1/sigma
+    const double sigma = s * rs;
     if (!wide) {
         for (int i = threadIdx.x; i < len; i += nthreads()) tk.US[(int64_t)i * tk.kpad] = sigma > 0.0 ? v[i] : 0.0;
         if (threadIdx.x == 0) {
@@ -279,7 +286,7 @@ __device__ void right_rank1(const DynTask& tk, const double* v, int len, int wid
     }
     const int im = block_argmax_abs(v, len, red);
     const double sgn = v[im] < 0.0 ? -1.0 : 1.0;
-    const double f = sigma > 0.0 ? sgn / sigma : 0.0;
+    const double f = sgn * rs;
     for (int c = threadIdx.x; c < len; c += nthreads()) tk.Vt[c] = sigma > 0.0 ? v[c] * f : (c == 0 ? 1.0 : 0.0);
     if (threadIdx.x == 0) {
         tk.US[0] = sgn * sigma;
@@ -390,10 +397,10 @@ template <bool CG>
 __device__ void cut_body(const CutTask& tk, const CutSector* __restrict__ secs, double* sm, int* s_n_ptr) {
     int& s_n = *s_n_ptr;
     double* val = sm;
-    int* sec = (int*)(val + tk.cap_total);
-    int* jj = sec + tk.cap_total;
-    int* order = jj + tk.cap_total;
-    int* off = order + tk.cap_total;   // n_sec + 1
+    double* sq = val + tk.cap_total;   // squares in sorted order
+    int* sec = (int*)(sq + tk.cap_total);
+    int* order = sec + tk.cap_total;
+    int* off = order + tk.cap_total;   // n_sec + 1 (later: kept counts per sector)
     if (threadIdx.x == 0) {
         int o = 0;
         for (int i = 0; i < tk.n_sec; ++i) {
@@ -410,51 +417,62 @@ __device__ void cut_body(const CutTask& tk, const CutSector* __restrict__ secs, 
         for (int j = threadIdx.x; j < c; j += nthreads()) {
             val[off[i] + j] = ldd<CG>(secs[tk.s_beg + i].S + j);
             sec[off[i] + j] = i;
-            jj[off[i] + j] = j;
         }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += nthreads()) {
-        const double se = val[e];
+        const double ve = val[e];
+        const long long se = dev::nonneg_key(ve);
         int rank = 0;
         for (int o = 0; o < n; ++o) {
-            const double so = val[o];
-            const bool before = so > se || (so == se && (sec[o] < sec[e] || (sec[o] == sec[e] && jj[o] < jj[e])));
-            rank += before ? 1 : 0;
+            const long long so = dev::nonneg_key(val[o]);
+            // entries are stored sector by sector and index by index, so ties
+            // in value are ordered by position
+            rank += (so > se || (so == se && o < e)) ? 1 : 0;
         }
         order[rank] = e;
+        sq[rank] = __dmul_rn(ve, ve);
     }
     __syncthreads();
+    __shared__ int s_keep;
     if (threadIdx.x == 0) {
         const double rtol = 1e-10;
         int keep = n;
         double acc = 0.0;
         while (keep > 0) {
-            const double sv = val[order[keep - 1]];
-            const double s2 = __dmul_rn(sv, sv);
-            if (__dadd_rn(acc, s2) <= tk.tol2) {
-                acc = __dadd_rn(acc, s2);
+            const double na = __dadd_rn(acc, sq[keep - 1]);
+            if (na <= tk.tol2) {
+                acc = na;
                 keep -= 1;
             } else {
                 break;
             }
         }
+        const int keep0 = keep;
         while (keep > 0 && keep < n && val[order[keep]] >= __dmul_rn(val[order[keep - 1]], 1.0 - rtol)) keep += 1;
-        double td = 0.0;
-        for (int i = keep; i < n; ++i) td = __dadd_rn(td, __dmul_rn(val[order[i]], val[order[i]]));
+        double td = acc;   // discarded squares, summed from the smallest
+        if (keep != keep0) {
+            td = 0.0;
+            for (int i = n - 1; i >= keep; --i) td = __dadd_rn(td, sq[i]);
+        }
         double cd = 0.0;
         if (tk.r_max > 0 && keep > tk.r_max) {
             int k2 = tk.r_max;
             while (k2 > 0 && val[order[k2]] >= __dmul_rn(val[order[k2 - 1]], 1.0 - rtol)) k2 -= 1;
             if (k2 == 0) k2 = tk.r_max;
-            for (int i = k2; i < keep; ++i) cd = __dadd_rn(cd, __dmul_rn(val[order[i]], val[order[i]]));
+            for (int i = k2; i < keep; ++i) cd = __dadd_rn(cd, sq[i]);
             keep = k2;
         }
-        for (int i = 0; i < tk.n_sec; ++i) tk.keep[i] = 0;
-        for (int r = 0; r < keep; ++r) tk.keep[sec[order[r]]] += 1;
         tk.disc[0] = __dadd_rn(tk.disc[0], td);
         tk.disc[1] = __dadd_rn(tk.disc[1], cd);
+        s_keep = keep;
     }
+    for (int i = threadIdx.x; i < tk.n_sec; i += nthreads()) off[i] = 0;
+    __syncthreads();
+    const int keep = s_keep;
+    for (int r = threadIdx.x; r < keep; r += nthreads()) atomicAdd(&off[sec[order[r]]], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < tk.n_sec; i += nthreads()) tk.keep[i] = off[i];
     __syncthreads();
 }
 
@@ -559,10 +577,22 @@ __global__ void __launch_bounds__(kThreads) k_right_sweep(const DynTask* __restr
     for (int p = 0; p < n_phase; ++p) {
         for (int ti = phase_beg[p] + (int)blockIdx.x; ti < phase_beg[p + 1]; ti += (int)gridDim.x) {
             __syncthreads();
-            right_body<true>(tasks[ti], parts, sm, red, sh, &s_rot, s_cols);
+            const DynTask tk = tasks[ti];
+            right_body<true>(tk, parts, sm, red, sh, &s_rot, s_cols);
+            // the CTA that completes the last task of this truncation's bond runs its cut
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const CutTask& ct = cuts[tk.cut];
+                s_flag = atomicAdd(ct.done, 1) == ct.n_tasks - 1 ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                cut_body<true>(cuts[tk.cut], secs, sm, &s_n);
+            }
         }
-        const CutTask ct = cuts[p];
-        if (!phase_end(gs, (unsigned)p, &s_flag, [&] { cut_body<true>(ct, secs, sm, &s_n); })) return;
+        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag, [] {})) return;
     }
 }
 
@@ -750,8 +780,7 @@ void launch_cut(Context* ctx, const CutTask& task, const std::vector<CutSector>&
     const size_t ot = pk.add(std::vector<CutTask>{task}), os = pk.add(secs);
     Scratch s(ctx);
     unsigned char* d = upload_pack(s, pk);
-    const size_t smem = sizeof(double) * (size_t)task.cap_total + sizeof(int) * (3 * (size_t)task.cap_total +
-                                                                                 task.n_sec + 1);
+    const size_t smem = cut_smem(task);
     Prof pr(ctx, KK_SUMSQ, 0.0, 8.0 * task.cap_total);
     allow_smem(k_cut_dyn);
     k_cut_dyn<<<1, kThreads, smem, ctx->stream>>>((const CutTask*)(d + ot), (const CutSector*)(d + os));
@@ -808,7 +837,7 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const s
                         const std::vector<CutSector>& secs, GridSync* gs, int* prof_idx) {
     *prof_idx = -1;
     const int n_phase = (int)phase_beg.size() - 1;
-    if (n_phase <= 0 || (int)cuts.size() != n_phase) return false;
+    if (n_phase <= 0 || cuts.empty()) return false;
     size_t smem = 0;
     int kmax = 1, maxt = 1;
     double by = 0.0;
@@ -817,9 +846,7 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const s
         kmax = std::max(kmax, t.kpad);
         by += 8.0 * ((double)t.M * t.ncols_pad + (double)t.M * t.kpad + (double)t.kpad * t.ncols_pad);
     }
-    for (const CutTask& c : cuts)
-        smem = std::max(smem, sizeof(double) * (size_t)c.cap_total +
-                                  sizeof(int) * (3 * (size_t)c.cap_total + c.n_sec + 1));
+    for (const CutTask& c : cuts) smem = std::max(smem, cut_smem(c));
     for (int p = 0; p < n_phase; ++p) maxt = std::max(maxt, phase_beg[p + 1] - phase_beg[p]);
     const int threads = block_for(kmax);
     allow_smem(k_right_sweep);
