@@ -26,41 +26,101 @@ Context* context_of(bsmps_ctx c) {
 
 void* Context::alloc(size_t bytes) {
     if (bytes == 0) return nullptr;
+#ifdef BSM_NO_ALLOC_CACHE   // host-side checking builds: every block goes back to the pool
+    {
+        void* q = nullptr;
+        BSM_CUDA(cudaMallocAsync(&q, bytes, stream));
+        return q;
+    }
+#endif
+    int c = 8;   // 256-byte minimum
+    while (c <= kMaxClass && (size_t(1) << c) < bytes) ++c;
     void* p = nullptr;
-    BSM_CUDA(cudaMallocAsync(&p, bytes, stream));
+    if (c > kMaxClass) {
+        BSM_CUDA(cudaMallocAsync(&p, bytes, stream));
+        block_class[p] = -1;
+        return p;
+    }
+    std::vector<void*>& fl = free_blocks[c];
+    if (!fl.empty()) {
+        p = fl.back();
+        fl.pop_back();
+        cached_bytes -= size_t(1) << c;
+        return p;
+    }
+    BSM_CUDA(cudaMallocAsync(&p, size_t(1) << c, stream));
+    block_class[p] = c;
     return p;
 }
 
 void Context::free(void* p) {
-    if (p) cudaFreeAsync(p, stream);
+    if (!p) return;
+#ifdef BSM_NO_ALLOC_CACHE
+    cudaFreeAsync(p, stream);
+    return;
+#endif
+    auto it = block_class.find(p);
+    if (it == block_class.end()) {
+        cudaFreeAsync(p, stream);
+        return;
+    }
+    const int c = it->second;
+    if (c < 0 || cached_bytes + (size_t(1) << c) > kCacheCap) {
+        block_class.erase(it);
+        cudaFreeAsync(p, stream);
+        return;
+    }
+    free_blocks[c].push_back(p);
+    cached_bytes += size_t(1) << c;
+}
+
+void Context::release_cache() {
+    for (auto& fl : free_blocks) {
+        for (void* p : fl) {
+            block_class.erase(p);
+            cudaFreeAsync(p, stream);
+        }
+        fl.clear();
+    }
+    cached_bytes = 0;
 }
 
 void* Context::upload_raw(const void* src, size_t bytes) {
     void* d = alloc(bytes);
-    if (bytes > kRingSlotBytes) {
+    const size_t half = kRingBytes / 2;
+    if (bytes > half) {
         BSM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, stream));
         return d;
     }
     if (!ring_host) {
-        BSM_CUDA(cudaMallocHost((void**)&ring_host, kRingSlots * kRingSlotBytes));
-        ring_ev.resize(kRingSlots);
-        ring_used.assign(kRingSlots, 0);
-        for (auto& e : ring_ev) BSM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        BSM_CUDA(cudaMallocHost((void**)&ring_host, kRingBytes));
+        for (auto& e : half_ev) BSM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ring_head = 0;
+        ring_half = 0;
     }
-    const int slot = ring_next;
-    ring_next = (ring_next + 1) % kRingSlots;
-    if (ring_used[slot]) BSM_CUDA(cudaEventSynchronize(ring_ev[slot]));
-    unsigned char* h = ring_host + (size_t)slot * kRingSlotBytes;
+    if (ring_head + bytes > (size_t)(ring_half + 1) * half) {
+        // leave this half: its copies complete before the event; wait for the other half's
+        BSM_CUDA(cudaEventRecord(half_ev[ring_half], stream));
+        half_pending[ring_half] = true;
+        ring_half ^= 1;
+        ring_head = (size_t)ring_half * half;
+        if (half_pending[ring_half]) {
+            BSM_CUDA(cudaEventSynchronize(half_ev[ring_half]));
+            half_pending[ring_half] = false;
+        }
+    }
+    unsigned char* h = ring_host + ring_head;
     std::memcpy(h, src, bytes);
     BSM_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, stream));
-    BSM_CUDA(cudaEventRecord(ring_ev[slot], stream));
-    ring_used[slot] = 1;
+    ring_head += (bytes + 255) & ~size_t(255);
     return d;
 }
 
 void Context::release_ring() {
-    for (auto e : ring_ev) cudaEventDestroy(e);
-    ring_ev.clear();
+    for (auto& e : half_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
     if (ring_host) cudaFreeHost(ring_host);
     ring_host = nullptr;
 }
@@ -157,6 +217,8 @@ bsmps_status bsmps_ctx_destroy(bsmps_ctx ctx) {
         }
         for (auto e : ctx->c.event_pool) cudaEventDestroy(e);
         ctx->c.release_ring();
+        ctx->c.release_cache();
+        ctx->c.sync();
     });
     delete ctx;
     return s;

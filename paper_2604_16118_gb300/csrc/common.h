@@ -7,6 +7,7 @@
 #include <map>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/bsmps.h"
@@ -128,26 +129,39 @@ struct Context {
     cudaEvent_t take_event();
     void prof_begin(cudaEvent_t* e0);
     void prof_end(int kind, double flops, double bytes, cudaEvent_t e0);
-    // pinned staging ring for task uploads: a copy from pageable memory can make
-    // the host wait for the stream, so uploads go through page-locked slots
-    // whose reuse is gated by an event recorded after their copy
-    static constexpr int kRingSlots = 64;
-    static constexpr size_t kRingSlotBytes = 256 * 1024;
+    // pinned staging ring for task uploads (a copy from pageable memory can
+    // make the host wait for the stream): two halves, filled in turn; an event
+    // recorded when a half is left gates its reuse
+    static constexpr size_t kRingBytes = 8u << 20;
     unsigned char* ring_host = nullptr;
-    std::vector<cudaEvent_t> ring_ev;
-    std::vector<char> ring_used;
-    int ring_next = 0;
+    size_t ring_head = 0;
+    int ring_half = 0;
+    cudaEvent_t half_ev[2] = {nullptr, nullptr};
+    bool half_pending[2] = {false, false};
     void* upload_raw(const void* src, size_t bytes);
     void release_ring();
-    // scratch for task uploads and temporaries
+    // Device memory: a caching sub-allocator over the stream-ordered pool.
+    // Blocks are rounded up to a power of two and recycled on this context's
+    // stream; stream order makes a block freed after the work that uses it
+    // safe for any later work, so alloc and free need no CUDA call once the
+    // cache is warm.
+    static constexpr int kMaxClass = 26;                 // 64 MiB; larger blocks bypass the cache
+    static constexpr size_t kCacheCap = size_t(4) << 30;
+    std::vector<std::vector<void*>> free_blocks = std::vector<std::vector<void*>>(kMaxClass + 1);
+    std::unordered_map<void*, int> block_class;
+    size_t cached_bytes = 0;
     void* alloc(size_t bytes);
     void free(void* p);
+    void release_cache();
     template <class T>
     T* upload(const std::vector<T>& v) {
         if (v.empty()) return nullptr;
         return (T*)upload_raw(v.data(), v.size() * sizeof(T));
     }
-    void sync() { BSM_CUDA(cudaStreamSynchronize(stream)); }
+    void sync() {
+        BSM_CUDA(cudaStreamSynchronize(stream));
+        half_pending[0] = half_pending[1] = false;   // every staged copy has completed
+    }
 };
 
 // RAII holder for temporary device allocations of one operation.

@@ -3,6 +3,7 @@
 // a block-sparse MPS.  All arithmetic is float64.
 #include <cfloat>
 #include <cmath>
+#include <cstring>
 
 #include "dense_dev.cuh"
 #include "kernels.h"
@@ -336,18 +337,29 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
     }
     if (tiles.empty() && small.empty()) return;
     ctx->flops += fl;
+    // one staged upload for all task arrays
+    std::vector<unsigned char> pack;
+    auto add = [&](const void* src, size_t bytes) {
+        const size_t off = (pack.size() + 15) & ~size_t(15);
+        pack.resize(off + bytes);
+        if (bytes) std::memcpy(pack.data() + off, src, bytes);
+        return off;
+    };
+    const size_t oo = add(outs.data(), outs.size() * sizeof(GemmOut));
+    const size_t oi = add(ins.data(), ins.size() * sizeof(GemmIn));
+    const size_t os = add(small.data(), small.size() * sizeof(int));
+    const size_t ot = add(tiles.data(), tiles.size() * sizeof(GemmTile));
     Scratch s(ctx);
-    GemmOut* d_o = s.up(outs);
-    GemmIn* d_i = s.up(ins);
+    unsigned char* d = s.up(pack);
+    const GemmOut* d_o = (const GemmOut*)(d + oo);
+    const GemmIn* d_i = (const GemmIn*)(d + oi);
     ProfScope ps(ctx, KK_GEMM, fl, by);
     if (!small.empty()) {
-        int* d_s = s.up(small);
-        k_gemm_small<<<(unsigned)small.size(), kSmallGemmThreads, 0, ctx->stream>>>(d_o, d_i, d_s);
+        k_gemm_small<<<(unsigned)small.size(), kSmallGemmThreads, 0, ctx->stream>>>(d_o, d_i, (const int*)(d + os));
         check_launch(ctx);
     }
     if (!tiles.empty()) {
-        GemmTile* d_t = s.up(tiles);
-        k_gemm<<<(unsigned)tiles.size(), kThreads, 0, ctx->stream>>>(d_o, d_i, d_t);
+        k_gemm<<<(unsigned)tiles.size(), kThreads, 0, ctx->stream>>>(d_o, d_i, (const GemmTile*)(d + ot));
         check_launch(ctx);
     }
     ps.done();

@@ -847,6 +847,23 @@ bool right_sweep_batch(Context* ctx, const std::vector<TruncJob*>& jobs, GridSyn
     BSM_CUDA(cudaMemsetAsync(disc, 0, sizeof(double) * 2 * nj, ctx->stream));
     int* done = ints + 2 * (size_t)std::max(nsec_tot, 1);
     {
+        // S, US and Vt of every sector of every bond and job, carved from one allocation
+        size_t total = 0;
+        for (RightPlan& rp : plans) {
+            const Layout& L = rp.J->L;
+            for (int b = 1; b < K; ++b)
+                for (size_t n = 0; n < L.bonds[b].q.size(); ++n) {
+                    const size_t kp = std::max(rp.kpad[b][n], 1), cp = std::max(rp.cpad[b][n], 1);
+                    total += kp + (size_t)L.bonds[b].dim[n] * kp + kp * cp;
+                }
+        }
+        double* arena = s.dbl(total);
+        size_t at = 0;
+        auto carve = [&](size_t n) {
+            double* q = arena + at;
+            at += n;
+            return q;
+        };
         int o = 0;
         for (int j = 0; j < nj; ++j) {
             RightPlan& rp = plans[j];
@@ -861,10 +878,10 @@ bool right_sweep_batch(Context* ctx, const std::vector<TruncJob*>& jobs, GridSyn
             for (int b = 1; b < K; ++b) {
                 const Bond& bn = L.bonds[b];
                 for (size_t n = 0; n < bn.q.size(); ++n) {
-                    const int kp = std::max(rp.kpad[b][n], 1), cp = std::max(rp.cpad[b][n], 1);
-                    rp.S[b].push_back(s.dbl((size_t)kp));
-                    rp.US[b].push_back(s.dbl((size_t)bn.dim[n] * kp));
-                    rp.Vt[b].push_back(s.dbl((size_t)kp * cp));
+                    const size_t kp = std::max(rp.kpad[b][n], 1), cp = std::max(rp.cpad[b][n], 1);
+                    rp.S[b].push_back(carve(kp));
+                    rp.US[b].push_back(carve((size_t)bn.dim[n] * kp));
+                    rp.Vt[b].push_back(carve(kp * cp));
                 }
             }
         }
