@@ -208,4 +208,19 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const s
                         const std::vector<int>& phase_beg, const std::vector<CutTask>& cuts,
                         const std::vector<CutSector>& secs, GridSync* gs, int* prof_idx);
 
+// ---- environment sweep of a batch of inner products (one cooperative launch) ----
+
+// Output tile of at most 32 x 32 entries of outs[out] starting at (m0, n0).
+struct EnvTile {
+    int out, m0, n0;
+};
+// Phase p computes tiles[phase_beg[p] .. phase_beg[p+1]) (outputs overwritten,
+// beta ignored); after the last phase, res[q] = sum of *finals[i] for i in
+// [final_beg[q], final_beg[q+1]).  Returns false (nothing launched) when the
+// grid cannot be co-resident.
+bool launch_env_sweep(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins,
+                      const std::vector<EnvTile>& tiles, const std::vector<int>& phase_beg,
+                      const std::vector<const double*>& finals, const std::vector<int>& final_beg, double* res,
+                      GridSync* gs);
+
 }  // namespace bsm

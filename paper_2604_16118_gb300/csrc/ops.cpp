@@ -1108,7 +1108,8 @@ Mpo identity_mpo(const Layout& L) {
 }
 }  // namespace
 
-std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs) {
+// Per-site launches (used when the persistent sweep cannot be resident).
+static std::vector<double> dot_batch_sitewise(Context* ctx, const std::vector<EnvProblem>& probs) {
     const int P = (int)probs.size();
     std::vector<double> result(P, 0.0);
     if (P == 0) return result;
@@ -1262,6 +1263,202 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
     BSM_CUDA(cudaMemcpyAsync(result.data(), res, sizeof(double) * P, cudaMemcpyDeviceToHost, ctx->stream));
     ctx->sync();
     if (prevbuf) ctx->free(prevbuf);
+    return result;
+}
+
+// <S_a a, O S_b b> for a batch, all sites in one persistent launch.  The left
+// environment E_t of a problem is a list of blocks (MPO channel c, sector ia of
+// a, sector ib of b) at bond t; site t takes two phases: T = E X_b(ib, s_in)
+// and E'(c', ra, rb) = sum over MPO entries (c -> c', s_out, s_in) of
+// alpha X_a(ia, s_out)^T T, with alpha = w f_a f_b.  E lives in two ping-pong
+// buffers, T in one buffer; the structure of every site follows on the host
+// from the layouts.
+std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs) {
+    const int P = (int)probs.size();
+    std::vector<double> result(P, 0.0);
+    if (P == 0) return result;
+    const int K = probs[0].a->lay.K;
+    std::vector<Mpo> ids;
+    ids.reserve(P);
+    std::vector<const Mpo*> ops(P);
+    for (int p = 0; p < P; ++p) {
+        const EnvProblem& pr = probs[p];
+        BSM_REQUIRE(same_space(pr.a->lay, pr.b->lay) && pr.a->lay.K == K, BSMPS_ERR_INVALID_ARG,
+                    "dot of MPS of different spaces");
+        if (pr.W) {
+            BSM_REQUIRE(pr.W->K == K && pr.W->species == pr.a->lay.species, BSMPS_ERR_INVALID_ARG,
+                        "MPO and MPS act on different sites");
+            ops[p] = pr.W;
+        } else {
+            ids.push_back(identity_mpo(pr.a->lay));
+            ops[p] = &ids.back();
+        }
+    }
+    // buffer references: id 0 = T, 1 / 2 = E ping-pong, 3 = the 1x1 block [1], -1 = a real pointer
+    struct Ref {
+        int id;
+        int64_t off;
+        const double* ptr;
+    };
+    struct EBlk {
+        int c, ia, ib, rows, cols;
+        int64_t off;
+    };
+    std::vector<GemmOut> outs;
+    std::vector<GemmIn> ins;
+    std::vector<Ref> out_ref, ina_ref, inb_ref;
+    std::vector<EnvTile> tiles;
+    std::vector<int> phase_beg{0};
+    int64_t maxT = 1, maxE = 1;
+    std::vector<std::vector<EBlk>> E(P);
+    for (int p = 0; p < P; ++p) {
+        const Layout& A = probs[p].a->lay;
+        const Layout& B = probs[p].b->lay;
+        if (!A.bonds[0].q.empty() && !B.bonds[0].q.empty()) E[p].push_back({0, 0, 0, 1, 1, 0});
+    }
+    auto add_tiles = [&](int o) {
+        for (int m0 = 0; m0 < outs[o].M; m0 += 32)
+            for (int n0 = 0; n0 < outs[o].N; n0 += 32) tiles.push_back({o, m0, n0});
+    };
+    struct Contrib {
+        uint64_t key;
+        int seq, ti, ab;
+        double alpha;
+    };
+    for (int t = 0; t < K; ++t) {
+        const int eid = t == 0 ? 3 : 1 + (t % 2);   // buffer of E at bond t
+        const int nid = 1 + ((t + 1) % 2);          // buffer of E at bond t + 1
+        struct TBlk {
+            int env, sigma, rows, cols;
+            int64_t off;
+        };
+        std::vector<std::vector<TBlk>> T(P);
+        std::vector<std::vector<Contrib>> contrib(P);
+        int64_t tot_T = 0;
+        // ---- stage 1: T = E X_b ----
+        for (int p = 0; p < P; ++p) {
+            const Layout& A = probs[p].a->lay;
+            const Layout& B = probs[p].b->lay;
+            const std::vector<int> blook = block_lookup(B, t);
+            const std::vector<int> alook = block_lookup(A, t);
+            std::vector<std::array<int, 2>> tidx(E[p].size(), {-1, -1});
+            for (int e = 0; e < (int)E[p].size(); ++e)
+                for (int si = 0; si < 2; ++si) {
+                    const int bb = blook[E[p][e].ib * 2 + si];
+                    if (bb < 0) continue;
+                    tidx[e][si] = (int)T[p].size();
+                    const Block& bk = B.blocks[t][bb];
+                    T[p].push_back({e, si, E[p][e].rows, bk.cols, tot_T});
+                    const int o = (int)outs.size();
+                    outs.push_back({nullptr, E[p][e].rows, bk.cols, bk.cols, (int)ins.size(), (int)ins.size() + 1, 0.0});
+                    out_ref.push_back({0, tot_T, nullptr});
+                    ins.push_back({nullptr, nullptr, E[p][e].cols, E[p][e].cols, bk.cols, 0, 1.0});
+                    ina_ref.push_back({eid, E[p][e].off, nullptr});
+                    inb_ref.push_back({-1, 0, probs[p].b->core[t] + bk.off});
+                    add_tiles(o);
+                    tot_T += (int64_t)E[p][e].rows * bk.cols;
+                }
+            // env blocks by channel
+            const Mpo& W = *ops[p];
+            const int nch = W.bond_dim(t);
+            std::vector<std::vector<int>> by_chan(nch);
+            for (int e = 0; e < (int)E[p].size(); ++e) by_chan[E[p][e].c].push_back(e);
+            int seq = 0;
+            for (int ei = 0; ei < (int)W.entries[t].size(); ++ei) {
+                const MpoEntry& me = W.entries[t][ei];
+                if (me.a >= nch || by_chan[me.a].empty()) continue;
+                double w = me.w;
+                if (probs[p].W && t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1]))
+                    w += probs[p].shift;
+                double fa = 1.0, fb = 1.0;
+                if (me.so == 0 ? probs[p].fa0 : probs[p].fa1) fa = (*(me.so == 0 ? probs[p].fa0 : probs[p].fa1))[t];
+                if (me.si == 0 ? probs[p].fb0 : probs[p].fb1) fb = (*(me.si == 0 ? probs[p].fb0 : probs[p].fb1))[t];
+                const double alpha = w * fa * fb;
+                for (int e : by_chan[me.a]) {
+                    const int ab = alook[E[p][e].ia * 2 + me.so];
+                    const int ti = tidx[e][me.si];
+                    if (ab < 0 || ti < 0) continue;
+                    const int bb = blook[E[p][e].ib * 2 + me.si];
+                    const uint64_t ra = (uint64_t)A.blocks[t][ab].ri, rb = (uint64_t)B.blocks[t][bb].ri;
+                    const uint64_t key = ((uint64_t)me.b << 42) | (ra << 21) | rb;
+                    contrib[p].push_back({key, seq++, ti, ab, alpha});
+                }
+            }
+        }
+        maxT = std::max(maxT, tot_T);
+        phase_beg.push_back((int)tiles.size());
+        // ---- stage 2: E'(d, ra, rb) = sum alpha X_a^T T ----
+        int64_t tot_E = 0;
+        std::vector<std::vector<EBlk>> En(P);
+        for (int p = 0; p < P; ++p) {
+            const Layout& A = probs[p].a->lay;
+            const Layout& B = probs[p].b->lay;
+            std::vector<Contrib>& cs = contrib[p];
+            std::sort(cs.begin(), cs.end(), [](const Contrib& x, const Contrib& y) {
+                return x.key != y.key ? x.key < y.key : x.seq < y.seq;
+            });
+            for (size_t i = 0; i < cs.size();) {
+                size_t j = i;
+                while (j < cs.size() && cs[j].key == cs[i].key) ++j;
+                const int d = (int)(cs[i].key >> 42), ra = (int)((cs[i].key >> 21) & 0x1fffff),
+                          rb = (int)(cs[i].key & 0x1fffff);
+                const int rows = A.bonds[t + 1].dim[ra], cols = B.bonds[t + 1].dim[rb];
+                En[p].push_back({d, ra, rb, rows, cols, tot_E});
+                const int o = (int)outs.size();
+                outs.push_back({nullptr, rows, cols, cols, (int)ins.size(), 0, 0.0});
+                out_ref.push_back({nid, tot_E, nullptr});
+                for (size_t u = i; u < j; ++u) {
+                    const TBlk& tb = T[p][cs[u].ti];
+                    const Block& abk = A.blocks[t][cs[u].ab];
+                    ins.push_back({nullptr, nullptr, abk.rows, abk.cols, tb.cols, 1, cs[u].alpha});
+                    ina_ref.push_back({-1, 0, probs[p].a->core[t] + abk.off});
+                    inb_ref.push_back({0, tb.off, nullptr});
+                }
+                outs[o].end = (int)ins.size();
+                add_tiles(o);
+                tot_E += (int64_t)rows * cols;
+                i = j;
+            }
+        }
+        maxE = std::max(maxE, tot_E);
+        phase_beg.push_back((int)tiles.size());
+        E.swap(En);
+    }
+    // buffers, then the references resolved
+    Scratch s(ctx);
+    double* base[4];
+    base[0] = s.dbl((size_t)maxT);
+    base[1] = s.dbl((size_t)maxE);
+    base[2] = s.dbl((size_t)maxE);
+    {
+        std::vector<double> one(1, 1.0);
+        base[3] = s.up(one);
+    }
+    double* res = s.dbl((size_t)P);
+    GridSync* gs = (GridSync*)ctx->alloc(sizeof(GridSync));
+    s.ptrs.push_back(gs);
+    BSM_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), ctx->stream));
+    auto resolve = [&](const Ref& r) -> const double* { return r.id < 0 ? r.ptr : base[r.id] + r.off; };
+    for (size_t o = 0; o < outs.size(); ++o) outs[o].C = (double*)resolve(out_ref[o]);
+    for (size_t i = 0; i < ins.size(); ++i) {
+        ins[i].A = resolve(ina_ref[i]);
+        ins[i].B = resolve(inb_ref[i]);
+    }
+    // bond K: the remaining 1x1 blocks of every problem
+    const int fid = 1 + (K % 2);
+    std::vector<const double*> finals;
+    std::vector<int> final_beg{0};
+    for (int p = 0; p < P; ++p) {
+        for (const EBlk& eb : E[p]) finals.push_back(base[fid] + eb.off);
+        final_beg.push_back((int)finals.size());
+    }
+    if (!launch_env_sweep(ctx, outs, ins, tiles, phase_beg, finals, final_beg, res, gs))
+        return dot_batch_sitewise(ctx, probs);
+    GridSync h;
+    BSM_CUDA(cudaMemcpyAsync(result.data(), res, sizeof(double) * P, cudaMemcpyDeviceToHost, ctx->stream));
+    BSM_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    BSM_REQUIRE(h.err == 0, BSMPS_ERR_TIMEOUT, "inner-product sweep: a grid-wide wait gave up");
     return result;
 }
 

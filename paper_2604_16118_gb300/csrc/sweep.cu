@@ -658,6 +658,54 @@ struct Prof {
     }
 };
 
+
+// Environment sweep: every phase is a set of independent output tiles of
+// grouped GEMMs whose inputs may have been written in earlier phases (loads go
+// through L2); one thread per output entry, the K loop reading A and B
+// directly so that no FP64 instruction is spent on padding.
+constexpr int kEnvThreads = 128;
+
+__global__ void __launch_bounds__(kEnvThreads) k_env_sweep(const GemmOut* __restrict__ outs,
+                                                           const GemmIn* __restrict__ ins,
+                                                           const EnvTile* __restrict__ tiles,
+                                                           const int* __restrict__ phase_beg, int n_phase,
+                                                           const double* const* __restrict__ finals,
+                                                           const int* __restrict__ final_beg, int n_prob,
+                                                           double* __restrict__ res, GridSync* gs) {
+    __shared__ int s_flag;
+    for (int p = 0; p < n_phase; ++p) {
+        for (int ti = phase_beg[p] + (int)blockIdx.x; ti < phase_beg[p + 1]; ti += (int)gridDim.x) {
+            const EnvTile tl = tiles[ti];
+            const GemmOut o = outs[tl.out];
+            const int tm = min(32, o.M - tl.m0), tn = min(32, o.N - tl.n0);
+            for (int e = threadIdx.x; e < tm * tn; e += kEnvThreads) {
+                const int m = tl.m0 + e / tn, n = tl.n0 + e % tn;
+                double acc = 0.0;
+                for (int c = o.beg; c < o.end; ++c) {
+                    const GemmIn in = ins[c];
+                    double part = 0.0;
+                    if (in.transA) {
+                        for (int k = 0; k < in.K; ++k)
+                            part = fma(__ldcg(in.A + (int64_t)k * in.lda + m), __ldcg(in.B + (int64_t)k * in.ldb + n), part);
+                    } else {
+                        for (int k = 0; k < in.K; ++k)
+                            part = fma(__ldcg(in.A + (int64_t)m * in.lda + k), __ldcg(in.B + (int64_t)k * in.ldb + n), part);
+                    }
+                    acc = fma(in.alpha, part, acc);
+                }
+                o.C[(int64_t)m * o.ldc + n] = acc;
+            }
+        }
+        if (!phase_end(gs, (unsigned)p, &s_flag, [] {})) return;
+    }
+    if (blockIdx.x == 0)
+        for (int q = threadIdx.x; q < n_prob; q += kEnvThreads) {
+            double sum = 0.0;
+            for (int i = final_beg[q]; i < final_beg[q + 1]; ++i) sum += __ldcg(finals[i]);
+            res[q] = sum;
+        }
+}
+
 }  // namespace
 
 bool left_site_fits(int M, int N, int64_t rx_fma) { return left_smem(M, N) <= kSweepSmem && rx_fma <= kFusedGemmMaxFma; }
@@ -872,6 +920,49 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const s
     count_launch(ctx);
     pr.done();
     if (ctx->profiling) *prof_idx = (int)ctx->prof.size() - 1;
+    return true;
+}
+
+bool launch_env_sweep(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins,
+                      const std::vector<EnvTile>& tiles, const std::vector<int>& phase_beg,
+                      const std::vector<const double*>& finals, const std::vector<int>& final_beg, double* res,
+                      GridSync* gs) {
+    const int n_phase = (int)phase_beg.size() - 1;
+    const int n_prob = (int)final_beg.size() - 1;
+    if (n_phase <= 0 || n_prob <= 0) return false;
+    int maxt = 1;
+    for (int p = 0; p < n_phase; ++p) maxt = std::max(maxt, phase_beg[p + 1] - phase_beg[p]);
+    double fl = 0.0, by = 0.0;
+    for (const GemmOut& o : outs)
+        for (int c = o.beg; c < o.end; ++c) {
+            fl += 2.0 * o.M * o.N * (double)ins[c].K;
+            by += 8.0 * ((double)o.M * ins[c].K + (double)ins[c].K * o.N);
+        }
+    const int cap = coresident_ctas(k_env_sweep, kEnvThreads, 0);
+    if (cap <= 0) return false;
+    const int grid = std::min(maxt, cap);
+    ctx->flops += fl;
+    Pack pk;
+    const size_t oo = pk.add(outs), oi = pk.add(ins), ot = pk.add(tiles), op = pk.add(phase_beg), of = pk.add(finals),
+                 ob = pk.add(final_beg);
+    Scratch s(ctx);
+    unsigned char* d = upload_pack(s, pk);
+    const GemmOut* a0 = (const GemmOut*)(d + oo);
+    const GemmIn* a1 = (const GemmIn*)(d + oi);
+    const EnvTile* a2 = (const EnvTile*)(d + ot);
+    const int* a3 = (const int*)(d + op);
+    int a4 = n_phase;
+    const double* const* a5 = (const double* const*)(d + of);
+    const int* a6 = (const int*)(d + ob);
+    int a7 = n_prob;
+    double* a8 = res;
+    GridSync* a9 = gs;
+    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9};
+    Prof pr(ctx, KK_GEMM, fl, by);
+    BSM_CUDA(cudaLaunchCooperativeKernel((const void*)k_env_sweep, dim3(grid), dim3(kEnvThreads), args, 0,
+                                         ctx->stream));
+    count_launch(ctx);
+    pr.done();
     return true;
 }
 
