@@ -47,6 +47,36 @@ __device__ __forceinline__ double seg_sum(double v, int S) {
     return v;
 }
 
+// acc + sum_{k < n} a[k sa] b[k sb] with the global loads issued eight terms
+// at a time, so that a dot product of length n waits for about n/8 memory
+// round trips instead of n.  CGA / CGB: loads of a / b through L2 (global
+// data written by other CTAs of the same launch); otherwise plain loads (which
+// also serve shared-memory operands).
+template <bool CGA, bool CGB>
+__device__ __forceinline__ double dot_global(const double* a, int64_t sa, const double* b, int64_t sb, int n,
+                                             double acc) {
+    for (int k0 = 0; k0 < n; k0 += 8) {
+        double x[8], y[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u;
+            if (k < n) {
+                if constexpr (CGA) x[u] = __ldcg(a + (int64_t)k * sa);
+                else x[u] = a[(int64_t)k * sa];
+                if constexpr (CGB) y[u] = __ldcg(b + (int64_t)k * sb);
+                else y[u] = b[(int64_t)k * sb];
+            } else {
+                x[u] = 0.0;
+                y[u] = 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (k0 + u < n) acc = fma(x[u], y[u], acc);
+    }
+    return acc;
+}
+
 __device__ __forceinline__ int pow2_at_least(int n) {
     int s = 1;
     while (s < n) s <<= 1;
@@ -264,9 +294,12 @@ __device__ __forceinline__ void jacobi_rotation_fast(double a, double b, double 
         df = __double2float_rn(d * sc);
         gf = __double2float_rn(g2 * sc);
     }
-    const float r = sqrtf(fmaf(df, df, gf * gf));
+    // the angle only needs FP32 accuracy: hardware reciprocal square root and
+    // fast division (the larger of |df|, |gf| is at least 2^-60, so both are in range)
+    const float w = fmaf(df, df, gf * gf);
+    const float r = w * rsqrtf(w);
     const float sz = (df == 0.0f || ((df > 0.0f) == (gf > 0.0f))) ? 1.0f : -1.0f;
-    const double t = (double)(sz * fabsf(gf) / (fabsf(df) + r));
+    const double t = (double)(sz * __fdividef(fabsf(gf), fabsf(df) + r));
     const double cd = rsqrt(fma(t, t, 1.0));
     *c = cd;
     *s = cd * t;

@@ -118,13 +118,10 @@ __global__ void __launch_bounds__(kSmallGemmThreads) k_gemm_small(const GemmOut*
         for (int c = o.beg; c < o.end; ++c) {
             const GemmIn in = ins[c];
             double part = 0.0;
-            if (in.transA) {
-                for (int k = 0; k < in.K; ++k)
-                    part = fma(in.A[(int64_t)k * in.lda + m], in.B[(int64_t)k * in.ldb + n], part);
-            } else {
-                for (int k = 0; k < in.K; ++k)
-                    part = fma(in.A[(int64_t)m * in.lda + k], in.B[(int64_t)k * in.ldb + n], part);
-            }
+            if (in.transA)
+                part = dev::dot_global<false, false>(in.A + m, in.lda, in.B + n, in.ldb, in.K, 0.0);
+            else
+                part = dev::dot_global<false, false>(in.A + (int64_t)m * in.lda, 1, in.B + n, in.ldb, in.K, 0.0);
             acc = fma(in.alpha, part, acc);
         }
         double* cp = o.C + (int64_t)m * o.ldc + n;

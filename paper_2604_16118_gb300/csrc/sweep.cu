@@ -81,7 +81,7 @@ __device__ void left_rank1(const LeftTask& tk, const LeftSrc* __restrict__ srcs,
         const LeftX lx = xs[x];
         for (int c = threadIdx.x; c < lx.cols; c += nthreads()) {
             double acc = 0.0;
-            for (int j = 0; j < N; ++j) acc = fma(sgn * A[(int64_t)j], ldd<CG>(lx.X + (int64_t)j * lx.cols + c), acc);
+            acc = sgn * dev::dot_global<false, CG>(A, 1, lx.X + c, lx.cols, N, 0.0);
             lx.dst[c] = acc;
         }
     }
@@ -134,7 +134,7 @@ __device__ void left_body(const LeftTask& tk, const LeftSrc* __restrict__ srcs, 
         for (int64_t e = threadIdx.x; e < (int64_t)k * lx.cols; e += nthreads()) {
             const int r = (int)(e / lx.cols), c = (int)(e % lx.cols);
             double acc = 0.0;
-            for (int j = r; j < N; ++j) acc = fma(R[(int64_t)r * N + j], ldd<CG>(lx.X + (int64_t)j * lx.cols + c), acc);
+            acc = dev::dot_global<false, CG>(R + (int64_t)r * N + r, 1, lx.X + (int64_t)r * lx.cols + c, lx.cols, N - r, acc);
             lx.dst[e] = acc;
         }
     }
@@ -330,8 +330,7 @@ __device__ void right_body(const DynTask& tk, const DynPart* __restrict__ parts,
             double v;
             if (pt.US) {
                 v = 0.0;
-                for (int q = 0; q < pt.xcols; ++q)
-                    v = fma(ldd<CG>(pt.X + (int64_t)i * pt.xcols + q), ldd<CG>(pt.US + (int64_t)q * pt.ldus + cc), v);
+                v = dev::dot_global<CG, CG>(pt.X + (int64_t)i * pt.xcols, 1, pt.US + cc, pt.ldus, pt.xcols, 0.0);
             } else {
                 v = ldd<CG>(pt.X + (int64_t)i * pt.xcols + cc);
             }
@@ -685,11 +684,9 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_sweep(const GemmOut* __rest
                     const GemmIn in = ins[c];
                     double part = 0.0;
                     if (in.transA) {
-                        for (int k = 0; k < in.K; ++k)
-                            part = fma(__ldcg(in.A + (int64_t)k * in.lda + m), __ldcg(in.B + (int64_t)k * in.ldb + n), part);
+                        part = dev::dot_global<true, true>(in.A + m, in.lda, in.B + n, in.ldb, in.K, 0.0);
                     } else {
-                        for (int k = 0; k < in.K; ++k)
-                            part = fma(__ldcg(in.A + (int64_t)m * in.lda + k), __ldcg(in.B + (int64_t)k * in.ldb + n), part);
+                        part = dev::dot_global<true, true>(in.A + (int64_t)m * in.lda, 1, in.B + n, in.ldb, in.K, 0.0);
                     }
                     acc = fma(in.alpha, part, acc);
                 }
