@@ -162,6 +162,15 @@ BSMPS_API bsmps_status bsmps_ctx_profile(bsmps_ctx ctx, int enable);
 BSMPS_API bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset, int64_t* launches,
                                               double* ms, double* flops, double* bytes);
 
+/* Diagnostic of the bounded grid-wide waits used by the persistent sweep
+ * kernels (no counterpart in the paper).  Launches a two-CTA cooperative
+ * kernel whose CTAs meet at one grid-wide phase boundary.  skip_cta < 0: both
+ * arrive, *timed_out = 0.  skip_cta = 0 or 1: that CTA returns without
+ * arriving, the other one gives up after the wait limit (about 1 s), and
+ * *timed_out = 1; the context stays usable.  Errors: INVALID_ARG (skip_cta >
+ * 1), CUDA. */
+BSMPS_API bsmps_status bsmps_check_grid_wait(bsmps_ctx ctx, int skip_cta, int* timed_out);
+
 /* ---- MPS ----------------------------------------------------------------- */
 
 /* Number of float64 entries of a fresh random iterate of maximal rank r_max

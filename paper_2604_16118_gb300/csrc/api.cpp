@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "kernels.h"
 #include "solver.h"
 
 struct bsmps_ctx_s {
@@ -222,6 +223,13 @@ bsmps_status bsmps_ctx_destroy(bsmps_ctx ctx) {
     });
     delete ctx;
     return s;
+}
+
+bsmps_status bsmps_check_grid_wait(bsmps_ctx ctx, int skip_cta, int* timed_out) {
+    return guarded(ctx, [&] {
+        BSM_REQUIRE(timed_out != nullptr && skip_cta <= 1, BSMPS_ERR_INVALID_ARG, "skip_cta must be < 2");
+        *timed_out = bsm::check_grid_wait(C(ctx), skip_cta < 0 ? -1 : skip_cta) != 0 ? 1 : 0;
+    });
 }
 
 bsmps_status bsmps_ctx_sync(bsmps_ctx ctx) {

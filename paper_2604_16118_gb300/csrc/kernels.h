@@ -223,4 +223,8 @@ bool launch_env_sweep(Context* ctx, const std::vector<GemmOut>& outs, const std:
                       const std::vector<const double*>& finals, const std::vector<int>& final_beg, double* res,
                       GridSync* gs);
 
+// Two-CTA cooperative kernel meeting at one phase boundary; CTA skip_cta (if
+// >= 0) never arrives.  Returns the error word of the wait (1: a wait gave up).
+int check_grid_wait(Context* ctx, int skip_cta);
+
 }  // namespace bsm

@@ -498,45 +498,38 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Phase p ends; `tail` runs on the last CTA to arrive.  False: give up.
-template <class F>
-__device__ bool phase_end(GridSync* gs, unsigned int p, int* s_flag, F&& tail) {
+// Phase p ends: every CTA arrives at a monotonic counter (acquire-release at
+// GPU scope, so the CTA's writes before the barrier are visible to every CTA
+// after it); the last CTA to arrive releases the phase, the others poll with
+// acquire loads.  Returns false when the wait gave up (error word set).
+__device__ bool phase_end(GridSync* gs, unsigned int p, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int t = atomicAdd(&gs->arrive, 1u);
-        *s_flag = (t == (p + 1) * gridDim.x - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (*s_flag == 1) {
-        __threadfence();
-        tail();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicExch(&gs->release, p + 1);
-        }
-        __syncthreads();
-        return true;
-    }
-    if (threadIdx.x == 0) {
-        const unsigned long long t0 = global_ns();
-        int ok = 1;
-        for (;;) {
-            if (*(volatile unsigned int*)&gs->release >= p + 1) break;
-            if (*(volatile int*)&gs->err) {
-                ok = 0;
-                break;
+        unsigned int t;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(&gs->arrive) : "memory");
+        if (t == (p + 1) * gridDim.x - 1) {
+            asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(&gs->release), "r"(p + 1) : "memory");
+            *s_flag = 2;
+        } else {
+            const unsigned long long t0 = global_ns();
+            int ok = 1;
+            for (;;) {
+                unsigned int r;
+                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(r) : "l"(&gs->release) : "memory");
+                if (r >= p + 1) break;
+                if (*(volatile int*)&gs->err) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > kWaitLimitNs) {
+                    atomicExch(&gs->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
-            if (global_ns() - t0 > kWaitLimitNs) {
-                atomicExch(&gs->err, 1);
-                ok = 0;
-                break;
-            }
-            __nanosleep(40);
+            *s_flag = ok ? 2 : 3;
         }
-        __threadfence();
-        *s_flag = ok ? 2 : 3;
     }
     __syncthreads();
     return *s_flag == 2;
@@ -556,7 +549,7 @@ __global__ void __launch_bounds__(kThreads) k_left_sweep(const LeftTask* __restr
             __syncthreads();
             left_body<true>(tasks[ti], srcs, xs, sm, red, sh);
         }
-        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag, [] {})) return;
+        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag)) return;
     }
 }
 
@@ -580,18 +573,24 @@ __global__ void __launch_bounds__(kThreads) k_right_sweep(const DynTask* __restr
             right_body<true>(tk, parts, sm, red, sh, &s_rot, s_cols);
             // the CTA that completes the last task of this truncation's bond runs its cut
             __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                const CutTask& ct = cuts[tk.cut];
-                s_flag = atomicAdd(ct.done, 1) == ct.n_tasks - 1 ? 1 : 0;
-            }
-            __syncthreads();
-            if (s_flag) {
-                __threadfence();
-                cut_body<true>(cuts[tk.cut], secs, sm, &s_n);
+            const CutTask& ct = cuts[tk.cut];
+            if (ct.n_tasks == 1) {
+                // the only sector of this truncation's bond: its own CTA cuts
+                cut_body<true>(ct, secs, sm, &s_n);
+            } else {
+                if (threadIdx.x == 0) {
+                    unsigned int old;
+                    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;"
+                                 : "=r"(old)
+                                 : "l"((unsigned int*)ct.done)
+                                 : "memory");
+                    s_flag = (int)old == ct.n_tasks - 1 ? 1 : 0;
+                }
+                __syncthreads();
+                if (s_flag) cut_body<true>(ct, secs, sm, &s_n);
             }
         }
-        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag, [] {})) return;
+        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag)) return;
     }
 }
 
@@ -693,7 +692,7 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_sweep(const GemmOut* __rest
                 o.C[(int64_t)m * o.ldc + n] = acc;
             }
         }
-        if (!phase_end(gs, (unsigned)p, &s_flag, [] {})) return;
+        if (!phase_end(gs, (unsigned)p, &s_flag)) return;
     }
     if (blockIdx.x == 0)
         for (int q = threadIdx.x; q < n_prob; q += kEnvThreads) {
@@ -701,6 +700,13 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_sweep(const GemmOut* __rest
             for (int i = final_beg[q]; i < final_beg[q + 1]; ++i) sum += __ldcg(finals[i]);
             res[q] = sum;
         }
+}
+
+// One phase boundary between two CTAs; CTA skip_cta returns without arriving.
+__global__ void k_grid_wait_check(int skip_cta, GridSync* gs) {
+    __shared__ int s_flag;
+    if ((int)blockIdx.x == skip_cta) return;
+    phase_end(gs, 0u, &s_flag);
 }
 
 }  // namespace
@@ -961,6 +967,22 @@ bool launch_env_sweep(Context* ctx, const std::vector<GemmOut>& outs, const std:
     count_launch(ctx);
     pr.done();
     return true;
+}
+
+int check_grid_wait(Context* ctx, int skip_cta) {
+    Scratch s(ctx);
+    GridSync* gs = (GridSync*)ctx->alloc(sizeof(GridSync));
+    s.ptrs.push_back(gs);
+    BSM_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), ctx->stream));
+    int a0 = skip_cta;
+    GridSync* a1 = gs;
+    void* args[] = {&a0, &a1};
+    BSM_CUDA(cudaLaunchCooperativeKernel((const void*)k_grid_wait_check, dim3(2), dim3(32), args, 0, ctx->stream));
+    count_launch(ctx);
+    GridSync h;
+    BSM_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    return h.err;
 }
 
 }  // namespace bsm

@@ -89,6 +89,7 @@ _SIGS = {
     "bsmps_precondition": (_i, [_vp, C.POINTER(Precond), _i, _vp, C.POINTER(_vp), _pi]),
     "bsmps_dot": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
     "bsmps_dot_noalloc": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
+    "bsmps_check_grid_wait": (_i, [_vp, _i, C.POINTER(C.c_int)]),
     "bsmps_mlp_create": (_i, [_vp, _i, _pi, C.POINTER(C.c_float), _i64, C.POINTER(_vp)]),
     "bsmps_mlp_num_params": (_i, [_vp, _pi64]),
     "bsmps_mlp_get_params": (_i, [_vp, C.POINTER(C.c_float)]),
@@ -372,6 +373,13 @@ def dot_noalloc(ctx, a, b, mpo=None, shift=0.0):
     _check(ctx, lib().bsmps_dot_noalloc(ctx.h, a.h, b.h, mpo.h if mpo is not None else None, shift,
                                         C.byref(out)))
     return out.value
+
+
+def check_grid_wait(ctx, skip_cta=-1):
+    """True when a grid-wide wait gave up (bsmps_check_grid_wait)."""
+    out = C.c_int()
+    _check(ctx, lib().bsmps_check_grid_wait(ctx.h, skip_cta, C.byref(out)))
+    return bool(out.value)
 
 
 def solver_params(c, delta, eps_num=None, t_eig=0.5, tau=1e-8, r_max=0, u_rel=1e-13):
