@@ -205,3 +205,59 @@ def step(x, mpo, prec, params, state):
     state.history.append(info)
     state.n += 1
     return xnext, info
+
+
+def outer_constants(c, K, alpha):
+    """kappa of Eq. (kappadef) and theta of Thm. quasioptr."""
+    kappa = math.sqrt((1.0 + c) / (1.0 - c)) * math.sqrt(K - 1)
+    theta = (1.0 + alpha) * kappa / (2.0 * (1.0 + (1.0 + alpha) * kappa))
+    return kappa, theta
+
+
+def outer(y0, mpo, prec, params, tau, alpha=1.0, max_outer=20, max_inner=100, keep=False):
+    """Outer perturbed inverse iteration (Alg. 3), D = 1.
+
+    eta_0 = 1/(2 theta); in outer step m the inner iteration (Alg. 2, fresh
+    state) runs from y^m until its eigenvector bound is at most
+    tau_m = eta_m / (2 (1 + (1 + alpha) kappa)); the outer iteration stops when
+    the relative eigenvalue bound of Eq. (releigerr) at the inner result is
+    below tau, else y^{m+1} = trunc_{theta eta_m}(y^+) (Euclidean tolerance, as
+    trunc is defined in Sec. 2.2) and eta_{m+1} = eta_m / 2.
+
+    Readings: alpha is not fixed by the paper (alpha = 1 by default); the rank
+    cap params.r_max applies inside the inner iteration only.
+    Returns (y, records, converged); records[m] holds the inner step count,
+    lambda, rho and bounds at y^+, eta_m, tau_m, and the ranks after the outer
+    truncation (keep=True: also y^+ and y^{m+1})."""
+    kappa, theta = outer_constants(params.c, y0.K, alpha)
+    eta = 1.0 / (2.0 * theta)
+    y = y0
+    records = []
+    for m in range(max_outer):
+        tau_m = eta / (2.0 * (1.0 + (1.0 + alpha) * kappa))
+        inner = SolverParams(params.c, params.delta, params.eps_num, params.t_eig, tau_m, params.r_max)
+        st = SolverState()
+        info = None
+        n_inner = 0
+        for _ in range(max_inner):
+            y, info = step(y, mpo, prec, inner, st)
+            n_inner += 1
+            if info["converged"]:
+                break
+        rec = {"m": m, "inner_steps": n_inner, "inner_converged": bool(info["converged"]),
+               "lambda": info["lambda"], "rho": info["rho"], "bound": info["bound"],
+               "releig_bound": info["releig_bound"], "eta_out": eta, "tau_m": tau_m,
+               "ranks_before": y.ranks()}
+        if keep:
+            rec["y_plus"] = y
+        if info["releig_bound"] < tau:
+            rec["ranks_after"] = y.ranks()
+            records.append(rec)
+            return y, records, True
+        y, _, _ = B.truncate(y, theta * eta)
+        rec["ranks_after"] = y.ranks()
+        if keep:
+            rec["y_next"] = y
+        records.append(rec)
+        eta *= 0.5
+    return y, records, False
