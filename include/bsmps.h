@@ -311,6 +311,40 @@ BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const b
                                    bsmps_solver_state* state, bsmps_mps* x,
                                    bsmps_step_info* info);
 
+/* One outer step of Alg. 3 as reported by bsmps_eigensolve_outer. */
+typedef struct {
+    int inner_steps;       /* Alg. 2 steps run from y^m */
+    int inner_converged;   /* 1 when the inner termination test (bound <= tau_m) held */
+    double lambda;         /* lambda(y^+) */
+    double rho;            /* rho(y^+), Eq. (rhobound) */
+    double releig_bound;   /* Eq. (releigerr) at y^+ */
+    double eta_out;        /* eta_m */
+    double tau_m;          /* inner tolerance eta_m / (2 (1 + (1 + alpha) kappa)) */
+    int max_rank_before;   /* largest bond dimension of y^+ */
+    int max_rank_after;    /* largest bond dimension of y^{m+1} (of y^+ at the last step) */
+    double flops;          /* algorithmic FP64 flops of the outer step */
+} bsmps_outer_record;
+
+/* Outer perturbed inverse iteration (Alg. 3, one eigenvector): with
+ * kappa = sqrt((1+c)/(1-c)) sqrt(K-1) (Eq. (kappadef)) and
+ * theta = (1+alpha) kappa / (2 (1 + (1+alpha) kappa)) (Thm. quasioptr),
+ * eta_0 = 1/(2 theta); outer step m runs Alg. 2 steps from y^m (fresh state,
+ * eta_res = +inf) until the eigenvector bound of Thm. aposterbound is at most
+ * tau_m = eta_m / (2 (1 + (1+alpha) kappa)) or max_inner steps were taken;
+ * it stops when the relative eigenvalue bound of Eq. (releigerr) at the
+ * result y^+ is below tau, else y^{m+1} = trunc_{theta eta_m}(y^+) and
+ * eta_{m+1} = eta_m / 2.  params as for bsmps_eigensolve_step except that
+ * params->tau is ignored (the inner tolerance is tau_m); params->r_max caps the
+ * inner iterates only.  alpha > 0 is not fixed by the paper.  *x (y^0) is
+ * replaced by the final y^+ (the old handle is destroyed); records (may be
+ * NULL) receives up to max_outer records, *n_outer the number of outer steps,
+ * *converged 1 when the tau test held.  Errors: INVALID_ARG, NOT_SPD, NUMERIC,
+ * OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_eigensolve_outer(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
+                                              const bsmps_solver_params* params, double alpha, double tau,
+                                              int max_outer, int max_inner, bsmps_mps* x,
+                                              bsmps_outer_record* records, int* n_outer, int* converged);
+
 /* ---- learned preconditioner network ------------------------------------- *
  * A multilayer perceptron (no counterpart in the paper; it serves the learned
  * preconditioner controller that predicts preconditioner parameters from the

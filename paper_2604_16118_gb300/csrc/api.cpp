@@ -552,6 +552,35 @@ bsmps_status bsmps_dot_noalloc(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mp
     });
 }
 
+bsmps_status bsmps_eigensolve_outer(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
+                                    const bsmps_solver_params* params, double alpha, double tau, int max_outer,
+                                    int max_inner, bsmps_mps* x, bsmps_outer_record* records, int* n_outer,
+                                    int* converged) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(W && params && x && *x && n_outer && converged, BSMPS_ERR_INVALID_ARG, "null argument");
+        BSM_REQUIRE(params->c > 0.0 && params->c < 1.0 && params->delta > 1.0 && params->eps_num > 0.0 &&
+                        params->eps_num < 1.0 - params->c && params->t_eig > 0.0 && params->t_eig < 1.0 &&
+                        params->r_max >= 0 && params->u_rel >= 0.0 && params->u_rel < 1e-3,
+                    BSMPS_ERR_INVALID_ARG, "solver parameters out of range");
+        BSM_REQUIRE(alpha > 0.0 && tau > 0.0 && max_outer > 0 && max_inner > 0, BSMPS_ERR_INVALID_ARG,
+                    "alpha, tau, max_outer and max_inner must be positive");
+        const bsm::PrecondTerms P = bsm::make_precond(p);
+        BSM_REQUIRE(p->K == M(*x)->lay.K, BSMPS_ERR_INVALID_ARG, "precond K differs from the MPS");
+        std::vector<bsmps_outer_record> recs;
+        bool ok = false;
+        bsm::MpsPtr r = bsm::eigensolve_outer(c, W->W, P, *params, alpha, tau, max_outer, max_inner, M(*x), recs, &ok);
+        c->sync();
+        if (records)
+            for (size_t i = 0; i < recs.size(); ++i) records[i] = recs[i];
+        *n_outer = (int)recs.size();
+        *converged = ok ? 1 : 0;
+        bsmps_mps old = *x;
+        *x = wrap(std::move(r));
+        delete old;
+    });
+}
+
 bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
                                    const bsmps_solver_params* params, bsmps_solver_state* state, bsmps_mps* x,
                                    bsmps_step_info* info) {

@@ -1,3 +1,4 @@
+#include <limits>
 // Exponential-sum preconditioner (Sec. 4) and one step of the perturbed
 // preconditioned inverse iteration (Alg. 2), orchestrated on the host over
 // device MPS operations.
@@ -290,6 +291,67 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
     info.flops = ctx->flops - flops0;
     st.n += 1;
     return xn;
+}
+
+static int max_bond(const Mps* x) {
+    int mr = 0;
+    for (const Bond& b : x->lay.bonds) mr = std::max(mr, b.total());
+    return mr;
+}
+
+// Outer perturbed inverse iteration (Alg. 3, D = 1): inner Alg. 2 runs to the
+// eigenvector tolerance tau_m, the termination test of Eq. (releigerr), and the
+// rank-controlling truncation trunc_{theta eta_m} with eta halved per step
+// (kappa of Eq. (kappadef), theta and tau_m of Thm. quasioptr).
+MpsPtr eigensolve_outer(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
+                        double alpha, double tau, int max_outer, int max_inner, const Mps* y0,
+                        std::vector<bsmps_outer_record>& records, bool* converged) {
+    const int K = y0->lay.K;
+    const double kappa = std::sqrt((1.0 + prm.c) / (1.0 - prm.c)) * std::sqrt((double)std::max(K - 1, 1));
+    const double theta = (1.0 + alpha) * kappa / (2.0 * (1.0 + (1.0 + alpha) * kappa));
+    double eta = 1.0 / (2.0 * theta);
+    *converged = false;
+    records.clear();
+    MpsPtr y;
+    const Mps* cur = y0;
+    for (int m = 0; m < max_outer; ++m) {
+        const double tau_m = eta / (2.0 * (1.0 + (1.0 + alpha) * kappa));
+        bsmps_solver_params inner = prm;
+        inner.tau = tau_m;
+        bsmps_solver_state st{std::numeric_limits<double>::infinity(), 0};
+        bsmps_outer_record rec{};
+        const double fl0 = ctx->flops;
+        bsmps_step_info info{};
+        for (int n = 0; n < max_inner; ++n) {
+            MpsPtr nx = eigensolve_step(ctx, W, P, inner, st, cur, info);
+            y = std::move(nx);
+            cur = y.get();
+            rec.inner_steps = n + 1;
+            if (info.converged) break;
+        }
+        BSM_REQUIRE(rec.inner_steps > 0, BSMPS_ERR_INVALID_ARG, "max_inner must be positive");
+        rec.inner_converged = info.converged;
+        rec.lambda = info.lambda;
+        rec.rho = info.rho;
+        rec.releig_bound = info.releig_bound;
+        rec.eta_out = eta;
+        rec.tau_m = tau_m;
+        rec.max_rank_before = max_bond(cur);
+        if (info.releig_bound < tau) {
+            rec.max_rank_after = rec.max_rank_before;
+            rec.flops = ctx->flops - fl0;
+            records.push_back(rec);
+            *converged = true;
+            return y;
+        }
+        y = op_truncate(ctx, cur, theta * eta, 0, nullptr, nullptr);
+        cur = y.get();
+        rec.max_rank_after = max_bond(cur);
+        rec.flops = ctx->flops - fl0;
+        records.push_back(rec);
+        eta *= 0.5;
+    }
+    return y;
 }
 
 }  // namespace bsm

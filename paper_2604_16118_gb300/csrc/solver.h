@@ -26,5 +26,9 @@ void rr2(const double H[2][2], const double E[2][2], double* mu, double v[2]);
 double delta_A(double rho, double q);
 MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
                        bsmps_solver_state& st, const Mps* x, bsmps_step_info& info);
+// Alg. 3; records: one per outer step taken.
+MpsPtr eigensolve_outer(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
+                        double alpha, double tau, int max_outer, int max_inner, const Mps* y0,
+                        std::vector<bsmps_outer_record>& records, bool* converged);
 
 }  // namespace bsm

@@ -50,6 +50,18 @@ class StepInfo(C.Structure):
         return d
 
 
+class OuterRecord(C.Structure):
+    _fields_ = [("inner_steps", C.c_int), ("inner_converged", C.c_int), ("lambda_", C.c_double),
+                ("rho", C.c_double), ("releig_bound", C.c_double), ("eta_out", C.c_double),
+                ("tau_m", C.c_double), ("max_rank_before", C.c_int), ("max_rank_after", C.c_int),
+                ("flops", C.c_double)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["lambda"] = d.pop("lambda_")
+        return d
+
+
 _vp = C.c_void_p
 _i = C.c_int
 _d = C.c_double
@@ -90,6 +102,8 @@ _SIGS = {
     "bsmps_dot": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
     "bsmps_dot_noalloc": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
     "bsmps_check_grid_wait": (_i, [_vp, _i, C.POINTER(C.c_int)]),
+    "bsmps_eigensolve_outer": (_i, [_vp, _vp, _vp, _vp, _d, _d, _i, _i, C.POINTER(_vp), _vp,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "bsmps_mlp_create": (_i, [_vp, _i, _pi, C.POINTER(C.c_float), _i64, C.POINTER(_vp)]),
     "bsmps_mlp_num_params": (_i, [_vp, _pi64]),
     "bsmps_mlp_get_params": (_i, [_vp, C.POINTER(C.c_float)]),
@@ -399,6 +413,18 @@ def eigensolve_step(ctx, mpo, p, params, state, x):
     _check(ctx, code)
     x.h = None          # destroyed by the library
     return MPS(ctx, h), info.as_dict()
+
+
+def eigensolve_outer(ctx, mpo, p, params, x, tau, alpha=1.0, max_outer=20, max_inner=100):
+    """Alg. 3 from x (consumed); returns (y, records, converged)."""
+    h = _vp(x.h.value)
+    recs = (OuterRecord * max_outer)()
+    n = C.c_int()
+    ok = C.c_int()
+    _check(ctx, lib().bsmps_eigensolve_outer(ctx.h, mpo.h, C.byref(p), C.byref(params), alpha, tau, max_outer,
+                                             max_inner, C.byref(h), recs, C.byref(n), C.byref(ok)))
+    x.h = None          # destroyed by the library
+    return MPS(ctx, h), [recs[i].as_dict() for i in range(n.value)], bool(ok.value)
 
 
 def _fptr(a):
