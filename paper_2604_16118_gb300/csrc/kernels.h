@@ -156,14 +156,15 @@ struct DynPart {
 };
 // One sector of bond b: SVD of [part_0 | part_1] into padded outputs
 // (S: kpad, US: rows x kpad, Vt: kpad x ncols_pad); *kact receives the rank.
-struct DynTask {
+struct alignas(16) DynTask {
     int M, kpad, ncols_pad;
     int p_beg, p_end;
     double* S;
     double* US;
     double* Vt;
     int* kact;
-    int cut;   // index of the cut of this task's truncation and bond
+    int cut;           // index of the cut of this task's truncation and bond
+    DynPart part[2];   // copies of parts[p_beg .. p_end), filled by the launchers
 };
 // Cut of one bond: the singular values of its sectors (sector i: S[i] with
 // *kact[i] values) pooled and cut exactly as choose_cut; keep[i] receives the

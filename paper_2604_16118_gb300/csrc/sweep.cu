@@ -296,13 +296,13 @@ __device__ void right_rank1(const DynTask& tk, const double* v, int len, int wid
 }
 
 template <bool CG>
-__device__ void right_body(const DynTask& tk, const DynPart* __restrict__ parts, double* sm, double* red,
+__device__ void right_body(const DynTask& tk, double* sm, double* red,
                            double* sh, int* s_rot, int* s_cols) {
     const int np = tk.p_end - tk.p_beg;
     if (threadIdx.x < 2) {
         int c = 0;
         if ((int)threadIdx.x < np) {
-            const DynPart pt = parts[tk.p_beg + threadIdx.x];
+            const DynPart& pt = tk.part[threadIdx.x];
             c = pt.keep ? ldi<CG>(pt.keep) : pt.xcols;
         }
         s_cols[threadIdx.x] = c;
@@ -323,7 +323,7 @@ __device__ void right_body(const DynTask& tk, const DynPart* __restrict__ parts,
     int* perm = (int*)(Sraw + k);
     int coff = 0;
     for (int p = 0; p < np; ++p) {
-        const DynPart pt = parts[tk.p_beg + p];
+        const DynPart& pt = tk.part[p];
         const int cols = s_cols[p];
         for (int64_t e = threadIdx.x; e < (int64_t)M * cols; e += nthreads()) {
             const int i = (int)(e / cols), cc = (int)(e % cols), c = coff + cc;
@@ -378,14 +378,13 @@ __device__ void right_body(const DynTask& tk, const DynPart* __restrict__ parts,
     if (threadIdx.x == 0) *tk.kact = k;
 }
 
-__global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restrict__ tasks,
-                                                        const DynPart* __restrict__ parts) {
+__global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restrict__ tasks) {
     extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ double sh[2];
     __shared__ int s_rot;
     __shared__ int s_cols[2];
-    right_body<false>(tasks[blockIdx.x], parts, sm, red, sh, &s_rot, s_cols);
+    right_body<false>(tasks[blockIdx.x], sm, red, sh, &s_rot, s_cols);
 }
 
 // Pooled cut of one bond (one CTA): stable descending order with ties by
@@ -400,23 +399,26 @@ __device__ void cut_body(const CutTask& tk, const CutSector* __restrict__ secs, 
     int* sec = (int*)(sq + tk.cap_total);
     int* order = sec + tk.cap_total;
     int* off = order + tk.cap_total;   // n_sec + 1 (later: kept counts per sector)
+    // counts of all sectors in parallel, then their offsets
+    for (int i = threadIdx.x; i < tk.n_sec; i += nthreads()) off[i + 1] = ldi<CG>(secs[tk.s_beg + i].kact);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        int o = 0;
-        for (int i = 0; i < tk.n_sec; ++i) {
-            off[i] = o;
-            o += ldi<CG>(secs[tk.s_beg + i].kact);
-        }
-        off[tk.n_sec] = o;
-        s_n = o;
+        off[0] = 0;
+        for (int i = 0; i < tk.n_sec; ++i) off[i + 1] += off[i];
+        s_n = off[tk.n_sec];
     }
     __syncthreads();
     const int n = s_n;
-    for (int i = 0; i < tk.n_sec; ++i) {
-        const int c = off[i + 1] - off[i];
-        for (int j = threadIdx.x; j < c; j += nthreads()) {
-            val[off[i] + j] = ldd<CG>(secs[tk.s_beg + i].S + j);
-            sec[off[i] + j] = i;
+    // every singular value in parallel (its sector by binary search over the offsets)
+    for (int e = threadIdx.x; e < n; e += nthreads()) {
+        int lo = 0, hi = tk.n_sec - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= e) lo = mid;
+            else hi = mid - 1;
         }
+        val[e] = ldd<CG>(secs[tk.s_beg + lo].S + (e - off[lo]));
+        sec[e] = lo;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += nthreads()) {
@@ -553,12 +555,22 @@ __global__ void __launch_bounds__(kThreads) k_left_sweep(const LeftTask* __restr
     }
 }
 
+// cp.async of 16 bytes (global -> shared), completed by cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// phase_beg (n_phase + 1 ints) is staged in shared memory behind the body's
+// working set (offset pb_off bytes); the descriptor of a CTA's first task of
+// phase p + 1 is copied asynchronously while phase p runs.
 __global__ void __launch_bounds__(kThreads) k_right_sweep(const DynTask* __restrict__ tasks,
-                                                          const DynPart* __restrict__ parts,
                                                           const int* __restrict__ phase_beg,
                                                           const CutTask* __restrict__ cuts,
                                                           const CutSector* __restrict__ secs, int n_phase,
-                                                          GridSync* gs) {
+                                                          int pb_off, GridSync* gs) {
     extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ double sh[2];
@@ -566,11 +578,29 @@ __global__ void __launch_bounds__(kThreads) k_right_sweep(const DynTask* __restr
     __shared__ int s_cols[2];
     __shared__ int s_n;
     __shared__ int s_flag;
+    __shared__ DynTask s_task[2];
+    int* pb = (int*)((char*)sm + pb_off);
+    for (int i = threadIdx.x; i <= n_phase; i += nthreads()) pb[i] = phase_beg[i];
+    __syncthreads();
+    constexpr int kChunks = (int)(sizeof(DynTask) / 16);
+    auto prefetch = [&](int p) {
+        if (p < n_phase) {
+            const int ti = pb[p] + (int)blockIdx.x;
+            if (ti < pb[p + 1] && (int)threadIdx.x < kChunks)
+                cp_async16((char*)&s_task[p & 1] + 16 * threadIdx.x, (const char*)(tasks + ti) + 16 * threadIdx.x);
+        }
+        cp_async_commit();
+    };
+    prefetch(0);
     for (int p = 0; p < n_phase; ++p) {
-        for (int ti = phase_beg[p] + (int)blockIdx.x; ti < phase_beg[p + 1]; ti += (int)gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        prefetch(p + 1);
+        for (int ti = pb[p] + (int)blockIdx.x; ti < pb[p + 1]; ti += (int)gridDim.x) {
             __syncthreads();
-            const DynTask tk = tasks[ti];
-            right_body<true>(tk, parts, sm, red, sh, &s_rot, s_cols);
+            const bool first = ti == pb[p] + (int)blockIdx.x;
+            const DynTask& tk = first ? s_task[p & 1] : tasks[ti];
+            right_body<true>(tk, sm, red, sh, &s_rot, s_cols);
             // the CTA that completes the last task of this truncation's bond runs its cut
             __syncthreads();
             const CutTask& ct = cuts[tk.cut];
@@ -590,8 +620,12 @@ __global__ void __launch_bounds__(kThreads) k_right_sweep(const DynTask* __restr
                 if (s_flag) cut_body<true>(ct, secs, sm, &s_n);
             }
         }
-        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag)) return;
+        if (p + 1 < n_phase && !phase_end(gs, (unsigned)p, &s_flag)) {
+            cp_async_wait_all();
+            return;
+        }
     }
+    cp_async_wait_all();
 }
 
 // All task arrays of one launch in one upload.
@@ -801,8 +835,20 @@ void launch_right_apply(Context* ctx, const std::vector<RTask>& tasks, const std
 
 namespace bsm {
 
-int launch_right_dyn(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts) {
-    if (tasks.empty()) return -1;
+// Copies of each task's parts into the task (a sector has at most two: sigma 0 and 1).
+std::vector<DynTask> with_parts(const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts) {
+    std::vector<DynTask> out = tasks;
+    for (DynTask& t : out) {
+        BSM_REQUIRE(t.p_end - t.p_beg >= 0 && t.p_end - t.p_beg <= 2, BSMPS_ERR_INVALID_ARG,
+                    "a sector has at most two parts");
+        for (int i = 0; i < t.p_end - t.p_beg; ++i) t.part[i] = parts[t.p_beg + i];
+    }
+    return out;
+}
+
+int launch_right_dyn(Context* ctx, const std::vector<DynTask>& tasks_in, const std::vector<DynPart>& parts) {
+    if (tasks_in.empty()) return -1;
+    const std::vector<DynTask> tasks = with_parts(tasks_in, parts);
     size_t smem = 0;
     int kmax = 1;
     double fl = 0.0, by = 0.0;
@@ -814,13 +860,12 @@ int launch_right_dyn(Context* ctx, const std::vector<DynTask>& tasks, const std:
         by += 8.0 * ((double)t.M * t.ncols_pad + t.M * k + k * t.ncols_pad);
     }
     Pack pk;
-    const size_t ot = pk.add(tasks), op = pk.add(parts);
+    const size_t ot = pk.add(tasks);
     Scratch s(ctx);
     unsigned char* d = upload_pack(s, pk);
     Prof pr(ctx, KK_SVD, fl, by);
     allow_smem(k_right_dyn);
-    k_right_dyn<<<(unsigned)tasks.size(), block_for(kmax), smem, ctx->stream>>>((const DynTask*)(d + ot),
-                                                                               (const DynPart*)(d + op));
+    k_right_dyn<<<(unsigned)tasks.size(), block_for(kmax), smem, ctx->stream>>>((const DynTask*)(d + ot));
     count_launch(ctx);
     pr.done();
     return ctx->profiling ? (int)ctx->prof.size() - 1 : -1;
@@ -883,12 +928,13 @@ bool launch_left_sweep(Context* ctx, const std::vector<LeftTask>& tasks, const s
     return true;
 }
 
-bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const std::vector<DynPart>& parts,
+bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks_in, const std::vector<DynPart>& parts,
                         const std::vector<int>& phase_beg, const std::vector<CutTask>& cuts,
                         const std::vector<CutSector>& secs, GridSync* gs, int* prof_idx) {
     *prof_idx = -1;
     const int n_phase = (int)phase_beg.size() - 1;
     if (n_phase <= 0 || cuts.empty()) return false;
+    const std::vector<DynTask> tasks = with_parts(tasks_in, parts);
     size_t smem = 0;
     int kmax = 1, maxt = 1;
     double by = 0.0;
@@ -899,22 +945,24 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const s
     }
     for (const CutTask& c : cuts) smem = std::max(smem, cut_smem(c));
     for (int p = 0; p < n_phase; ++p) maxt = std::max(maxt, phase_beg[p + 1] - phase_beg[p]);
+    const size_t pb_off = (smem + 15) & ~size_t(15);   // phase_beg staged behind the working set
+    smem = pb_off + sizeof(int) * (size_t)(n_phase + 1);
+    if (smem > kSweepSmem) return false;
     const int threads = block_for(kmax);
     allow_smem(k_right_sweep);
     const int cap = coresident_ctas(k_right_sweep, threads, smem);
     if (cap <= 0) return false;
     const int grid = std::min(maxt, cap);
     Pack pk;
-    const size_t ot = pk.add(tasks), opa = pk.add(parts), oph = pk.add(phase_beg), oc = pk.add(cuts),
-                 os = pk.add(secs);
+    const size_t ot = pk.add(tasks), oph = pk.add(phase_beg), oc = pk.add(cuts), os = pk.add(secs);
     Scratch s(ctx);
     unsigned char* d = upload_pack(s, pk);
     const DynTask* a0 = (const DynTask*)(d + ot);
-    const DynPart* a1 = (const DynPart*)(d + opa);
-    const int* a2 = (const int*)(d + oph);
-    const CutTask* a3 = (const CutTask*)(d + oc);
-    const CutSector* a4 = (const CutSector*)(d + os);
-    int a5 = n_phase;
+    const int* a1 = (const int*)(d + oph);
+    const CutTask* a2 = (const CutTask*)(d + oc);
+    const CutSector* a3 = (const CutSector*)(d + os);
+    int a4 = n_phase;
+    int a5 = (int)pb_off;
     GridSync* a6 = gs;
     void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
     Prof pr(ctx, KK_SVD, 0.0, by);   // flops entered by the caller once the ranks are known
