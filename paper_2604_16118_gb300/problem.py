@@ -65,12 +65,26 @@ def theta_diagonal(h, eri, spin, n_particles, gamma):
     return th
 
 
-def spectrum_bounds(theta, spin, n_up, n_dn):
+def spectrum_bounds(theta, spin, n_up, n_dn, h=None):
+    """t_min / t_max of the exponential-sum interval.  With the one-body matrix
+    h given and its diagonal strictly increasing along a species' sites (the
+    paper's orbital basis), the sums of theta over that species' first / last
+    n sites (t_min = D at e_1, as the printed t_min, t_max and T of Sec. 7.2
+    require); otherwise the sums of the n smallest / largest theta (the range
+    of the spectrum of D)."""
     lo = hi = 0.0
-    groups = [(theta[0::2], n_up), (theta[1::2], n_dn)] if spin else [(theta, n_up)]
-    for vals, n in groups:
-        s = np.sort(vals)
-        if n:
-            lo += float(s[:n].sum())
-            hi += float(s[-n:].sum())
+    K = len(theta)
+    diag = None
+    if h is not None:
+        d = np.diag(np.asarray(h, dtype=np.float64))
+        diag = np.repeat(d, 2) if spin else d
+    groups = [(np.arange(0, K, 2), n_up), (np.arange(1, K, 2), n_dn)] if spin else [(np.arange(K), n_up)]
+    for idx, n in groups:
+        if not n:
+            continue
+        vals = np.asarray(theta)[idx]
+        if diag is None or not np.all(np.diff(diag[idx]) > 0):
+            vals = np.sort(vals)
+        lo += float(np.sum(vals[:n]))
+        hi += float(np.sum(vals[-n:]))
     return lo, hi

@@ -10,6 +10,7 @@ from .generators import (  # noqa: F401
     spinless_random_chain,
     hubbard_chain,
     molecule_like,
+    coulomb_1d,
     random_block_values,
     Workload,
 )

@@ -13,6 +13,14 @@ Recipes (sizes as used by the tests and the bench):
   (pp|pp) = U, everything else zero.
 * molecule-like: h_pp = linspace(-2, 2, L); off-diagonal N(0, 0.05) exp(-|p-q|/6)
   (symmetric); (pq|rs) from n_chol Cholesky-like vectors, L^g = 0.1 G^g.
+* one-dimensional Coulomb-like model (the paper's Sec. 7.2 Hamiltonian, with
+  finite-difference orbitals standing in for the paper's multiwavelet ones):
+  N particles of equal spin on [-b, b] with V(x) = -N delta_0(x) and
+  V_2(x, y) = c_V exp(-|x - y|).  The orbitals are the K lowest eigenvectors of
+  -1/2 d^2/dx^2 + V on a uniform grid (n_grid intervals, Dirichlet ends, the
+  delta as -N/h at the node x = 0), so h = diag(omega); (pq|rs) are grid sums
+  h sum_s phi_p phi_q (s) [V_2 (phi_r phi_s)](s), the discrete convolution
+  with exp(-|x - y|) taken by a forward and a backward recursion.
 """
 
 from dataclasses import dataclass, field
@@ -90,6 +98,33 @@ def molecule_like(L=24, n_up=None, n_dn=None, r_max=1024, seed=0, n_chol=None):
     h = off + np.diag(np.linspace(-2.0, 2.0, L))
     eri = _cholesky_eri(rng, L, n_chol, 0.1)
     return Workload("molecule_like", L, 1, n_up, n_dn, h, eri, r_max, seed)
+
+
+def coulomb_1d(K=14, N=4, b=4.0, c_v=4.0, n_grid=16384, r_max=64):
+    import scipy.linalg
+
+    hx = 2.0 * b / n_grid
+    m = n_grid - 1                                    # interior nodes
+    diag = np.full(m, 1.0 / hx ** 2)
+    diag[m // 2] += -N / hx                           # delta potential at x = 0
+    off = np.full(m - 1, -0.5 / hx ** 2)
+    omega, vec = scipy.linalg.eigh_tridiagonal(diag, off, select="i", select_range=(0, K - 1))
+    phi = vec / np.sqrt(hx)                           # L2-normalised on the grid
+    prod = np.einsum("sp,sq->pqs", phi, phi).reshape(K * K, m)
+    a = np.exp(-hx)
+    fwd = np.empty_like(prod)
+    bwd = np.empty_like(prod)
+    fwd[:, 0] = prod[:, 0]
+    for s in range(1, m):
+        fwd[:, s] = prod[:, s] + a * fwd[:, s - 1]
+    bwd[:, m - 1] = prod[:, m - 1]
+    for s in range(m - 2, -1, -1):
+        bwd[:, s] = prod[:, s] + a * bwd[:, s + 1]
+    conv = c_v * hx * (fwd + bwd - prod)              # [V_2 (phi_r phi_s)] on the grid
+    eri = (hx * prod @ conv.T).reshape(K, K, K, K)
+    eri = 0.5 * (eri + eri.transpose(2, 3, 0, 1))     # exact pair symmetry against rounding
+    return Workload("coulomb_1d", K, 0, N, 0, np.diag(omega), eri, r_max, 0,
+                    extra={"b": b, "c_v": c_v, "n_grid": n_grid})
 
 
 def random_block_values(n, seed=0):
