@@ -66,3 +66,23 @@ def test_exact_eigenvalues_k14(k14):
     assert abs(lam[1] - g["lambda2"]) <= tol
     delta = lam[1] / (lam[1] - lam[0])
     assert abs(delta - g["delta"]) <= 2e-3
+
+
+def test_preconditioned_spectrum_and_higher_eigenvalues_k14(k14):
+    # c is the spectral equivalence constant of A = S H_gamma S (eps_iter = c for omega = 1):
+    # its exact value by diagonalisation gives the printed 1 - c, 1 + c, eps_iter and eps_num
+    g = GOLD["K14"]
+    gamma = GOLD["model"]["gamma"]
+    H, states = F.sector_hamiltonian(k14.h, k14.eri, 0, 4, 0, gamma=gamma)
+    th, (tmin, tmax) = interval(k14, gamma)
+    prec = P.Preconditioner(th, tmin, tmax, 0.1, 1.0)
+    occ = np.array([[(int(m) >> s) & 1 for s in range(k14.n_orb)] for m in states])
+    S = prec.dense_diag(occ)
+    mu = np.linalg.eigvalsh(S[:, None] * H * S[None, :])
+    c = (mu[-1] - mu[0]) / (mu[-1] + mu[0])
+    assert abs((1 - c) - g["one_minus_c"]) <= half_unit(g["one_minus_c"])
+    assert abs((1 + c) - g["one_plus_c"]) <= half_unit(g["one_plus_c"])
+    assert abs(c - g["eps_iter"]) <= half_unit(g["eps_iter"])
+    assert abs(0.5 * (1 - c) - g["eps_num"]) <= half_unit(g["eps_num"])
+    lam = np.linalg.eigvalsh(H)[:4]
+    assert np.all(np.abs(lam - np.array(g["lambda_1to4"])) <= GOLD["tolerances"]["discretisation"])
