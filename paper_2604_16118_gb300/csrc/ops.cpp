@@ -1278,20 +1278,43 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
     std::vector<double> result(P, 0.0);
     if (P == 0) return result;
     const int K = probs[0].a->lay.K;
-    std::vector<Mpo> ids;
-    ids.reserve(P);
-    std::vector<const Mpo*> ops(P);
     for (int p = 0; p < P; ++p) {
         const EnvProblem& pr = probs[p];
         BSM_REQUIRE(same_space(pr.a->lay, pr.b->lay) && pr.a->lay.K == K, BSMPS_ERR_INVALID_ARG,
                     "dot of MPS of different spaces");
-        if (pr.W) {
+        if (pr.W)
             BSM_REQUIRE(pr.W->K == K && pr.W->species == pr.a->lay.species, BSMPS_ERR_INVALID_ARG,
                         "MPO and MPS act on different sites");
-            ops[p] = pr.W;
+    }
+    // Problems with the same a, b, operator and shift share every block structure
+    // and differ only in the per-site scale factors: the structure is planned once
+    // per group and replicated for each member with its own factors and buffers.
+    std::vector<int> group_of(P, -1), rep;
+    std::vector<std::vector<int>> members;
+    for (int p = 0; p < P; ++p) {
+        for (int g = 0; g < (int)rep.size() && group_of[p] < 0; ++g) {
+            const EnvProblem& q = probs[rep[g]];
+            if (q.a == probs[p].a && q.b == probs[p].b && q.W == probs[p].W &&
+                (q.W == nullptr || q.shift == probs[p].shift))
+                group_of[p] = g;
+        }
+        if (group_of[p] < 0) {
+            group_of[p] = (int)rep.size();
+            rep.push_back(p);
+            members.emplace_back();
+        }
+        members[group_of[p]].push_back(p);
+    }
+    const int G = (int)rep.size();
+    std::vector<Mpo> ids;
+    ids.reserve(G);
+    std::vector<const Mpo*> ops(G);
+    for (int g = 0; g < G; ++g) {
+        if (probs[rep[g]].W) {
+            ops[g] = probs[rep[g]].W;
         } else {
-            ids.push_back(identity_mpo(pr.a->lay));
-            ops[p] = &ids.back();
+            ids.push_back(identity_mpo(probs[rep[g]].a->lay));
+            ops[g] = &ids.back();
         }
     }
     // buffer references: id 0 = T, 1 / 2 = E ping-pong, 3 = the 1x1 block [1], -1 = a real pointer
@@ -1302,7 +1325,7 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
     };
     struct EBlk {
         int c, ia, ib, rows, cols;
-        int64_t off;
+        int64_t off;   // within a member's share of the E buffer
     };
     std::vector<GemmOut> outs;
     std::vector<GemmIn> ins;
@@ -1310,11 +1333,14 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
     std::vector<EnvTile> tiles;
     std::vector<int> phase_beg{0};
     int64_t maxT = 1, maxE = 1;
-    std::vector<std::vector<EBlk>> E(P);
-    for (int p = 0; p < P; ++p) {
-        const Layout& A = probs[p].a->lay;
-        const Layout& B = probs[p].b->lay;
-        if (!A.bonds[0].q.empty() && !B.bonds[0].q.empty()) E[p].push_back({0, 0, 0, 1, 1, 0});
+    std::vector<std::vector<EBlk>> E(G);              // per group: blocks of E at the current bond
+    std::vector<int64_t> E_size(G, 0);                // per group: entries per member
+    std::vector<int64_t> e_base(P, 0), e_next(P, 0);  // per problem: its share of the E buffer
+    for (int g = 0; g < G; ++g) {
+        const Layout& A = probs[rep[g]].a->lay;
+        const Layout& B = probs[rep[g]].b->lay;
+        if (!A.bonds[0].q.empty() && !B.bonds[0].q.empty()) E[g].push_back({0, 0, 0, 1, 1, 0});
+        E_size[g] = 1;
     }
     auto add_tiles = [&](int o) {
         for (int m0 = 0; m0 < outs[o].M; m0 += 32)
@@ -1322,107 +1348,139 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
     };
     struct Contrib {
         uint64_t key;
-        int seq, ti, ab;
-        double alpha;
+        int seq, ti, ab, ei;
+        int so, si;
+    };
+    struct TBlk {
+        int env, sigma, rows, cols, bb;
+        int64_t off;   // within a member's share of the T buffer
     };
     for (int t = 0; t < K; ++t) {
         const int eid = t == 0 ? 3 : 1 + (t % 2);   // buffer of E at bond t
         const int nid = 1 + ((t + 1) % 2);          // buffer of E at bond t + 1
-        struct TBlk {
-            int env, sigma, rows, cols;
-            int64_t off;
-        };
-        std::vector<std::vector<TBlk>> T(P);
-        std::vector<std::vector<Contrib>> contrib(P);
-        int64_t tot_T = 0;
-        // ---- stage 1: T = E X_b ----
-        for (int p = 0; p < P; ++p) {
-            const Layout& A = probs[p].a->lay;
-            const Layout& B = probs[p].b->lay;
+        std::vector<std::vector<TBlk>> T(G);
+        std::vector<int64_t> T_size(G, 0);
+        std::vector<std::vector<Contrib>> contrib(G);
+        // ---- structure of the site, once per group ----
+        for (int g = 0; g < G; ++g) {
+            const Layout& A = probs[rep[g]].a->lay;
+            const Layout& B = probs[rep[g]].b->lay;
             const std::vector<int> blook = block_lookup(B, t);
             const std::vector<int> alook = block_lookup(A, t);
-            std::vector<std::array<int, 2>> tidx(E[p].size(), {-1, -1});
-            for (int e = 0; e < (int)E[p].size(); ++e)
+            std::vector<std::array<int, 2>> tidx(E[g].size(), {-1, -1});
+            for (int e = 0; e < (int)E[g].size(); ++e)
                 for (int si = 0; si < 2; ++si) {
-                    const int bb = blook[E[p][e].ib * 2 + si];
+                    const int bb = blook[E[g][e].ib * 2 + si];
                     if (bb < 0) continue;
-                    tidx[e][si] = (int)T[p].size();
+                    tidx[e][si] = (int)T[g].size();
                     const Block& bk = B.blocks[t][bb];
-                    T[p].push_back({e, si, E[p][e].rows, bk.cols, tot_T});
-                    const int o = (int)outs.size();
-                    outs.push_back({nullptr, E[p][e].rows, bk.cols, bk.cols, (int)ins.size(), (int)ins.size() + 1, 0.0});
-                    out_ref.push_back({0, tot_T, nullptr});
-                    ins.push_back({nullptr, nullptr, E[p][e].cols, E[p][e].cols, bk.cols, 0, 1.0});
-                    ina_ref.push_back({eid, E[p][e].off, nullptr});
-                    inb_ref.push_back({-1, 0, probs[p].b->core[t] + bk.off});
-                    add_tiles(o);
-                    tot_T += (int64_t)E[p][e].rows * bk.cols;
+                    T[g].push_back({e, si, E[g][e].rows, bk.cols, bb, T_size[g]});
+                    T_size[g] += (int64_t)E[g][e].rows * bk.cols;
                 }
-            // env blocks by channel
-            const Mpo& W = *ops[p];
+            const Mpo& W = *ops[g];
             const int nch = W.bond_dim(t);
             std::vector<std::vector<int>> by_chan(nch);
-            for (int e = 0; e < (int)E[p].size(); ++e) by_chan[E[p][e].c].push_back(e);
+            for (int e = 0; e < (int)E[g].size(); ++e) by_chan[E[g][e].c].push_back(e);
             int seq = 0;
             for (int ei = 0; ei < (int)W.entries[t].size(); ++ei) {
                 const MpoEntry& me = W.entries[t][ei];
                 if (me.a >= nch || by_chan[me.a].empty()) continue;
-                double w = me.w;
-                if (probs[p].W && t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1]))
-                    w += probs[p].shift;
-                double fa = 1.0, fb = 1.0;
-                if (me.so == 0 ? probs[p].fa0 : probs[p].fa1) fa = (*(me.so == 0 ? probs[p].fa0 : probs[p].fa1))[t];
-                if (me.si == 0 ? probs[p].fb0 : probs[p].fb1) fb = (*(me.si == 0 ? probs[p].fb0 : probs[p].fb1))[t];
-                const double alpha = w * fa * fb;
                 for (int e : by_chan[me.a]) {
-                    const int ab = alook[E[p][e].ia * 2 + me.so];
+                    const int ab = alook[E[g][e].ia * 2 + me.so];
                     const int ti = tidx[e][me.si];
                     if (ab < 0 || ti < 0) continue;
-                    const int bb = blook[E[p][e].ib * 2 + me.si];
+                    const int bb = blook[E[g][e].ib * 2 + me.si];
                     const uint64_t ra = (uint64_t)A.blocks[t][ab].ri, rb = (uint64_t)B.blocks[t][bb].ri;
                     const uint64_t key = ((uint64_t)me.b << 42) | (ra << 21) | rb;
-                    contrib[p].push_back({key, seq++, ti, ab, alpha});
+                    contrib[g].push_back({key, seq++, ti, ab, ei, me.so, me.si});
                 }
             }
-        }
-        maxT = std::max(maxT, tot_T);
-        phase_beg.push_back((int)tiles.size());
-        // ---- stage 2: E'(d, ra, rb) = sum alpha X_a^T T ----
-        int64_t tot_E = 0;
-        std::vector<std::vector<EBlk>> En(P);
-        for (int p = 0; p < P; ++p) {
-            const Layout& A = probs[p].a->lay;
-            const Layout& B = probs[p].b->lay;
-            std::vector<Contrib>& cs = contrib[p];
-            std::sort(cs.begin(), cs.end(), [](const Contrib& x, const Contrib& y) {
+            std::sort(contrib[g].begin(), contrib[g].end(), [](const Contrib& x, const Contrib& y) {
                 return x.key != y.key ? x.key < y.key : x.seq < y.seq;
             });
+        }
+        // ---- stage 1: T = E X_b, every member ----
+        int64_t tot_T = 0;
+        std::vector<int64_t> t_base(P, 0);
+        for (int g = 0; g < G; ++g)
+            for (int p : members[g]) {
+                t_base[p] = tot_T;
+                tot_T += T_size[g];
+                const Layout& B = probs[p].b->lay;
+                for (const TBlk& tb : T[g]) {
+                    const EBlk& eb = E[g][tb.env];
+                    const Block& bk = B.blocks[t][tb.bb];
+                    const int o = (int)outs.size();
+                    outs.push_back({nullptr, tb.rows, tb.cols, tb.cols, (int)ins.size(), (int)ins.size() + 1, 0.0});
+                    out_ref.push_back({0, t_base[p] + tb.off, nullptr});
+                    ins.push_back({nullptr, nullptr, eb.cols, eb.cols, bk.cols, 0, 1.0});
+                    ina_ref.push_back({eid, e_base[p] + eb.off, nullptr});
+                    inb_ref.push_back({-1, 0, probs[p].b->core[t] + bk.off});
+                    add_tiles(o);
+                }
+            }
+        maxT = std::max(maxT, tot_T);
+        phase_beg.push_back((int)tiles.size());
+        // ---- stage 2: E'(d, ra, rb) = sum alpha X_a^T T, every member ----
+        std::vector<std::vector<EBlk>> En(G);
+        std::vector<int64_t> En_size(G, 0);
+        for (int g = 0; g < G; ++g) {
+            const Layout& A = probs[rep[g]].a->lay;
+            const Layout& B = probs[rep[g]].b->lay;
+            const std::vector<Contrib>& cs = contrib[g];
             for (size_t i = 0; i < cs.size();) {
                 size_t j = i;
                 while (j < cs.size() && cs[j].key == cs[i].key) ++j;
                 const int d = (int)(cs[i].key >> 42), ra = (int)((cs[i].key >> 21) & 0x1fffff),
                           rb = (int)(cs[i].key & 0x1fffff);
                 const int rows = A.bonds[t + 1].dim[ra], cols = B.bonds[t + 1].dim[rb];
-                En[p].push_back({d, ra, rb, rows, cols, tot_E});
-                const int o = (int)outs.size();
-                outs.push_back({nullptr, rows, cols, cols, (int)ins.size(), 0, 0.0});
-                out_ref.push_back({nid, tot_E, nullptr});
-                for (size_t u = i; u < j; ++u) {
-                    const TBlk& tb = T[p][cs[u].ti];
-                    const Block& abk = A.blocks[t][cs[u].ab];
-                    ins.push_back({nullptr, nullptr, abk.rows, abk.cols, tb.cols, 1, cs[u].alpha});
-                    ina_ref.push_back({-1, 0, probs[p].a->core[t] + abk.off});
-                    inb_ref.push_back({0, tb.off, nullptr});
-                }
-                outs[o].end = (int)ins.size();
-                add_tiles(o);
-                tot_E += (int64_t)rows * cols;
+                En[g].push_back({d, ra, rb, rows, cols, En_size[g]});
+                En_size[g] += (int64_t)rows * cols;
                 i = j;
+            }
+        }
+        int64_t tot_E = 0;
+        for (int g = 0; g < G; ++g) {
+            const Mpo& W = *ops[g];
+            const std::vector<Contrib>& cs = contrib[g];
+            for (int p : members[g]) {
+                e_next[p] = tot_E;
+                tot_E += En_size[g];
+                const EnvProblem& pr = probs[p];
+                size_t q = 0;
+                for (size_t i = 0; i < cs.size(); ++q) {
+                    size_t j = i;
+                    while (j < cs.size() && cs[j].key == cs[i].key) ++j;
+                    const EBlk& nb = En[g][q];
+                    const int o = (int)outs.size();
+                    outs.push_back({nullptr, nb.rows, nb.cols, nb.cols, (int)ins.size(), 0, 0.0});
+                    out_ref.push_back({nid, e_next[p] + nb.off, nullptr});
+                    for (size_t u = i; u < j; ++u) {
+                        const Contrib& c = cs[u];
+                        const MpoEntry& me = W.entries[t][c.ei];
+                        double w = me.w;
+                        if (pr.W && t == 0 && (c.ei == W.shift_entry[0] || c.ei == W.shift_entry[1])) w += pr.shift;
+                        double fa = 1.0, fb = 1.0;
+                        const std::vector<double>* va = c.so == 0 ? pr.fa0 : pr.fa1;
+                        const std::vector<double>* vb = c.si == 0 ? pr.fb0 : pr.fb1;
+                        if (va) fa = (*va)[t];
+                        if (vb) fb = (*vb)[t];
+                        const TBlk& tb = T[g][c.ti];
+                        const Block& abk = pr.a->lay.blocks[t][c.ab];
+                        ins.push_back({nullptr, nullptr, abk.rows, abk.cols, tb.cols, 1, w * fa * fb});
+                        ina_ref.push_back({-1, 0, pr.a->core[t] + abk.off});
+                        inb_ref.push_back({0, t_base[p] + tb.off, nullptr});
+                    }
+                    outs[o].end = (int)ins.size();
+                    add_tiles(o);
+                    i = j;
+                }
             }
         }
         maxE = std::max(maxE, tot_E);
         phase_beg.push_back((int)tiles.size());
         E.swap(En);
+        e_base.swap(e_next);
     }
     // buffers, then the references resolved
     Scratch s(ctx);
@@ -1449,7 +1507,7 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
     std::vector<const double*> finals;
     std::vector<int> final_beg{0};
     for (int p = 0; p < P; ++p) {
-        for (const EBlk& eb : E[p]) finals.push_back(base[fid] + eb.off);
+        for (const EBlk& eb : E[group_of[p]]) finals.push_back(base[fid] + e_base[p] + eb.off);
         final_beg.push_back((int)finals.size());
     }
     if (!launch_env_sweep(ctx, outs, ins, tiles, phase_beg, finals, final_beg, res, gs))
