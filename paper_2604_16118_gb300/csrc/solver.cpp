@@ -37,24 +37,30 @@ PrecondTerms make_precond(const bsmps_precond* p) {
 }
 
 // sum_{k,k'} <O S_k a, S_k' b> for several (a, b, O) at once (Eq. (exactrq)).
+// sum_{k,k'} <S_k a, O S_k' b> per job (Eq. (exactrq)).  O is symmetric, so
+// for a == b the (k, k') and (k', k) terms are equal: only k <= k' is
+// computed and the off-diagonal terms count twice.
 std::vector<double> pair_sums(Context* ctx, const PrecondTerms& P,
                               const std::vector<std::tuple<const Mps*, const Mps*, const Mpo*>>& jobs) {
     const int nt = P.n_terms();
     std::vector<EnvProblem> probs;
-    for (auto& j : jobs)
+    std::vector<std::pair<int, double>> weight;   // (job, multiplicity) per problem
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const bool same = std::get<0>(jobs[j]) == std::get<1>(jobs[j]);
         for (int k = 0; k < nt; ++k)
-            for (int kp = 0; kp < nt; ++kp) {
-                EnvProblem pr{std::get<0>(j), std::get<1>(j), std::get<2>(j), 0.0};
+            for (int kp = same ? k : 0; kp < nt; ++kp) {
+                EnvProblem pr{std::get<0>(jobs[j]), std::get<1>(jobs[j]), std::get<2>(jobs[j]), 0.0};
                 pr.fa0 = &P.f0[k];
                 pr.fa1 = &P.f1[k];
                 pr.fb0 = &P.f0[kp];
                 pr.fb1 = &P.f1[kp];
                 probs.push_back(pr);
+                weight.push_back({(int)j, same && kp != k ? 2.0 : 1.0});
             }
+    }
     const std::vector<double> v = op_dot_batch(ctx, probs);
     std::vector<double> out(jobs.size(), 0.0);
-    for (size_t j = 0; j < jobs.size(); ++j)
-        for (int q = 0; q < nt * nt; ++q) out[j] += v[j * nt * nt + q];
+    for (size_t q = 0; q < v.size(); ++q) out[weight[q].first] += weight[q].second * v[q];
     return out;
 }
 
@@ -249,12 +255,12 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
         return x;
     }
     // 2x2 Rayleigh-Ritz in the normalised basis (Remark omegamin)
-    const auto g = pair_sums(ctx, P, {{x.get(), x.get(), &W}, {x.get(), r.get(), &W}, {r.get(), x.get(), &W},
-                                      {r.get(), r.get(), &W}, {x.get(), x.get(), nullptr},
-                                      {x.get(), r.get(), nullptr}, {r.get(), x.get(), nullptr},
+    // the Gram matrices are symmetric (H_gamma and the S_k are): <x, r> entries once
+    const auto g = pair_sums(ctx, P, {{x.get(), x.get(), &W}, {x.get(), r.get(), &W}, {r.get(), r.get(), &W},
+                                      {x.get(), x.get(), nullptr}, {x.get(), r.get(), nullptr},
                                       {r.get(), r.get(), nullptr}});
-    const double GH[2][2] = {{g[0], g[1]}, {g[2], g[3]}};
-    const double GE[2][2] = {{g[4], g[5]}, {g[6], g[7]}};
+    const double GH[2][2] = {{g[0], g[1]}, {g[1], g[2]}};
+    const double GE[2][2] = {{g[3], g[4]}, {g[4], g[5]}};
     const double nrm[2] = {std::sqrt(GE[0][0]), std::sqrt(GE[1][1])};
     double Hn[2][2], En[2][2];
     for (int i = 0; i < 2; ++i)
