@@ -292,6 +292,34 @@ void Context::prof_end(int kind, double fl, double by, cudaEvent_t e0) {
     prof.push_back({kind, fl, by, e0, e1});
 }
 
+struct ZeroChunk {
+    double* p;
+    int64_t n;
+};
+
+__global__ void __launch_bounds__(kThreads) k_zero(const ZeroChunk* __restrict__ chunks) {
+    const ZeroChunk c = chunks[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < c.n; e += kThreads) c.p[e] = 0.0;
+}
+
+void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n) {
+    std::vector<ZeroChunk> chunks;
+    for (size_t i = 0; i < ptr.size(); ++i)
+        for (int64_t b = 0; b < n[i]; b += kCopyChunk) chunks.push_back({ptr[i] + b, std::min(n[i] - b, kCopyChunk)});
+    if (chunks.empty()) return;
+    configure_carveout();
+    Scratch s(ctx);
+    const ZeroChunk* d = s.up(chunks);
+    ProfScope ps(ctx, KK_COPY, 0.0, 8.0 * [&] {
+        double t = 0.0;
+        for (int64_t v : n) t += (double)v;
+        return t;
+    }());
+    k_zero<<<(unsigned)chunks.size(), kThreads, 0, ctx->stream>>>(d);
+    check_launch(ctx);
+    ps.done();
+}
+
 void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
     if (tasks.empty()) return;
     configure_carveout();

@@ -65,6 +65,8 @@ struct SvdTask {
 };
 
 void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks);
+// Sets n[i] doubles at ptr[i] to zero, all regions in one launch.
+void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n);
 void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins);
 void launch_qr(Context* ctx, const std::vector<QrTask>& tasks);
 void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks);

@@ -22,13 +22,17 @@ Mps* new_mps(Context* ctx, const Layout& L, bool zero) {
     x->ctx = ctx;
     x->lay = L;
     x->core.assign(L.K, nullptr);
+    std::vector<double*> zp;
+    std::vector<int64_t> zn;
     for (int t = 0; t < L.K; ++t) {
         const int64_t n = L.core_size[t];
         if (n > 0) {
             x->core[t] = (double*)ctx->alloc((size_t)n * sizeof(double));
-            if (zero) BSM_CUDA(cudaMemsetAsync(x->core[t], 0, (size_t)n * sizeof(double), ctx->stream));
+            zp.push_back(x->core[t]);
+            zn.push_back(n);
         }
     }
+    if (zero) launch_zero(ctx, zp, zn);   // every core in one launch
     return x.release();
 }
 
@@ -122,10 +126,12 @@ MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms) {
     R.rebuild_blocks();
     MpsPtr y = make_mps(ctx, R, true);
     std::vector<std::vector<CopyTask>> per_term(terms.size());
+    std::vector<std::vector<int>> looks(K);
+    for (int t = 0; t < K; ++t) looks[t] = block_lookup(R, t);
     for (size_t i = 0; i < terms.size(); ++i) {
         const Mps* x = terms[i].x;
         for (int t = 0; t < K; ++t) {
-            const std::vector<int> look = block_lookup(R, t);
+            const std::vector<int>& look = looks[t];
             for (const Block& bk : x->lay.blocks[t]) {
                 const int li = R.bonds[t].find(x->lay.bonds[t].q[bk.li]);
                 const int ri = R.bonds[t + 1].find(x->lay.bonds[t + 1].q[bk.ri]);
