@@ -213,21 +213,50 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks, const s
 
 // ---- environment sweep of a batch of inner products (one cooperative launch) ----
 
-// Output tile of at most 32 x 32 entries of outs[out] starting at (m0, n0).
-struct EnvTile {
-    int out, m0, n0;
-};
-// Phase p computes tiles[phase_beg[p] .. phase_beg[p+1]) (outputs overwritten,
-// beta ignored); after the last phase, res[q] = sum of *finals[i] for i in
-// [final_beg[q], final_beg[q+1]).  Returns false (nothing launched) when the
-// grid cannot be co-resident.
-bool launch_env_sweep(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins,
-                      const std::vector<EnvTile>& tiles, const std::vector<int>& phase_beg,
-                      const std::vector<const double*>& finals, const std::vector<int>& final_beg, double* res,
-                      GridSync* gs);
-
 // Two-CTA cooperative kernel meeting at one phase boundary; CTA skip_cta (if
 // >= 0) never arrives.  Returns the error word of the wait (1: a wait gave up).
 int check_grid_wait(Context* ctx, int skip_cta);
+
+// ---- environment sweep with structures shared by groups of problems ----
+//
+// Problems with the same MPS pair and operator share every block structure;
+// an output or input refers to a buffer (0: T, 1 / 2: E ping-pong, 3: the 1x1
+// block [1]) by a relative offset, and member m of the output's group finds its
+// copy at base[buf] + gp.base[buf] + m gp.stride[buf] + offset.
+struct EnvGroupPhase {
+    int64_t base[4], stride[4];
+    int mem_beg, n_mem;   // members: member_fac[mem_beg .. mem_beg + n_mem)
+    double shift;         // added to the weight of inputs with shift_flag
+};
+struct EnvOutT {
+    int M, N, ldc, beg, end;
+    int gp;    // its group-phase entry
+    int cbuf;
+    int64_t coff;
+};
+struct EnvInT {
+    const double* A;   // real pointer when abuf < 0
+    const double* B;   // real pointer when bbuf < 0
+    int64_t aoff, boff;
+    int abuf, bbuf;
+    int K, lda, ldb, transA;
+    double w;
+    int shift_flag;
+    int so, si;        // factor rows: fa[so], fb[si] of the member (so < 0: no factors)
+    int site;
+};
+struct EnvTileT {
+    int out, m0, n0, member;
+};
+// rows of the factor table (K doubles each) per member: fa0, fa1, fb0, fb1 (-1: 1.0)
+struct EnvMemberFac {
+    int row[4];
+};
+bool launch_env_sweep_t(Context* ctx, const std::vector<EnvOutT>& outs, const std::vector<EnvInT>& ins,
+                        const std::vector<EnvTileT>& tiles, const std::vector<int>& phase_beg,
+                        const std::vector<EnvGroupPhase>& gph, const std::vector<EnvMemberFac>& mfac,
+                        const std::vector<double>& ftab, int K, double* const base[4],
+                        const std::vector<const double*>& finals, const std::vector<int>& final_beg, double* res,
+                        GridSync* gs);
 
 }  // namespace bsm

@@ -1323,34 +1323,54 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
             ops[g] = &ids.back();
         }
     }
-    // buffer references: id 0 = T, 1 / 2 = E ping-pong, 3 = the 1x1 block [1], -1 = a real pointer
-    struct Ref {
-        int id;
-        int64_t off;
-        const double* ptr;
+    // factor table: the distinct per-site scale vectors of all problems
+    std::vector<const std::vector<double>*> fvec;
+    std::vector<double> ftab;
+    auto frow = [&](const std::vector<double>* v) -> int {
+        if (!v) return -1;
+        for (size_t r = 0; r < fvec.size(); ++r)
+            if (fvec[r] == v) return (int)r;
+        BSM_REQUIRE((int)v->size() >= K, BSMPS_ERR_INVALID_ARG, "scale factors shorter than the chain");
+        fvec.push_back(v);
+        ftab.insert(ftab.end(), v->begin(), v->begin() + K);
+        return (int)fvec.size() - 1;
     };
+    std::vector<EnvMemberFac> mfac;
+    std::vector<int> mem_beg(G);
+    for (int g = 0; g < G; ++g) {
+        mem_beg[g] = (int)mfac.size();
+        for (int p : members[g])
+            mfac.push_back({{frow(probs[p].fa0), frow(probs[p].fa1), frow(probs[p].fb0), frow(probs[p].fb1)}});
+    }
     struct EBlk {
         int c, ia, ib, rows, cols;
         int64_t off;   // within a member's share of the E buffer
     };
-    std::vector<GemmOut> outs;
-    std::vector<GemmIn> ins;
-    std::vector<Ref> out_ref, ina_ref, inb_ref;
-    std::vector<EnvTile> tiles;
+    std::vector<EnvOutT> outs;
+    std::vector<EnvInT> ins;
+    std::vector<EnvTileT> tiles;
+    std::vector<EnvGroupPhase> gph;
     std::vector<int> phase_beg{0};
     int64_t maxT = 1, maxE = 1;
     std::vector<std::vector<EBlk>> E(G);              // per group: blocks of E at the current bond
-    std::vector<int64_t> E_size(G, 0);                // per group: entries per member
-    std::vector<int64_t> e_base(P, 0), e_next(P, 0);  // per problem: its share of the E buffer
+    std::vector<int64_t> E_size(G, 0), E_base(G, 0);  // per group: entries per member, start of its region
     for (int g = 0; g < G; ++g) {
         const Layout& A = probs[rep[g]].a->lay;
         const Layout& B = probs[rep[g]].b->lay;
         if (!A.bonds[0].q.empty() && !B.bonds[0].q.empty()) E[g].push_back({0, 0, 0, 1, 1, 0});
-        E_size[g] = 1;
     }
-    auto add_tiles = [&](int o) {
-        for (int m0 = 0; m0 < outs[o].M; m0 += 32)
-            for (int n0 = 0; n0 < outs[o].N; n0 += 32) tiles.push_back({o, m0, n0});
+    auto add_tiles = [&](int o, int n_mem) {
+        for (int m = 0; m < n_mem; ++m)
+            for (int m0 = 0; m0 < outs[o].M; m0 += 32)
+                for (int n0 = 0; n0 < outs[o].N; n0 += 32) tiles.push_back({o, m0, n0, m});
+    };
+    auto group_phase = [&](int g) {
+        EnvGroupPhase e{};
+        e.mem_beg = mem_beg[g];
+        e.n_mem = (int)members[g].size();
+        e.shift = probs[rep[g]].W ? probs[rep[g]].shift : 0.0;
+        gph.push_back(e);
+        return (int)gph.size() - 1;
     };
     struct Contrib {
         uint64_t key;
@@ -1405,35 +1425,44 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
                 return x.key != y.key ? x.key < y.key : x.seq < y.seq;
             });
         }
-        // ---- stage 1: T = E X_b, every member ----
+        // ---- stage 1: T = E X_b (templates once per group) ----
         int64_t tot_T = 0;
-        std::vector<int64_t> t_base(P, 0);
-        for (int g = 0; g < G; ++g)
-            for (int p : members[g]) {
-                t_base[p] = tot_T;
-                tot_T += T_size[g];
-                const Layout& B = probs[p].b->lay;
-                for (const TBlk& tb : T[g]) {
-                    const EBlk& eb = E[g][tb.env];
-                    const Block& bk = B.blocks[t][tb.bb];
-                    const int o = (int)outs.size();
-                    outs.push_back({nullptr, tb.rows, tb.cols, tb.cols, (int)ins.size(), (int)ins.size() + 1, 0.0});
-                    out_ref.push_back({0, t_base[p] + tb.off, nullptr});
-                    ins.push_back({nullptr, nullptr, eb.cols, eb.cols, bk.cols, 0, 1.0});
-                    ina_ref.push_back({eid, e_base[p] + eb.off, nullptr});
-                    inb_ref.push_back({-1, 0, probs[p].b->core[t] + bk.off});
-                    add_tiles(o);
-                }
+        std::vector<int64_t> T_base(G, 0);
+        for (int g = 0; g < G; ++g) {
+            T_base[g] = tot_T;
+            tot_T += (int64_t)members[g].size() * T_size[g];
+            const int gp = group_phase(g);
+            gph[gp].base[0] = T_base[g];
+            gph[gp].stride[0] = T_size[g];
+            if (eid != 3) {
+                gph[gp].base[eid] = E_base[g];
+                gph[gp].stride[eid] = E_size[g];
             }
+            const Mps* b = probs[rep[g]].b;
+            for (const TBlk& tb : T[g]) {
+                const EBlk& eb = E[g][tb.env];
+                const Block& bk = b->lay.blocks[t][tb.bb];
+                const int o = (int)outs.size();
+                outs.push_back({tb.rows, tb.cols, tb.cols, (int)ins.size(), (int)ins.size() + 1, gp, 0, tb.off});
+                ins.push_back({nullptr, b->core[t] + bk.off, eb.off, 0, eid, -1, eb.cols, eb.cols, bk.cols, 0, 1.0,
+                               0, -1, -1, t});
+                add_tiles(o, (int)members[g].size());
+            }
+        }
         maxT = std::max(maxT, tot_T);
         phase_beg.push_back((int)tiles.size());
-        // ---- stage 2: E'(d, ra, rb) = sum alpha X_a^T T, every member ----
+        // ---- stage 2: E'(d, ra, rb) = sum alpha X_a^T T ----
         std::vector<std::vector<EBlk>> En(G);
-        std::vector<int64_t> En_size(G, 0);
+        std::vector<int64_t> En_size(G, 0), En_base(G, 0);
+        int64_t tot_E = 0;
         for (int g = 0; g < G; ++g) {
-            const Layout& A = probs[rep[g]].a->lay;
+            const Mps* a_ = probs[rep[g]].a;
+            const Layout& A = a_->lay;
             const Layout& B = probs[rep[g]].b->lay;
+            const Mpo& W = *ops[g];
+            const bool real_op = probs[rep[g]].W != nullptr;
             const std::vector<Contrib>& cs = contrib[g];
+            // blocks of E' first (their sizes fix the member stride)
             for (size_t i = 0; i < cs.size();) {
                 size_t j = i;
                 while (j < cs.size() && cs[j].key == cs[i].key) ++j;
@@ -1444,51 +1473,41 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
                 En_size[g] += (int64_t)rows * cols;
                 i = j;
             }
-        }
-        int64_t tot_E = 0;
-        for (int g = 0; g < G; ++g) {
-            const Mpo& W = *ops[g];
-            const std::vector<Contrib>& cs = contrib[g];
-            for (int p : members[g]) {
-                e_next[p] = tot_E;
-                tot_E += En_size[g];
-                const EnvProblem& pr = probs[p];
-                size_t q = 0;
-                for (size_t i = 0; i < cs.size(); ++q) {
-                    size_t j = i;
-                    while (j < cs.size() && cs[j].key == cs[i].key) ++j;
-                    const EBlk& nb = En[g][q];
-                    const int o = (int)outs.size();
-                    outs.push_back({nullptr, nb.rows, nb.cols, nb.cols, (int)ins.size(), 0, 0.0});
-                    out_ref.push_back({nid, e_next[p] + nb.off, nullptr});
-                    for (size_t u = i; u < j; ++u) {
-                        const Contrib& c = cs[u];
-                        const MpoEntry& me = W.entries[t][c.ei];
-                        double w = me.w;
-                        if (pr.W && t == 0 && (c.ei == W.shift_entry[0] || c.ei == W.shift_entry[1])) w += pr.shift;
-                        double fa = 1.0, fb = 1.0;
-                        const std::vector<double>* va = c.so == 0 ? pr.fa0 : pr.fa1;
-                        const std::vector<double>* vb = c.si == 0 ? pr.fb0 : pr.fb1;
-                        if (va) fa = (*va)[t];
-                        if (vb) fb = (*vb)[t];
-                        const TBlk& tb = T[g][c.ti];
-                        const Block& abk = pr.a->lay.blocks[t][c.ab];
-                        ins.push_back({nullptr, nullptr, abk.rows, abk.cols, tb.cols, 1, w * fa * fb});
-                        ina_ref.push_back({-1, 0, pr.a->core[t] + abk.off});
-                        inb_ref.push_back({0, t_base[p] + tb.off, nullptr});
-                    }
-                    outs[o].end = (int)ins.size();
-                    add_tiles(o);
-                    i = j;
+            En_base[g] = tot_E;
+            tot_E += (int64_t)members[g].size() * En_size[g];
+            const int gp = group_phase(g);
+            gph[gp].base[0] = T_base[g];
+            gph[gp].stride[0] = T_size[g];
+            gph[gp].base[nid] = En_base[g];
+            gph[gp].stride[nid] = En_size[g];
+            size_t q = 0;
+            for (size_t i = 0; i < cs.size(); ++q) {
+                size_t j = i;
+                while (j < cs.size() && cs[j].key == cs[i].key) ++j;
+                const EBlk& nb = En[g][q];
+                const int o = (int)outs.size();
+                outs.push_back({nb.rows, nb.cols, nb.cols, (int)ins.size(), 0, gp, nid, nb.off});
+                for (size_t u = i; u < j; ++u) {
+                    const Contrib& c = cs[u];
+                    const MpoEntry& me = W.entries[t][c.ei];
+                    const int sf = real_op && t == 0 && (c.ei == W.shift_entry[0] || c.ei == W.shift_entry[1]);
+                    const TBlk& tb = T[g][c.ti];
+                    const Block& abk = A.blocks[t][c.ab];
+                    ins.push_back({a_->core[t] + abk.off, nullptr, 0, tb.off, -1, 0, abk.rows, abk.cols, tb.cols, 1,
+                                   me.w, sf, c.so, c.si, t});
                 }
+                outs[o].end = (int)ins.size();
+                add_tiles(o, (int)members[g].size());
+                i = j;
             }
         }
         maxE = std::max(maxE, tot_E);
         phase_beg.push_back((int)tiles.size());
         E.swap(En);
-        e_base.swap(e_next);
+        E_size.swap(En_size);
+        E_base.swap(En_base);
     }
-    // buffers, then the references resolved
+    // buffers
     Scratch s(ctx);
     double* base[4];
     base[0] = s.dbl((size_t)maxT);
@@ -1502,21 +1521,21 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
     GridSync* gs = (GridSync*)ctx->alloc(sizeof(GridSync));
     s.ptrs.push_back(gs);
     BSM_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), ctx->stream));
-    auto resolve = [&](const Ref& r) -> const double* { return r.id < 0 ? r.ptr : base[r.id] + r.off; };
-    for (size_t o = 0; o < outs.size(); ++o) outs[o].C = (double*)resolve(out_ref[o]);
-    for (size_t i = 0; i < ins.size(); ++i) {
-        ins[i].A = resolve(ina_ref[i]);
-        ins[i].B = resolve(inb_ref[i]);
-    }
     // bond K: the remaining 1x1 blocks of every problem
     const int fid = 1 + (K % 2);
     std::vector<const double*> finals;
     std::vector<int> final_beg{0};
+    std::vector<int> member_index(P, 0);
+    for (int g = 0; g < G; ++g)
+        for (size_t m = 0; m < members[g].size(); ++m) member_index[members[g][m]] = (int)m;
     for (int p = 0; p < P; ++p) {
-        for (const EBlk& eb : E[group_of[p]]) finals.push_back(base[fid] + e_base[p] + eb.off);
+        const int g = group_of[p];
+        for (const EBlk& eb : E[g])
+            finals.push_back(base[fid] + E_base[g] + (int64_t)member_index[p] * E_size[g] + eb.off);
         final_beg.push_back((int)finals.size());
     }
-    if (!launch_env_sweep(ctx, outs, ins, tiles, phase_beg, finals, final_beg, res, gs))
+    if (!launch_env_sweep_t(ctx, outs, ins, tiles, phase_beg, gph, mfac, ftab, K, base, finals, final_beg, res,
+                            gs))
         return dot_batch_sitewise(ctx, probs);
     GridSync h;
     BSM_CUDA(cudaMemcpyAsync(result.data(), res, sizeof(double) * P, cudaMemcpyDeviceToHost, ctx->stream));

@@ -697,33 +697,58 @@ struct Prof {
 // directly so that no FP64 instruction is spent on padding.
 constexpr int kEnvThreads = 128;
 
-__global__ void __launch_bounds__(kEnvThreads) k_env_sweep(const GemmOut* __restrict__ outs,
-                                                           const GemmIn* __restrict__ ins,
-                                                           const EnvTile* __restrict__ tiles,
-                                                           const int* __restrict__ phase_beg, int n_phase,
-                                                           const double* const* __restrict__ finals,
-                                                           const int* __restrict__ final_beg, int n_prob,
-                                                           double* __restrict__ res, GridSync* gs) {
+// One phase boundary between two CTAs; CTA skip_cta returns without arriving.
+__global__ void k_grid_wait_check(int skip_cta, GridSync* gs) {
     __shared__ int s_flag;
+    if ((int)blockIdx.x == skip_cta) return;
+    phase_end(gs, 0u, &s_flag);
+}
+
+__global__ void __launch_bounds__(kEnvThreads) k_env_sweep_t(const EnvOutT* __restrict__ outs,
+                                                             const EnvInT* __restrict__ ins,
+                                                             const EnvTileT* __restrict__ tiles,
+                                                             const int* __restrict__ phase_beg, int n_phase,
+                                                             const EnvGroupPhase* __restrict__ gph,
+                                                             const EnvMemberFac* __restrict__ mfac,
+                                                             const double* __restrict__ ftab, int K,
+                                                             const double* b0, const double* b1, const double* b2,
+                                                             const double* b3,
+                                                             const double* const* __restrict__ finals,
+                                                             const int* __restrict__ final_beg, int n_prob,
+                                                             double* __restrict__ res, GridSync* gs) {
+    __shared__ int s_flag;
+    const double* bases[4] = {b0, b1, b2, b3};
     for (int p = 0; p < n_phase; ++p) {
         for (int ti = phase_beg[p] + (int)blockIdx.x; ti < phase_beg[p + 1]; ti += (int)gridDim.x) {
-            const EnvTile tl = tiles[ti];
-            const GemmOut o = outs[tl.out];
+            const EnvTileT tl = tiles[ti];
+            const EnvOutT o = outs[tl.out];
+            const EnvGroupPhase g = gph[o.gp];
+            const EnvMemberFac mf = mfac[g.mem_beg + tl.member];
+            const int64_t mem = tl.member;
+            double* C = const_cast<double*>(bases[o.cbuf]) + g.base[o.cbuf] + mem * g.stride[o.cbuf] + o.coff;
             const int tm = min(32, o.M - tl.m0), tn = min(32, o.N - tl.n0);
             for (int e = threadIdx.x; e < tm * tn; e += kEnvThreads) {
                 const int m = tl.m0 + e / tn, n = tl.n0 + e % tn;
                 double acc = 0.0;
                 for (int c = o.beg; c < o.end; ++c) {
-                    const GemmIn in = ins[c];
-                    double part = 0.0;
-                    if (in.transA) {
-                        part = dev::dot_global<true, true>(in.A + m, in.lda, in.B + n, in.ldb, in.K, 0.0);
-                    } else {
-                        part = dev::dot_global<true, true>(in.A + (int64_t)m * in.lda, 1, in.B + n, in.ldb, in.K, 0.0);
+                    const EnvInT in = ins[c];
+                    const double* A = in.abuf < 0 ? in.A : bases[in.abuf] + g.base[in.abuf] + mem * g.stride[in.abuf] + in.aoff;
+                    const double* B = in.bbuf < 0 ? in.B : bases[in.bbuf] + g.base[in.bbuf] + mem * g.stride[in.bbuf] + in.boff;
+                    double alpha = in.w;
+                    if (in.so >= 0) {
+                        alpha += in.shift_flag ? g.shift : 0.0;
+                        const int ra = mf.row[in.so], rb = mf.row[2 + in.si];
+                        if (ra >= 0) alpha *= ftab[(int64_t)ra * K + in.site];
+                        if (rb >= 0) alpha *= ftab[(int64_t)rb * K + in.site];
                     }
-                    acc = fma(in.alpha, part, acc);
+                    double part;
+                    if (in.transA)
+                        part = dev::dot_global<true, true>(A + m, in.lda, B + n, in.ldb, in.K, 0.0);
+                    else
+                        part = dev::dot_global<true, true>(A + (int64_t)m * in.lda, 1, B + n, in.ldb, in.K, 0.0);
+                    acc = fma(alpha, part, acc);
                 }
-                o.C[(int64_t)m * o.ldc + n] = acc;
+                C[(int64_t)m * o.ldc + n] = acc;
             }
         }
         if (!phase_end(gs, (unsigned)p, &s_flag)) return;
@@ -734,13 +759,6 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_sweep(const GemmOut* __rest
             for (int i = final_beg[q]; i < final_beg[q + 1]; ++i) sum += __ldcg(finals[i]);
             res[q] = sum;
         }
-}
-
-// One phase boundary between two CTAs; CTA skip_cta returns without arriving.
-__global__ void k_grid_wait_check(int skip_cta, GridSync* gs) {
-    __shared__ int s_flag;
-    if ((int)blockIdx.x == skip_cta) return;
-    phase_end(gs, 0u, &s_flag);
 }
 
 }  // namespace
@@ -974,49 +992,6 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks_in, cons
     return true;
 }
 
-bool launch_env_sweep(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins,
-                      const std::vector<EnvTile>& tiles, const std::vector<int>& phase_beg,
-                      const std::vector<const double*>& finals, const std::vector<int>& final_beg, double* res,
-                      GridSync* gs) {
-    const int n_phase = (int)phase_beg.size() - 1;
-    const int n_prob = (int)final_beg.size() - 1;
-    if (n_phase <= 0 || n_prob <= 0) return false;
-    int maxt = 1;
-    for (int p = 0; p < n_phase; ++p) maxt = std::max(maxt, phase_beg[p + 1] - phase_beg[p]);
-    double fl = 0.0, by = 0.0;
-    for (const GemmOut& o : outs)
-        for (int c = o.beg; c < o.end; ++c) {
-            fl += 2.0 * o.M * o.N * (double)ins[c].K;
-            by += 8.0 * ((double)o.M * ins[c].K + (double)ins[c].K * o.N);
-        }
-    const int cap = coresident_ctas(k_env_sweep, kEnvThreads, 0);
-    if (cap <= 0) return false;
-    const int grid = std::min(maxt, cap);
-    ctx->flops += fl;
-    Pack pk;
-    const size_t oo = pk.add(outs), oi = pk.add(ins), ot = pk.add(tiles), op = pk.add(phase_beg), of = pk.add(finals),
-                 ob = pk.add(final_beg);
-    Scratch s(ctx);
-    unsigned char* d = upload_pack(s, pk);
-    const GemmOut* a0 = (const GemmOut*)(d + oo);
-    const GemmIn* a1 = (const GemmIn*)(d + oi);
-    const EnvTile* a2 = (const EnvTile*)(d + ot);
-    const int* a3 = (const int*)(d + op);
-    int a4 = n_phase;
-    const double* const* a5 = (const double* const*)(d + of);
-    const int* a6 = (const int*)(d + ob);
-    int a7 = n_prob;
-    double* a8 = res;
-    GridSync* a9 = gs;
-    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9};
-    Prof pr(ctx, KK_GEMM, fl, by);
-    BSM_CUDA(cudaLaunchCooperativeKernel((const void*)k_env_sweep, dim3(grid), dim3(kEnvThreads), args, 0,
-                                         ctx->stream));
-    count_launch(ctx);
-    pr.done();
-    return true;
-}
-
 int check_grid_wait(Context* ctx, int skip_cta) {
     Scratch s(ctx);
     GridSync* gs = (GridSync*)ctx->alloc(sizeof(GridSync));
@@ -1031,6 +1006,62 @@ int check_grid_wait(Context* ctx, int skip_cta) {
     BSM_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     ctx->sync();
     return h.err;
+}
+
+bool launch_env_sweep_t(Context* ctx, const std::vector<EnvOutT>& outs, const std::vector<EnvInT>& ins,
+                        const std::vector<EnvTileT>& tiles, const std::vector<int>& phase_beg,
+                        const std::vector<EnvGroupPhase>& gph, const std::vector<EnvMemberFac>& mfac,
+                        const std::vector<double>& ftab, int K, double* const base[4],
+                        const std::vector<const double*>& finals, const std::vector<int>& final_beg, double* res,
+                        GridSync* gs) {
+    const int n_phase = (int)phase_beg.size() - 1;
+    const int n_prob = (int)final_beg.size() - 1;
+    if (n_phase <= 0 || n_prob <= 0) return false;
+    int maxt = 1;
+    for (int p = 0; p < n_phase; ++p) maxt = std::max(maxt, phase_beg[p + 1] - phase_beg[p]);
+    double fl = 0.0, by = 0.0;
+    std::vector<int> tiles_of(outs.size(), 0);   // flops per output template times its members
+    for (const EnvTileT& t : tiles)
+        if (t.m0 == 0 && t.n0 == 0) tiles_of[t.out] += 1;
+    for (size_t o = 0; o < outs.size(); ++o)
+        for (int c = outs[o].beg; c < outs[o].end; ++c) {
+            fl += 2.0 * outs[o].M * outs[o].N * (double)ins[c].K * tiles_of[o];
+            by += 8.0 * ((double)outs[o].M * ins[c].K + (double)ins[c].K * outs[o].N) * tiles_of[o];
+        }
+    const int cap = coresident_ctas(k_env_sweep_t, kEnvThreads, 0);
+    if (cap <= 0) return false;
+    const int grid = std::min(maxt, cap);
+    ctx->flops += fl;
+    Pack pk;
+    const size_t oo = pk.add(outs), oi = pk.add(ins), ot = pk.add(tiles), op = pk.add(phase_beg), og = pk.add(gph),
+                 om = pk.add(mfac), of = pk.add(ftab), ofi = pk.add(finals), ob = pk.add(final_beg);
+    Scratch s(ctx);
+    unsigned char* d = upload_pack(s, pk);
+    const EnvOutT* a0 = (const EnvOutT*)(d + oo);
+    const EnvInT* a1 = (const EnvInT*)(d + oi);
+    const EnvTileT* a2 = (const EnvTileT*)(d + ot);
+    const int* a3 = (const int*)(d + op);
+    int a4 = n_phase;
+    const EnvGroupPhase* a5 = (const EnvGroupPhase*)(d + og);
+    const EnvMemberFac* a6 = (const EnvMemberFac*)(d + om);
+    const double* a7 = ftab.empty() ? nullptr : (const double*)(d + of);
+    int a8 = K;
+    const double* a9 = base[0];
+    const double* a10 = base[1];
+    const double* a11 = base[2];
+    const double* a12 = base[3];
+    const double* const* a13 = (const double* const*)(d + ofi);
+    const int* a14 = (const int*)(d + ob);
+    int a15 = n_prob;
+    double* a16 = res;
+    GridSync* a17 = gs;
+    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10, &a11, &a12, &a13, &a14, &a15, &a16, &a17};
+    Prof pr(ctx, KK_GEMM, fl, by);
+    BSM_CUDA(cudaLaunchCooperativeKernel((const void*)k_env_sweep_t, dim3(grid), dim3(kEnvThreads), args, 0,
+                                         ctx->stream));
+    count_launch(ctx);
+    pr.done();
+    return true;
 }
 
 }  // namespace bsm
