@@ -104,6 +104,27 @@ __device__ void left_body(const LeftTask& tk, const LeftSrc* __restrict__ srcs, 
         }
     }
     __syncthreads();
+    if (M <= N) {
+        // a stack with no more rows than columns is orthogonalised by Q = I:
+        // the new core holds the rows of the identity, R = A carries the block
+        // to the next site (any exact orthogonalisation serves the sweep: the
+        // SVD sweep that follows fixes the gauge)
+        for (int s = tk.s_beg; s < tk.s_end; ++s) {
+            const LeftSrc sr = srcs[s];
+            for (int64_t e = threadIdx.x; e < (int64_t)sr.rows * M; e += nthreads()) {
+                const int i = (int)(e / M), c = (int)(e % M);
+                sr.dst[e] = sr.r0 + i == c ? 1.0 : 0.0;
+            }
+        }
+        for (int x = tk.x_beg; x < tk.x_end; ++x) {
+            const LeftX lx = xs[x];
+            for (int64_t e = threadIdx.x; e < (int64_t)M * lx.cols; e += nthreads()) {
+                const int r = (int)(e / lx.cols), c = (int)(e % lx.cols);
+                lx.dst[e] = dev::dot_global<false, CG>(A + r, M, lx.X + c, lx.cols, N, 0.0);
+            }
+        }
+        return;
+    }
     if (k == 1) {
         left_rank1<CG>(tk, srcs, xs, A, red);
         return;
@@ -777,7 +798,8 @@ void launch_left_site(Context* ctx, const std::vector<LeftTask>& tasks, const st
     for (const LeftTask& t : tasks) {
         smem = std::max(smem, left_smem(t.M, t.N));
         const double m = t.M, n = t.N, k = t.k;
-        fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;
+        if (t.M > t.N)   // stacks with M <= N take Q = I
+            fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;
         by += 8.0 * (m * n + m * k);
         for (int x = t.x_beg; x < t.x_end; ++x) {
             fl += 2.0 * k * n * xs[x].cols;
@@ -913,7 +935,8 @@ bool launch_left_sweep(Context* ctx, const std::vector<LeftTask>& tasks, const s
         smem = std::max(smem, left_smem(t.M, t.N));
         kmax = std::max(kmax, 2 * t.k);
         const double m = t.M, n = t.N, k = t.k;
-        fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;
+        if (t.M > t.N)   // stacks with M <= N take Q = I
+            fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;
         by += 8.0 * (m * n + m * k);
         for (int x = t.x_beg; x < t.x_end; ++x) {
             fl += 2.0 * k * n * xs[x].cols;
