@@ -170,66 +170,95 @@ MpsPtr op_scale_sites(Context* ctx, const Mps* x, const std::vector<double>& f0,
     return y;
 }
 
-MpsPtr op_apply_exact(Context* ctx, const Mpo& W, const Mps* x, double shift) {
+std::vector<MpsPtr> op_apply_exact_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
+                                          const std::vector<std::vector<double>>& f0,
+                                          const std::vector<std::vector<double>>& f1) {
     const Layout& X = x->lay;
     BSM_REQUIRE(W.K == X.K && W.species == X.species, BSMPS_ERR_INVALID_ARG,
                 "MPO and MPS act on different sites");
+    BSM_REQUIRE(f0.size() == f1.size() && !f0.empty(), BSMPS_ERR_INVALID_ARG, "scalings mismatch");
     const int K = X.K;
+    const int n = (int)f0.size();
     const auto valid = valid_sectors(X.species, X.target);
     Layout Y;
     Y.K = K;
     Y.species = X.species;
     Y.target = X.target;
     Y.bonds.resize(K + 1);
-    // chan_off[b][sector][channel] = row offset of the channel's segment (-1: absent)
-    std::vector<std::vector<std::vector<int>>> chan_off(K + 1);
+    // For bond b, X sector li and channel a: the output sector holding the
+    // product (-1: none) and the row offset of channel a's segment in it.
+    std::vector<std::vector<int>> ysec(K + 1), yoff(K + 1);
     for (int b = 0; b <= K; ++b) {
         const int w = W.bond_dim(b);
+        const int nx = (int)X.bonds[b].q.size();
+        ysec[b].assign((size_t)nx * w, -1);
+        yoff[b].assign((size_t)nx * w, -1);
         for (const Charge& m : valid[b]) {
-            std::vector<int> co(w, -1);
+            const int ml = (int)Y.bonds[b].q.size();
             int tot = 0;
             for (int a = 0; a < w; ++a) {
-                const int ni = X.bonds[b].find(m - W.charges[b][a]);
-                if (ni < 0) continue;
-                co[a] = tot;
-                tot += X.bonds[b].dim[ni];
+                const int li = X.bonds[b].find(m - W.charges[b][a]);
+                if (li < 0) continue;
+                ysec[b][(size_t)li * w + a] = ml;
+                yoff[b][(size_t)li * w + a] = tot;
+                tot += X.bonds[b].dim[li];
             }
             if (tot > 0) {
                 Y.bonds[b].q.push_back(m);
                 Y.bonds[b].dim.push_back(tot);
-                chan_off[b].push_back(co);
             }
         }
     }
     Y.rebuild_blocks();
-    MpsPtr y = make_mps(ctx, Y, true);
+    // every output zeroed in one launch, then every piece of every output in one copy launch
+    std::vector<MpsPtr> ys;
+    std::vector<double*> zp;
+    std::vector<int64_t> zn;
+    for (int i = 0; i < n; ++i) {
+        ys.push_back(make_mps(ctx, Y, false));
+        for (int t = 0; t < K; ++t)
+            if (Y.core_size[t] > 0) {
+                zp.push_back(ys[i]->core[t]);
+                zn.push_back(Y.core_size[t]);
+            }
+    }
+    launch_zero(ctx, zp, zn);
     std::vector<CopyTask> tasks;
     double fl = 0.0;
     for (int t = 0; t < K; ++t) {
         const std::vector<int> look = block_lookup(Y, t);
+        const int wl = W.bond_dim(t), wr = W.bond_dim(t + 1);
         const auto& ents = W.entries[t];
-        for (int ei = 0; ei < (int)ents.size(); ++ei) {
-            const MpoEntry& e = ents[ei];
-            double w = e.w;
-            if (t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1])) w += shift;
-            for (const Block& bk : X.blocks[t]) {
+        for (const Block& bk : X.blocks[t])
+            for (int ei = 0; ei < (int)ents.size(); ++ei) {
+                const MpoEntry& e = ents[ei];
                 if (bk.sigma != e.si) continue;
-                const int ml = Y.bonds[t].find(X.bonds[t].q[bk.li] + W.charges[t][e.a]);
-                const int mr = Y.bonds[t + 1].find(X.bonds[t + 1].q[bk.ri] + W.charges[t + 1][e.b]);
+                const size_t il = (size_t)bk.li * wl + e.a, ir = (size_t)bk.ri * wr + e.b;
+                const int ml = ysec[t][il], mr = ysec[t + 1][ir];
                 if (ml < 0 || mr < 0) continue;
-                const int ra = chan_off[t][ml][e.a], rb = chan_off[t + 1][mr][e.b];
                 const int yb = look[ml * 2 + e.so];
-                if (ra < 0 || rb < 0 || yb < 0) continue;
+                if (yb < 0) continue;
                 const Block& yk = Y.blocks[t][yb];
-                tasks.push_back({x->core[t] + bk.off, y->core[t] + yk.off + (int64_t)ra * yk.cols + rb,
-                                 bk.rows, bk.cols, bk.cols, yk.cols, 0, 0, 0, w});
-                fl += 2.0 * bk.rows * bk.cols;
+                double w = e.w;
+                if (t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1])) w += shift;
+                const int64_t dst = yk.off + (int64_t)yoff[t][il] * yk.cols + yoff[t + 1][ir];
+                for (int i = 0; i < n; ++i) {
+                    const std::vector<double>& f = bk.sigma ? f1[i] : f0[i];
+                    tasks.push_back({x->core[t] + bk.off, ys[i]->core[t] + dst, bk.rows, bk.cols, bk.cols,
+                                     yk.cols, 0, 0, 0, f.empty() ? w : w * f[t]});
+                }
+                fl += 2.0 * n * bk.rows * bk.cols;
             }
-        }
     }
     ctx->flops += fl;
     launch_copy(ctx, tasks);
-    return y;
+    return ys;
+}
+
+MpsPtr op_apply_exact(Context* ctx, const Mpo& W, const Mps* x, double shift) {
+    const std::vector<std::vector<double>> none(1);   // one output, unscaled
+    std::vector<MpsPtr> ys = op_apply_exact_scaled(ctx, W, x, shift, none, none);
+    return std::move(ys[0]);
 }
 
 std::vector<int> choose_cut(std::vector<SvEntry> sv, int n_sectors, double tol2, int r_max,

@@ -29,6 +29,12 @@ MpsPtr op_scale_sites(Context* ctx, const Mps* x, const std::vector<double>& f0,
 // y = (H_gamma + shift I) x exactly (Sec. 2.4).
 MpsPtr op_apply_exact(Context* ctx, const Mpo& W, const Mps* x, double shift);
 
+// y_i = (H_gamma + shift I) S_i x for site scalings S_i = (f0[i], f1[i]) as in
+// ConcatTerm: one layout, one zeroing launch and one copy launch for all i.
+std::vector<MpsPtr> op_apply_exact_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
+                                          const std::vector<std::vector<double>>& f0,
+                                          const std::vector<std::vector<double>>& f1);
+
 // trunc_eps with rank cap (Sec. 2.2); discarded norms are returned.
 MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
                    double* disc_cap);

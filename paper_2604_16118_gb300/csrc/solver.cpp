@@ -154,11 +154,7 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
     s0[0] = s1[0] = 1.0 / std::sqrt(num);
     MpsPtr x = op_scale_sites(ctx, x_in, s0, s1);
     // residual terms: u_k' = (H_gamma - lambda) S_k' x, s_{k,k'} = S_k u_k'
-    std::vector<MpsPtr> u(nt);
-    for (int kp = 0; kp < nt; ++kp) {
-        MpsPtr sx = op_scale_sites(ctx, x.get(), P.f0[kp], P.f1[kp]);
-        u[kp] = op_apply_exact(ctx, W, sx.get(), -lam);
-    }
+    std::vector<MpsPtr> u = op_apply_exact_scaled(ctx, W, x.get(), -lam, P.f0, P.f1);
     if (prm.u_rel > 0.0) {
         // one near-lossless compression per exactly applied term (trunc at u_rel ||u||)
         std::vector<EnvProblem> up;
