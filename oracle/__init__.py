@@ -20,4 +20,6 @@ Modules (each function cites the part of the paper it follows):
 * ``pinvit``   -- one step of the perturbed inverse iteration (Alg. 2) with
   the adaptive residual (Sec. 5.3.1), the 2x2 Rayleigh--Ritz step (Remark
   omegamin) and the a-posteriori bounds (Sec. 5.4).
+* ``joint``    -- joint block MPS of D vectors and the perturbed inverse
+  subspace iteration (Alg. 4, Sec. 6).
 """

@@ -74,16 +74,18 @@ def config_counts(species, target, b, q):
     return left, right
 
 
-def default_dims(species, target, r_max):
+def default_dims(species, target, r_max, D=1):
     """Block dims rho_{b,q} of a fresh iterate of maximal rank r_max:
     rho = min(left count, right count) when these fit r_max in total, otherwise
     rho = min(left, right, floor(r_max * left*right / sum_q left*right)) (exact
-    integer arithmetic); sectors of dim 0 are dropped."""
+    integer arithmetic); sectors of dim 0 are dropped.  For a joint block MPS of
+    D columns (Sec. 6.2, column index after the last site) the right counts are
+    multiplied by D, so the last bond has dimension D."""
     K = len(species)
     ranges = valid_ranges(species, target)
     dims = []
     for b in range(K + 1):
-        cnt = [config_counts(species, target, b, q) for q in ranges[b]]
+        cnt = [(l, r * D) for l, r in (config_counts(species, target, b, q) for q in ranges[b])]
         exact = [min(l, r) for l, r in cnt]
         if sum(exact) <= r_max:
             d = exact
@@ -203,6 +205,32 @@ def to_dense(x):
     return cur[x.target][:, 0]
 
 
+def columns(x):
+    """Number of represented vectors: the dimension of the last bond (1 for a
+    plain MPS, D for a joint block MPS with the eigenvector index there, Sec. 6.2)."""
+    return sum(x.bonds[x.K].values())
+
+
+def to_dense_cols(x):
+    """Dense 2^K x D matrix of a joint block MPS (column i = vector i), tiny K only."""
+    K = x.K
+    cur = {(0, 0): np.ones((1, 1))}
+    for t in range(K):
+        nxt = {}
+        for (n, sg), B in x.cores[t].items():
+            if n not in cur:
+                continue
+            m = add_charge(n, delta(x.species[t], sg))
+            left = cur[n]
+            blk = np.zeros((left.shape[0] * 2, B.shape[1]))
+            blk[sg::2] = left @ B
+            nxt[m] = nxt[m] + blk if m in nxt else blk
+        cur = nxt
+    if x.target not in cur:
+        return np.zeros((1 << K, columns(x)))
+    return cur[x.target]
+
+
 def scale_sites(x, f0, f1):
     """Multiply every sigma=0 block of site t by f0[t] and every sigma=1 block by f1[t]
     (action of one rank-one diagonal Kronecker factor, Sec. 4.3)."""
@@ -228,9 +256,17 @@ def add(x, y, alpha=1.0, beta=1.0):
     K = x.K
     bonds = []
     for b in range(K + 1):
-        if b in (0, K):
+        if b == 0:
             qs = sorted(set(x.bonds[b]) | set(y.bonds[b]))
             bonds.append({q: 1 for q in qs})
+        elif b == K:
+            # the last bond carries the column index of a joint block MPS (Sec. 6.2):
+            # both summands have the same columns, which are added, not stacked
+            qs = sorted(set(x.bonds[b]) | set(y.bonds[b]))
+            for q in qs:
+                if q in x.bonds[b] and q in y.bonds[b]:
+                    assert x.bonds[b][q] == y.bonds[b][q], "different column counts"
+            bonds.append({q: x.bonds[b].get(q, y.bonds[b].get(q)) for q in qs})
         else:
             qs = sorted(set(x.bonds[b]) | set(y.bonds[b]))
             bonds.append({q: x.bonds[b].get(q, 0) + y.bonds[b].get(q, 0) for q in qs})
@@ -255,12 +291,18 @@ def add(x, y, alpha=1.0, beta=1.0):
     return BSMPS(x.species, x.target, bonds, cores)
 
 
-def apply_exact(mpo, x, shift=0.0):
+def apply_exact(mpo, x, shift=0.0, col_shift=None):
     """y = (H + shift I) x without truncation (Sec. 2.4): y's bond-b basis is the
     product of MPO channels a and x's basis; sector m holds segments (a, n) with
     n = m - Delta_a, ordered by channel; sectors outside the valid sets are
     dropped (no complete path runs through them).  Each sub-block (a, b) of
-    y's block (m, sigma') equals sum w(a,b,sigma',sigma) X(n_a, sigma)."""
+    y's block (m, sigma') equals sum w(a,b,sigma',sigma) X(n_a, sigma).
+
+    col_shift (joint block MPS, Sec. 6.1): column i of y gets col_shift[i] x_i
+    added, i.e. y = H X + X diag(col_shift).  The identity reaches the last site
+    on the MPO's identity rail (channel I on every bond before the last site),
+    so the term is X's last core times diag(col_shift) added to the (I, F)
+    sub-block of each last-site block."""
     K = x.K
     ranges = valid_ranges(x.species, x.target)
     segs = []
@@ -300,12 +342,31 @@ def apply_exact(mpo, x, shift=0.0):
                         continue
                     assert add_charge(n_a, delta(sp, ei)) == n_b
                     Y[r0:r0 + rd, c0:c0 + cd] += w * x.cores[t][(n_a, ei)]
+                if col_shift is not None and t == K - 1:
+                    a = mpo.channels[t].index(("I",))
+                    if a in rowseg and 0 in colseg and (rowseg[a][0], so) in x.cores[t]:
+                        n_a, r0, rd = rowseg[a]
+                        _, c0, cd = colseg[0]
+                        Y[r0:r0 + rd, c0:c0 + cd] += x.cores[t][(n_a, so)] * np.asarray(col_shift)[None, :]
                 cores[t][(m, so)] = Y
     return BSMPS(x.species, x.target, bonds, cores)
 
 
-def dot(a, b, mpo=None, shift=0.0):
-    """<a, O b> by the left-to-right environment recursion (Sec. 2.4):
+def mix_columns(x, W):
+    """X W for a joint block MPS (Sec. 6.1): the last core's blocks times the
+    D_in x D_out matrix W; the last bond becomes D_out wide."""
+    W = np.asarray(W, dtype=np.float64)
+    assert W.shape[0] == columns(x)
+    y = x.copy()
+    K = y.K
+    for k in list(y.cores[K - 1].keys()):
+        y.cores[K - 1][k] = y.cores[K - 1][k] @ W
+    y.bonds[K] = {q: W.shape[1] for q in y.bonds[K]}
+    return y
+
+
+def _environments(a, b, mpo=None, shift=0.0):
+    """Environments at bond K of <a, O b> by the left-to-right recursion (Sec. 2.4):
     E_{t+1}[d](n_a', n_b') = sum w(c,d,s',s) A(n_a,s')^T E_t[c](n_a,n_b) B(n_b,s).
     With mpo=None, O is the identity (one channel)."""
     K = a.K
@@ -334,11 +395,26 @@ def dot(a, b, mpo=None, shift=0.0):
                 Ed = nE.setdefault(d, {})
                 Ed[key] = Ed[key] + val if key in Ed else val
         E = nE
+    return E
+
+
+def dot(a, b, mpo=None, shift=0.0):
+    """<a, O b> (Sec. 2.4) for MPS with one column."""
     tot = 0.0
-    for Ec in E.values():
+    for Ec in _environments(a, b, mpo, shift).values():
         for M in Ec.values():
             tot += M[0, 0]
     return tot
+
+
+def gram(a, b, mpo=None, shift=0.0):
+    """The D_a x D_b matrix <a_i, O b_j> of two joint block MPS (Sec. 6.1): the
+    same recursion, whose last environment keeps both column indices."""
+    G = np.zeros((columns(a), columns(b)))
+    for Ec in _environments(a, b, mpo, shift).values():
+        for M in Ec.values():
+            G += M
+    return G
 
 
 def norm(x):
