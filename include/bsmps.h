@@ -311,6 +311,96 @@ BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const b
                                    bsmps_solver_state* state, bsmps_mps* x,
                                    bsmps_step_info* info);
 
+/* ---- joint block MPS and the subspace iteration (Alg. 4, Sec. 6) -------- */
+
+/* A joint block MPS holds D vectors x_1..x_D in one MPS whose last bond (the
+ * single target sector) has dimension D: the eigenvector-specific core of
+ * Sec. 6.2 placed after the last site (position p = K + 1) and absorbed into
+ * the last core.  Inner bonds carry the vectors' bases stacked block-diagonally,
+ * so their ranks are at most the sums of the individual ranks.  Vector i is
+ * column i of the last core's blocks.  A plain MPS is the case D = 1.
+ * bsmps_truncate (one tolerance for the whole joint tensor, Frobenius norm
+ * over all columns), bsmps_add (columns added, not stacked) and
+ * bsmps_scale_sites accept joint MPS; bsmps_dot, bsmps_dot_noalloc and the
+ * single-vector solvers require D = 1. */
+#define BSMPS_MAX_COLUMNS 16
+
+/* Number of float64 entries of a fresh random joint iterate of D columns: the
+ * rule of bsmps_mps_random_size with every right configuration count
+ * multiplied by D.  Errors: INVALID_ARG, CHARGE. */
+BSMPS_API bsmps_status bsmps_mps_joint_random_size(int n_orb, int spin, int n_up, int n_dn, int r_max, int D,
+                                                   int64_t* n_values);
+
+/* New joint iterate of D columns.  init = 0: the unit vectors of the D
+ * occupation strings in occ (host, D x K bytes, row i = vector i, entries 0/1,
+ * each in the particle sector): vector i owns one basis index on every inner
+ * bond (block-diagonal stacking of Sec. 6.2).  init = 1: random, blocks of the
+ * rule of bsmps_mps_joint_random_size filled from values (host, flat layout).
+ * Errors: INVALID_ARG, CHARGE, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_mps_create_joint(bsmps_ctx ctx, int n_orb, int spin, int n_up, int n_dn, int D,
+                                              int init, const unsigned char* occ, int r_max, const double* values,
+                                              int64_t n_values, bsmps_mps* out);
+
+/* D of a (joint) MPS. */
+BSMPS_API bsmps_status bsmps_mps_num_columns(bsmps_mps x, int* D);
+
+/* out = the D_a x D_b matrix <a_i, O b_j> (row-major, host) with
+ * O = H_gamma + shift I given by W, or the identity when W is NULL: one
+ * left-to-right environment sweep whose last environment keeps both column
+ * indices (Sec. 6.1).  Errors: INVALID_ARG, RANK_CAP (environments too large
+ * for the persistent sweep), OOM, CUDA, TIMEOUT. */
+BSMPS_API bsmps_status bsmps_gram(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, double shift,
+                                  double* out);
+
+/* Exact y = (H_gamma + shift I) X + X diag(col_shift) for a joint block MPS X of
+ * D columns (col_shift: host, D entries), the operator of Eq. (respara) with
+ * shift = 0 and col_shift = -Lambda.  The column term enters on the MPO's
+ * identity rail at the last site, so y has the bond dimensions of the exact
+ * application (see bsmps_apply_H).  Errors: INVALID_ARG, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_apply_columns(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift,
+                                           const double* col_shift, bsmps_mps* y);
+
+/* y = X Wm: the D_in x D_out row-major host matrix Wm mixes the columns (the
+ * last core's blocks are multiplied by Wm), y has D_out columns (Sec. 6.1).
+ * Errors: INVALID_ARG (K = 1), OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_mix_columns(bsmps_ctx ctx, bsmps_mps x, const double* Wm, int D_out, bsmps_mps* y);
+
+/* Scalars reported by one step of Alg. 4 (column i = i-th lowest Ritz value). */
+typedef struct {
+    int D;
+    double lambda[BSMPS_MAX_COLUMNS];       /* Lambda^n after the Rayleigh-Ritz step on X^n */
+    double rho[BSMPS_MAX_COLUMNS];          /* rho_i^n, Eq. (rhobound) with ||x_i||_A = 1 */
+    double res_norm[BSMPS_MAX_COLUMNS];     /* ||r_i^n|| of res_eta(X^n) */
+    double lambda_star[BSMPS_MAX_COLUMNS];  /* lowest D Ritz values on span (X^n R^n) */
+    double delta_A[BSMPS_MAX_COLUMNS];
+    double eta_res;      /* accepted residual tolerance */
+    int eta_tries;       /* passes of the eta_res loop beyond the first */
+    double bound;        /* eigenvector bound of column 1 (Thm. aposterbound) */
+    double releig_bound; /* relative eigenvalue bound of column 1, Eq. (releigerr) */
+    double eta_in;       /* truncation tolerance of the iterate */
+    int converged;       /* 1 when the termination test of Alg. 4 held */
+    int max_rank;        /* largest bond dimension of the returned iterate */
+    double flops;        /* algorithmic FP64 flops issued by the step */
+    double cap_discarded;
+} bsmps_joint_step_info;
+
+/* One pass of the loop body of Alg. 4 on the joint iterate X^n = *x (D
+ * columns, 1 <= D <= BSMPS_MAX_COLUMNS): Rayleigh-Ritz on span X^n (lowest
+ * generalized eigenpairs of X^T A X, X^T E X; A-orthonormal columns, Lambda^n);
+ * residual terms S_k (H_gamma S_k' X - S_k' X Lambda) (Eq. (respara)) summed by
+ * res_eta as in Alg. 2 with Frobenius norms of the joint terms, eta_res
+ * multiplied by 4/5 while min_i ||r_i|| < (1 + 1/zeta) eta_res; rho_i; the
+ * termination test on rho_1; Rayleigh-Ritz on span (X^n R^n) in the basis
+ * normalised by the column norms (Sec. 6.1), lowest D pairs;
+ * eta_in = (1+c)^{-1/2} min_i Delta_{A,i}; X^{n+1} = trunc_{eta_in}(X*) capped at
+ * params->r_max.  Gram matrices use the symmetry of H_gamma and the S_k.
+ * *x is replaced (old handle destroyed); state as for bsmps_eigensolve_step.
+ * Errors: INVALID_ARG, NOT_SPD, NUMERIC (also a singular subspace basis), OOM,
+ * CUDA, TIMEOUT. */
+BSMPS_API bsmps_status bsmps_eigensolve_joint_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
+                                                   const bsmps_solver_params* params, bsmps_solver_state* state,
+                                                   bsmps_mps* x, bsmps_joint_step_info* info);
+
 /* One outer step of Alg. 3 as reported by bsmps_eigensolve_outer. */
 typedef struct {
     int inner_steps;       /* Alg. 2 steps run from y^m */

@@ -174,6 +174,13 @@ bsm::Charge target_of(int n_up, int n_dn, int spin) {
     return spin ? bsm::Charge{n_up, n_dn} : bsm::Charge{n_up, 0};
 }
 
+void check_params(const bsmps_solver_params* params) {
+    BSM_REQUIRE(params->c > 0.0 && params->c < 1.0 && params->delta > 1.0 && params->eps_num > 0.0 &&
+                    params->eps_num < 1.0 - params->c && params->t_eig > 0.0 && params->t_eig < 1.0 &&
+                    params->r_max >= 0 && params->u_rel >= 0.0 && params->u_rel < 1e-3,
+                BSMPS_ERR_INVALID_ARG, "solver parameters out of range");
+}
+
 }  // namespace
 
 extern "C" {
@@ -275,6 +282,86 @@ bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset, int64_t*
             }
             c->prof.clear();
         }
+    });
+}
+
+bsmps_status bsmps_mps_joint_random_size(int n_orb, int spin, int n_up, int n_dn, int r_max, int D,
+                                         int64_t* n_values) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(n_orb > 0 && r_max > 0 && D >= 1 && n_values, BSMPS_ERR_INVALID_ARG,
+                    "n_orb, r_max, D > 0 required");
+        bsm::Layout L = bsm::default_layout(bsm::species_of(n_orb, spin), target_of(n_up, n_dn, spin), r_max, D);
+        *n_values = L.total();
+    });
+}
+
+bsmps_status bsmps_mps_create_joint(bsmps_ctx ctx, int n_orb, int spin, int n_up, int n_dn, int D, int init,
+                                    const unsigned char* occ, int r_max, const double* values, int64_t n_values,
+                                    bsmps_mps* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(n_orb > 0 && D >= 1 && out && (init == 0 || init == 1), BSMPS_ERR_INVALID_ARG,
+                    "n_orb > 0, D >= 1, init in {0, 1} and out required");
+        const auto species = bsm::species_of(n_orb, spin);
+        const bsm::Charge tgt = target_of(n_up, n_dn, spin);
+        bsm::Layout L;
+        std::vector<double> vals;
+        const double* src = values;
+        if (init == 0) {
+            L = bsm::determinant_layout(species, tgt, occ, D, &vals);
+            src = vals.data();
+        } else {
+            BSM_REQUIRE(r_max > 0, BSMPS_ERR_INVALID_ARG, "r_max > 0 required");
+            L = bsm::default_layout(species, tgt, r_max, D);
+            BSM_REQUIRE(values && n_values == L.total(), BSMPS_ERR_INVALID_ARG,
+                        "values must hold exactly bsmps_mps_joint_random_size entries");
+        }
+        bsm::check_layout(L);
+        bsm::MpsPtr x(bsm::new_mps(c, L, false));
+        bsm::mps_upload(x.get(), src);
+        *out = wrap(std::move(x));
+    });
+}
+
+bsmps_status bsmps_mps_num_columns(bsmps_mps x, int* D) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(x && D, BSMPS_ERR_INVALID_ARG, "null argument");
+        *D = M(x)->lay.columns();
+    });
+}
+
+bsmps_status bsmps_gram(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, double shift, double* out) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(a && b && out, BSMPS_ERR_INVALID_ARG, "null argument");
+        bsm::EnvProblem pr{M(a), M(b), W ? &W->W : nullptr, shift};
+        const auto g = bsm::op_gram_batch(c, {pr});
+        std::copy(g[0].begin(), g[0].end(), out);
+    });
+}
+
+bsmps_status bsmps_apply_columns(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift, const double* col_shift,
+                                 bsmps_mps* y) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(W && x && col_shift && y, BSMPS_ERR_INVALID_ARG, "null argument");
+        const std::vector<double> cs(col_shift, col_shift + M(x)->lay.columns());
+        const std::vector<std::vector<double>> none(1);
+        std::vector<bsm::MpsPtr> r = bsm::op_apply_exact_scaled(c, W->W, M(x), shift, none, none, &cs);
+        c->sync();
+        *y = wrap(std::move(r[0]));
+    });
+}
+
+bsmps_status bsmps_mix_columns(bsmps_ctx ctx, bsmps_mps x, const double* Wm, int D_out, bsmps_mps* y) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(x && Wm && D_out >= 1 && y, BSMPS_ERR_INVALID_ARG, "null argument or D_out < 1");
+        const int din = M(x)->lay.columns();
+        bsm::ConcatTerm t{M(x), {}, {}, std::vector<double>(Wm, Wm + (size_t)din * D_out), D_out};
+        bsm::MpsPtr r = bsm::op_concat(c, {t});
+        c->sync();
+        *y = wrap(std::move(r));
     });
 }
 
@@ -538,6 +625,8 @@ bsmps_status bsmps_dot(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mpo W, dou
     return guarded(ctx, [&] {
         bsm::Context* c = C(ctx);
         BSM_REQUIRE(out, BSMPS_ERR_INVALID_ARG, "null out");
+        BSM_REQUIRE(M(a)->lay.columns() == 1 && M(b)->lay.columns() == 1, BSMPS_ERR_INVALID_ARG,
+                    "joint block MPS: use bsmps_gram");
         bsm::EnvProblem pr{M(a), M(b), W ? &W->W : nullptr, shift};
         *out = bsm::op_dot_batch(c, {pr})[0];
     });
@@ -548,6 +637,8 @@ bsmps_status bsmps_dot_noalloc(bsmps_ctx ctx, bsmps_mps a, bsmps_mps b, bsmps_mp
     return guarded(ctx, [&] {
         bsm::Context* c = C(ctx);
         BSM_REQUIRE(out, BSMPS_ERR_INVALID_ARG, "null out");
+        BSM_REQUIRE(M(a)->lay.columns() == 1 && M(b)->lay.columns() == 1, BSMPS_ERR_INVALID_ARG,
+                    "joint block MPS: use bsmps_gram");
         *out = bsm::op_dot_noalloc(c, M(a), M(b), W ? &W->W : nullptr, shift);
     });
 }
@@ -581,18 +672,38 @@ bsmps_status bsmps_eigensolve_outer(bsmps_ctx ctx, bsmps_mpo W, const bsmps_prec
     });
 }
 
+bsmps_status bsmps_eigensolve_joint_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
+                                         const bsmps_solver_params* params, bsmps_solver_state* state, bsmps_mps* x,
+                                         bsmps_joint_step_info* info) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(W && params && state && x && *x && info, BSMPS_ERR_INVALID_ARG, "null argument");
+        check_params(params);
+        const bsm::PrecondTerms P = bsm::make_precond(p);
+        BSM_REQUIRE(p->K == M(*x)->lay.K, BSMPS_ERR_INVALID_ARG, "precond K differs from the MPS");
+        bsmps_joint_step_info inf;
+        bsmps_solver_state st = *state;
+        bsm::MpsPtr r = bsm::eigensolve_joint_step(c, W->W, P, *params, st, M(*x), inf);
+        c->sync();
+        *state = st;
+        *info = inf;
+        bsmps_mps old = *x;
+        *x = wrap(std::move(r));
+        delete old;
+    });
+}
+
 bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const bsmps_precond* p,
                                    const bsmps_solver_params* params, bsmps_solver_state* state, bsmps_mps* x,
                                    bsmps_step_info* info) {
     return guarded(ctx, [&] {
         bsm::Context* c = C(ctx);
         BSM_REQUIRE(W && params && state && x && *x && info, BSMPS_ERR_INVALID_ARG, "null argument");
-        BSM_REQUIRE(params->c > 0.0 && params->c < 1.0 && params->delta > 1.0 && params->eps_num > 0.0 &&
-                        params->eps_num < 1.0 - params->c && params->t_eig > 0.0 && params->t_eig < 1.0 &&
-                        params->r_max >= 0 && params->u_rel >= 0.0 && params->u_rel < 1e-3,
-                    BSMPS_ERR_INVALID_ARG, "solver parameters out of range");
+        check_params(params);
         const bsm::PrecondTerms P = bsm::make_precond(p);
         BSM_REQUIRE(p->K == M(*x)->lay.K, BSMPS_ERR_INVALID_ARG, "precond K differs from the MPS");
+        BSM_REQUIRE(M(*x)->lay.columns() == 1, BSMPS_ERR_INVALID_ARG,
+                    "joint block MPS: use bsmps_eigensolve_joint_step");
         bsmps_step_info inf;
         bsmps_solver_state st = *state;
         bsm::MpsPtr r = bsm::eigensolve_step(c, W->W, P, *params, st, M(*x), inf);

@@ -72,12 +72,21 @@ struct Layout {
     void rebuild_blocks();             // from bonds
     int64_t total() const;
     int block_index(int t, int li, int sigma) const;  // -1 if absent
+    // Represented vectors: the dimension of the last bond (1 for a plain MPS,
+    // D for a joint block MPS whose column index follows the last site, Sec. 6.2).
+    int columns() const { return bonds.empty() || bonds.back().q.empty() ? 1 : bonds.back().dim[0]; }
 };
 
 std::vector<int> species_of(int n_orb, int spin);
 std::vector<std::vector<Charge>> valid_sectors(const std::vector<int>& species, Charge target);
-Layout default_layout(const std::vector<int>& species, Charge target, int r_max);
+// D > 1: a joint block MPS of D columns (right counts times D, last bond D wide).
+Layout default_layout(const std::vector<int>& species, Charge target, int r_max, int D = 1);
 Layout e1_layout(const std::vector<int>& species, Charge target);
+// Joint block MPS of the unit vectors given by D occupation strings (occ: D x K
+// bytes, row i = vector i): every vector owns one index per inner bond, in
+// order of i; values (one 1 per vector and site) written to *values.
+Layout determinant_layout(const std::vector<int>& species, Charge target, const unsigned char* occ, int D,
+                          std::vector<double>* values);
 void check_layout(const Layout& L);
 
 // MPO: per site a sorted list of entries; per bond channel charges.
@@ -92,6 +101,7 @@ struct Mpo {
     std::vector<std::vector<Charge>> charges;     // per bond, per channel
     std::vector<std::vector<MpoEntry>> entries;   // per site, sorted (a, b, so, si)
     int shift_entry[2] = {-1, -1};                // site-0 entries (I->F, s, s)
+    int ident_last = -1;                          // identity channel I on bond K-1
     int bond_dim(int b) const { return (int)charges[b].size(); }
 };
 

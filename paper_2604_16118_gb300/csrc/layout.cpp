@@ -108,13 +108,14 @@ void check_layout(const Layout& L) {
                     "bond 0 must be the single sector (0,0) of dim 1");
     }
     if (!L.bonds[L.K].q.empty()) {
-        BSM_REQUIRE(L.bonds[L.K].q.size() == 1 && L.bonds[L.K].dim[0] == 1,
-                    BSMPS_ERR_INVALID_ARG, "bond K must be the single target sector of dim 1");
+        // dim > 1: the column index of a joint block MPS (Sec. 6.2)
+        BSM_REQUIRE(L.bonds[L.K].q.size() == 1, BSMPS_ERR_INVALID_ARG,
+                    "bond K must be the single target sector");
     }
 }
 
 // Block dims of a fresh iterate (see bsmps_mps_random_size).
-Layout default_layout(const std::vector<int>& species, Charge target, int r_max) {
+Layout default_layout(const std::vector<int>& species, Charge target, int r_max, int D) {
     Layout L;
     L.K = (int)species.size();
     L.species = species;
@@ -133,7 +134,7 @@ Layout default_layout(const std::vector<int>& species, Charge target, int r_max)
         unsigned __int128 exact_sum = 0, wsum = 0;
         for (const Charge& q : valid[b]) {
             unsigned __int128 l = binom(Lc[0], q.q0) * binom(Lc[1], q.q1);
-            unsigned __int128 r = binom(R0, target.q0 - q.q0) * binom(R1, target.q1 - q.q1);
+            unsigned __int128 r = binom(R0, target.q0 - q.q0) * binom(R1, target.q1 - q.q1) * (unsigned)D;
             lc.push_back(l);
             rc.push_back(r);
             exact_sum += std::min(l, r);
@@ -179,6 +180,65 @@ Layout e1_layout(const std::vector<int>& species, Charge target) {
     }
     BSM_REQUIRE(q == target, BSMPS_ERR_CHARGE, "particle numbers exceed the number of sites");
     L.rebuild_blocks();
+    return L;
+}
+
+Layout determinant_layout(const std::vector<int>& species, Charge target, const unsigned char* occ, int D,
+                          std::vector<double>* values) {
+    const int K = (int)species.size();
+    BSM_REQUIRE(D >= 1 && occ, BSMPS_ERR_INVALID_ARG, "D >= 1 occupation strings required");
+    // charge path and index of every vector on every bond
+    std::vector<std::vector<Charge>> path(D, std::vector<Charge>(K + 1));
+    for (int i = 0; i < D; ++i) {
+        Charge q{0, 0};
+        path[i][0] = q;
+        for (int t = 0; t < K; ++t) {
+            const unsigned char o = occ[(size_t)i * K + t];
+            BSM_REQUIRE(o <= 1, BSMPS_ERR_INVALID_ARG, "occupations must be 0 or 1");
+            q = q + site_delta(species[t], o);
+            path[i][t + 1] = q;
+        }
+        BSM_REQUIRE(q == target, BSMPS_ERR_CHARGE, "occupation string outside the particle sector");
+    }
+    Layout L;
+    L.K = K;
+    L.species = species;
+    L.target = target;
+    L.bonds.resize(K + 1);
+    std::vector<std::vector<int>> pos(D, std::vector<int>(K + 1, 0));
+    for (int b = 0; b <= K; ++b) {
+        std::vector<Charge> qs;
+        for (int i = 0; i < D; ++i) qs.push_back(path[i][b]);
+        std::sort(qs.begin(), qs.end());
+        qs.erase(std::unique(qs.begin(), qs.end()), qs.end());
+        std::vector<int> cnt(qs.size(), 0);
+        for (int i = 0; i < D; ++i) {
+            const int s = (int)(std::lower_bound(qs.begin(), qs.end(), path[i][b]) - qs.begin());
+            if (b == 0) {
+                cnt[s] = 1;
+                pos[i][b] = 0;
+            } else if (b == K) {
+                cnt[s] = D;
+                pos[i][b] = i;
+            } else {
+                pos[i][b] = cnt[s]++;
+            }
+        }
+        L.bonds[b].q = qs;
+        L.bonds[b].dim = cnt;
+    }
+    L.rebuild_blocks();
+    values->assign((size_t)L.total(), 0.0);
+    int64_t base = 0;
+    for (int t = 0; t < K; ++t) {
+        for (int i = 0; i < D; ++i) {
+            const int li = L.bonds[t].find(path[i][t]);
+            const int bi = L.block_index(t, li, occ[(size_t)i * K + t]);
+            const Block& bk = L.blocks[t][bi];
+            (*values)[(size_t)(base + bk.off + (int64_t)pos[i][t] * bk.cols + pos[i][t + 1])] = 1.0;
+        }
+        base += L.core_size[t];
+    }
     return L;
 }
 

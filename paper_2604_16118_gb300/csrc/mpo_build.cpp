@@ -290,6 +290,7 @@ Mpo build_mpo(int n_orb, const double* h, const double* eri, int spin, int n_par
         }
     };
     const State sI{0, 0, 0}, sF{3, 0, 0};
+    W.ident_last = index[K - 1][sI];
     for (int t = 0; t + 1 < K; ++t) put(t, index[t][sI], index[t + 1][sI], kI, 1.0, false);
     for (int t = 1; t < K; ++t) put(t, index[t][sF], index[t + 1][sF], kI, 1.0, false);
     {

@@ -97,6 +97,18 @@ MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms) {
         BSM_REQUIRE(same_space(tm.x->lay, L0), BSMPS_ERR_INVALID_ARG,
                     "MPS of different sites or particle numbers");
     const int K = L0.K;
+    int D = -1;   // columns of the result
+    for (auto& tm : terms) {
+        const int din = tm.x->lay.columns();
+        int dout = din;
+        if (!tm.mix.empty()) {
+            BSM_REQUIRE(tm.mix_out > 0 && (int64_t)tm.mix.size() == (int64_t)din * tm.mix_out && K > 1,
+                        BSMPS_ERR_INVALID_ARG, "mixing matrix must be columns x mix_out (K > 1)");
+            dout = tm.mix_out;
+        }
+        BSM_REQUIRE(D < 0 || D == dout, BSMPS_ERR_INVALID_ARG, "terms with different column counts");
+        D = dout;
+    }
     Layout R;
     R.K = K;
     R.species = L0.species;
@@ -120,7 +132,7 @@ MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms) {
                 const int j = terms[i].x->lay.bonds[b].find(qs[s]);
                 if (j >= 0) acc += terms[i].x->lay.bonds[b].dim[j];
             }
-            R.bonds[b].dim[s] = (b == 0 || b == K) ? 1 : acc;
+            R.bonds[b].dim[s] = b == 0 ? 1 : (b == K ? D : acc);
         }
     }
     R.rebuild_blocks();
@@ -128,8 +140,13 @@ MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms) {
     std::vector<std::vector<CopyTask>> per_term(terms.size());
     std::vector<std::vector<int>> looks(K);
     for (int t = 0; t < K; ++t) looks[t] = block_lookup(R, t);
+    // mixed terms: their last-site blocks are products X_block W (one GEMM output each)
+    Scratch sm(ctx);
+    std::vector<GemmOut> gouts;
+    std::vector<GemmIn> gins;
     for (size_t i = 0; i < terms.size(); ++i) {
         const Mps* x = terms[i].x;
+        const double* dmix = terms[i].mix.empty() ? nullptr : sm.up(terms[i].mix);
         for (int t = 0; t < K; ++t) {
             const std::vector<int>& look = looks[t];
             for (const Block& bk : x->lay.blocks[t]) {
@@ -140,12 +157,18 @@ MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms) {
                 double f = 1.0;
                 const std::vector<double>& fv = bk.sigma ? terms[i].f1 : terms[i].f0;
                 if (!fv.empty()) f = fv[t];
-                CopyTask ct{x->core[t] + bk.off, y->core[t] + rb.off + (int64_t)r0 * rb.cols + c0,
-                            bk.rows, bk.cols, bk.cols, rb.cols, 0, 0, K == 1 ? 1 : 0, f};
+                double* dst = y->core[t] + rb.off + (int64_t)r0 * rb.cols + c0;
+                if (dmix && t == K - 1) {
+                    gouts.push_back({dst, bk.rows, rb.cols, rb.cols, (int)gins.size(), (int)gins.size() + 1, 0.0});
+                    gins.push_back({x->core[t] + bk.off, dmix, bk.cols, bk.cols, rb.cols, 0, f});
+                    continue;
+                }
+                CopyTask ct{x->core[t] + bk.off, dst, bk.rows, bk.cols, bk.cols, rb.cols, 0, 0, K == 1 ? 1 : 0, f};
                 per_term[i].push_back(ct);
             }
         }
     }
+    launch_gemm(ctx, gouts, gins);
     if (K == 1) {
         for (auto& v : per_term) launch_copy(ctx, v);   // same destination: one launch per term
     } else {
@@ -172,7 +195,8 @@ MpsPtr op_scale_sites(Context* ctx, const Mps* x, const std::vector<double>& f0,
 
 std::vector<MpsPtr> op_apply_exact_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
                                           const std::vector<std::vector<double>>& f0,
-                                          const std::vector<std::vector<double>>& f1) {
+                                          const std::vector<std::vector<double>>& f1,
+                                          const std::vector<double>* col_shift) {
     const Layout& X = x->lay;
     BSM_REQUIRE(W.K == X.K && W.species == X.species, BSMPS_ERR_INVALID_ARG,
                 "MPO and MPS act on different sites");
@@ -225,30 +249,52 @@ std::vector<MpsPtr> op_apply_exact_scaled(Context* ctx, const Mpo& W, const Mps*
     launch_zero(ctx, zp, zn);
     std::vector<CopyTask> tasks;
     double fl = 0.0;
+    const int ncol = X.columns();
+    if (col_shift) {
+        BSM_REQUIRE((int)col_shift->size() == ncol && W.ident_last >= 0 && W.bond_dim(K) == 1,
+                    BSMPS_ERR_INVALID_ARG, "one column shift per column and an MPO with an identity rail");
+    }
     for (int t = 0; t < K; ++t) {
         const std::vector<int> look = block_lookup(Y, t);
         const int wl = W.bond_dim(t), wr = W.bond_dim(t + 1);
         const auto& ents = W.entries[t];
-        for (const Block& bk : X.blocks[t])
-            for (int ei = 0; ei < (int)ents.size(); ++ei) {
-                const MpoEntry& e = ents[ei];
-                if (bk.sigma != e.si) continue;
-                const size_t il = (size_t)bk.li * wl + e.a, ir = (size_t)bk.ri * wr + e.b;
+        const bool rail = col_shift && t == K - 1;   // the (I -> F, s, s) sub-blocks get the column shifts
+        for (const Block& bk : X.blocks[t]) {
+            bool rail_done = false;
+            auto emit = [&](int so, int a, int b, double w, bool on_rail) {
+                const size_t il = (size_t)bk.li * wl + a, ir = (size_t)bk.ri * wr + b;
                 const int ml = ysec[t][il], mr = ysec[t + 1][ir];
-                if (ml < 0 || mr < 0) continue;
-                const int yb = look[ml * 2 + e.so];
-                if (yb < 0) continue;
+                if (ml < 0 || mr < 0) return;
+                const int yb = look[ml * 2 + so];
+                if (yb < 0) return;
                 const Block& yk = Y.blocks[t][yb];
-                double w = e.w;
-                if (t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1])) w += shift;
                 const int64_t dst = yk.off + (int64_t)yoff[t][il] * yk.cols + yoff[t + 1][ir];
                 for (int i = 0; i < n; ++i) {
                     const std::vector<double>& f = bk.sigma ? f1[i] : f0[i];
-                    tasks.push_back({x->core[t] + bk.off, ys[i]->core[t] + dst, bk.rows, bk.cols, bk.cols,
-                                     yk.cols, 0, 0, 0, f.empty() ? w : w * f[t]});
+                    const double fs = f.empty() ? 1.0 : f[t];
+                    if (!on_rail) {
+                        tasks.push_back({x->core[t] + bk.off, ys[i]->core[t] + dst, bk.rows, bk.cols, bk.cols,
+                                         yk.cols, 0, 0, 0, w * fs});
+                    } else {
+                        // one task per column j: weight (w + col_shift[j])
+                        for (int j = 0; j < bk.cols; ++j)
+                            tasks.push_back({x->core[t] + bk.off + j, ys[i]->core[t] + dst + j, bk.rows, 1,
+                                             bk.cols, yk.cols, 0, 0, 0, (w + (*col_shift)[j]) * fs});
+                    }
                 }
                 fl += 2.0 * n * bk.rows * bk.cols;
+            };
+            for (int ei = 0; ei < (int)ents.size(); ++ei) {
+                const MpoEntry& e = ents[ei];
+                if (bk.sigma != e.si) continue;
+                double w = e.w;
+                if (t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1])) w += shift;
+                const bool on_rail = rail && e.a == W.ident_last && e.b == 0 && e.so == e.si;
+                rail_done = rail_done || on_rail;
+                emit(e.so, e.a, e.b, w, on_rail);
             }
+            if (rail && !rail_done) emit(bk.sigma, W.ident_last, 0, 0.0, true);
+        }
     }
     ctx->flops += fl;
     launch_copy(ctx, tasks);
@@ -1308,9 +1354,13 @@ static std::vector<double> dot_batch_sitewise(Context* ctx, const std::vector<En
 // alpha X_a(ia, s_out)^T T, with alpha = w f_a f_b.  E lives in two ping-pong
 // buffers, T in one buffer; the structure of every site follows on the host
 // from the layouts.
-std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs) {
+// grams != nullptr: also return each problem's last environment, the Gram
+// matrix of the columns of a and b.
+static std::vector<double> dot_batch_impl(Context* ctx, const std::vector<EnvProblem>& probs,
+                                          std::vector<std::vector<double>>* grams) {
     const int P = (int)probs.size();
     std::vector<double> result(P, 0.0);
+    if (grams) grams->assign(P, {});
     if (P == 0) return result;
     const int K = probs[0].a->lay.K;
     for (int p = 0; p < P; ++p) {
@@ -1564,14 +1614,55 @@ std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& pr
         final_beg.push_back((int)finals.size());
     }
     if (!launch_env_sweep_t(ctx, outs, ins, tiles, phase_beg, gph, mfac, ftab, K, base, finals, final_beg, res,
-                            gs))
+                            gs)) {
+        BSM_REQUIRE(!grams, BSMPS_ERR_RANK_CAP, "Gram matrices need the persistent environment sweep");
         return dot_batch_sitewise(ctx, probs);
+    }
+    // Gram matrices: gather every problem's last environment block (one per
+    // problem: bond K has one sector and one channel) into one buffer
+    std::vector<double> gh;
+    double* gd = nullptr;
+    std::vector<int64_t> goff(P + 1, 0);
+    if (grams) {
+        std::vector<CopyTask> gt;
+        for (int p = 0; p < P; ++p) {
+            const int g = group_of[p];
+            const int da = probs[p].a->lay.columns(), db = probs[p].b->lay.columns();
+            goff[p + 1] = goff[p] + (int64_t)da * db;
+            BSM_REQUIRE(E[g].size() <= 1, BSMPS_ERR_INVALID_ARG, "more than one environment block at bond K");
+            for (const EBlk& eb : E[g]) {
+                BSM_REQUIRE(eb.rows == da && eb.cols == db, BSMPS_ERR_INVALID_ARG, "Gram block shape");
+                gt.push_back({base[fid] + E_base[g] + (int64_t)member_index[p] * E_size[g] + eb.off, nullptr, da, db,
+                              db, db, 0, 0, 0, 1.0});
+            }
+        }
+        gd = s.dbl((size_t)std::max<int64_t>(goff[P], 1));
+        BSM_CUDA(cudaMemsetAsync(gd, 0, sizeof(double) * std::max<int64_t>(goff[P], 1), ctx->stream));
+        size_t k = 0;
+        for (int p = 0; p < P; ++p)
+            if (!E[group_of[p]].empty()) gt[k++].dst = gd + goff[p];
+        launch_copy(ctx, gt);
+        gh.assign((size_t)std::max<int64_t>(goff[P], 1), 0.0);
+        BSM_CUDA(cudaMemcpyAsync(gh.data(), gd, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    }
     GridSync h;
     BSM_CUDA(cudaMemcpyAsync(result.data(), res, sizeof(double) * P, cudaMemcpyDeviceToHost, ctx->stream));
     BSM_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     ctx->sync();
     BSM_REQUIRE(h.err == 0, BSMPS_ERR_TIMEOUT, "inner-product sweep: a grid-wide wait gave up");
+    if (grams)
+        for (int p = 0; p < P; ++p) (*grams)[p].assign(gh.begin() + goff[p], gh.begin() + goff[p + 1]);
     return result;
+}
+
+std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs) {
+    return dot_batch_impl(ctx, probs, nullptr);
+}
+
+std::vector<std::vector<double>> op_gram_batch(Context* ctx, const std::vector<EnvProblem>& probs) {
+    std::vector<std::vector<double>> g;
+    dot_batch_impl(ctx, probs, &g);
+    return g;
 }
 
 double op_core0_norm(Context* ctx, const Mps* x) {

@@ -18,10 +18,15 @@ void mps_download(const Mps* x, double* host_flat);
 struct ConcatTerm {
     const Mps* x;
     std::vector<double> f0, f1;
+    // optional column mixing x W of a joint block MPS (Sec. 6.1): W is
+    // columns(x) x mix_out, row-major; empty: no mixing
+    std::vector<double> mix = {};
+    int mix_out = 0;
 };
 
 // sum_i term_i by block concatenation (Sec. 2.3): union of sectors, inner
 // bonds stacked in term order, first core side by side, last core stacked.
+// The last bond keeps the common column count of the (mixed) terms.
 MpsPtr op_concat(Context* ctx, const std::vector<ConcatTerm>& terms);
 MpsPtr op_scale_sites(Context* ctx, const Mps* x, const std::vector<double>& f0,
                       const std::vector<double>& f1);
@@ -31,9 +36,12 @@ MpsPtr op_apply_exact(Context* ctx, const Mpo& W, const Mps* x, double shift);
 
 // y_i = (H_gamma + shift I) S_i x for site scalings S_i = (f0[i], f1[i]) as in
 // ConcatTerm: one layout, one zeroing launch and one copy launch for all i.
+// col_shift (joint block MPS, length columns(x)): y_i also gets
+// S_i X diag(col_shift), entered on the MPO's identity rail at the last site.
 std::vector<MpsPtr> op_apply_exact_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
                                           const std::vector<std::vector<double>>& f0,
-                                          const std::vector<std::vector<double>>& f1);
+                                          const std::vector<std::vector<double>>& f1,
+                                          const std::vector<double>* col_shift = nullptr);
 
 // trunc_eps with rank cap (Sec. 2.2); discarded norms are returned.
 MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
@@ -65,6 +73,9 @@ struct EnvProblem {
     const std::vector<double>* fb1 = nullptr;
 };
 std::vector<double> op_dot_batch(Context* ctx, const std::vector<EnvProblem>& probs);
+// The Gram matrices <S_a a_i, O S_b b_j> (columns(a) x columns(b), row-major)
+// of joint block MPS, one per problem (Sec. 6.1).
+std::vector<std::vector<double>> op_gram_batch(Context* ctx, const std::vector<EnvProblem>& probs);
 
 // <a, O b> with every temporary in a fixed file-scope device array (no allocation).
 double op_dot_noalloc(Context* ctx, const Mps* a, const Mps* b, const Mpo* W, double shift);

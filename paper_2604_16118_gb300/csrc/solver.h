@@ -26,6 +26,12 @@ void rr2(const double H[2][2], const double E[2][2], double* mu, double v[2]);
 double delta_A(double rho, double q);
 MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
                        bsmps_solver_state& st, const Mps* x, bsmps_step_info& info);
+// Gram-matrix pair sums of joint block MPS (row-major columns(a) x columns(b)).
+std::vector<std::vector<double>> gram_pair_sums(
+    Context* ctx, const PrecondTerms& P, const std::vector<std::tuple<const Mps*, const Mps*, const Mpo*>>& jobs);
+// Alg. 4, one step on a joint iterate.
+MpsPtr eigensolve_joint_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
+                             bsmps_solver_state& st, const Mps* X, bsmps_joint_step_info& info);
 // Alg. 3; records: one per outer step taken.
 MpsPtr eigensolve_outer(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
                         double alpha, double tau, int max_outer, int max_inner, const Mps* y0,

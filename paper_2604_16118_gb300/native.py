@@ -62,6 +62,27 @@ class OuterRecord(C.Structure):
         return d
 
 
+MAX_COLUMNS = 16
+
+
+class JointStepInfo(C.Structure):
+    _fields_ = [("D", C.c_int), ("lambda_", C.c_double * MAX_COLUMNS), ("rho", C.c_double * MAX_COLUMNS),
+                ("res_norm", C.c_double * MAX_COLUMNS), ("lambda_star", C.c_double * MAX_COLUMNS),
+                ("delta_A", C.c_double * MAX_COLUMNS), ("eta_res", C.c_double), ("eta_tries", C.c_int),
+                ("bound", C.c_double), ("releig_bound", C.c_double), ("eta_in", C.c_double),
+                ("converged", C.c_int), ("max_rank", C.c_int), ("flops", C.c_double),
+                ("cap_discarded", C.c_double)]
+
+    def as_dict(self):
+        D = self.D
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = np.array(v[:D]) if isinstance(v, C.Array) else v
+        d["lambda"] = d.pop("lambda_")
+        return d
+
+
 _vp = C.c_void_p
 _i = C.c_int
 _d = C.c_double
@@ -115,6 +136,15 @@ _SIGS = {
     "bsmps_mlp_destroy": (_i, [_vp]),
     "bsmps_eigensolve_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
                                    C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(StepInfo)]),
+    "bsmps_mps_joint_random_size": (_i, [_i, _i, _i, _i, _i, _i, _pi64]),
+    "bsmps_mps_create_joint": (_i, [_vp, _i, _i, _i, _i, _i, _i, C.POINTER(C.c_ubyte), _i, _pd, _i64,
+                                    C.POINTER(_vp)]),
+    "bsmps_mps_num_columns": (_i, [_vp, _pi]),
+    "bsmps_gram": (_i, [_vp, _vp, _vp, _vp, _d, _pd]),
+    "bsmps_apply_columns": (_i, [_vp, _vp, _vp, _d, _pd, C.POINTER(_vp)]),
+    "bsmps_mix_columns": (_i, [_vp, _vp, _pd, _i, C.POINTER(_vp)]),
+    "bsmps_eigensolve_joint_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
+                                         C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(JointStepInfo)]),
 }
 
 DECLARED = tuple(_SIGS.keys())
@@ -425,6 +455,68 @@ def eigensolve_outer(ctx, mpo, p, params, x, tau, alpha=1.0, max_outer=20, max_i
                                              max_inner, C.byref(h), recs, C.byref(n), C.byref(ok)))
     x.h = None          # destroyed by the library
     return MPS(ctx, h), [recs[i].as_dict() for i in range(n.value)], bool(ok.value)
+
+
+def mps_joint_random_size(n_orb, spin, n_up, n_dn, r_max, D):
+    n = C.c_int64()
+    _check(None, lib().bsmps_mps_joint_random_size(n_orb, spin, n_up, n_dn, r_max, D, C.byref(n)))
+    return n.value
+
+
+def mps_create_joint(ctx, n_orb, spin, n_up, n_dn, D, occ=None, r_max=1, values=None):
+    """Joint block MPS of D columns: the unit vectors of the occupation strings
+    occ (D x K of 0/1) when given, else the random-rule iterate filled from values."""
+    h = _vp()
+    if occ is not None:
+        o = np.ascontiguousarray(occ, dtype=np.uint8)
+        assert o.shape[0] == D
+        _check(ctx, lib().bsmps_mps_create_joint(ctx.h, n_orb, spin, n_up, n_dn, D, 0,
+                                                  o.ctypes.data_as(C.POINTER(C.c_ubyte)), 0, None, 0, C.byref(h)))
+    else:
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        _check(ctx, lib().bsmps_mps_create_joint(ctx.h, n_orb, spin, n_up, n_dn, D, 1, None, r_max, _dptr(v),
+                                                  len(v), C.byref(h)))
+    return MPS(ctx, h)
+
+
+def num_columns(x):
+    d = C.c_int()
+    _check(None, lib().bsmps_mps_num_columns(x.h, C.byref(d)))
+    return d.value
+
+
+def gram(ctx, a, b, mpo=None, shift=0.0):
+    """The columns(a) x columns(b) matrix <a_i, O b_j>."""
+    out = np.zeros((num_columns(a), num_columns(b)))
+    _check(ctx, lib().bsmps_gram(ctx.h, a.h, b.h, mpo.h if mpo is not None else None, shift, _dptr(out)))
+    return out
+
+
+def apply_columns(ctx, mpo, x, col_shift, shift=0.0):
+    """Exact (H_gamma + shift) X + X diag(col_shift)."""
+    cs = np.ascontiguousarray(col_shift, dtype=np.float64)
+    y = _vp()
+    _check(ctx, lib().bsmps_apply_columns(ctx.h, mpo.h, x.h, shift, _dptr(cs), C.byref(y)))
+    return MPS(ctx, y)
+
+
+def mix_columns(ctx, x, Wm):
+    """X Wm (Wm: columns(x) x D_out)."""
+    w = np.ascontiguousarray(Wm, dtype=np.float64)
+    y = _vp()
+    _check(ctx, lib().bsmps_mix_columns(ctx.h, x.h, _dptr(w), w.shape[1], C.byref(y)))
+    return MPS(ctx, y)
+
+
+def eigensolve_joint_step(ctx, mpo, p, params, state, x):
+    """One Alg. 4 step on a joint iterate; returns (X_next, info dict).  x's handle is consumed."""
+    h = _vp(x.h.value)
+    info = JointStepInfo()
+    code = lib().bsmps_eigensolve_joint_step(ctx.h, mpo.h, C.byref(p), C.byref(params), C.byref(state),
+                                             C.byref(h), C.byref(info))
+    _check(ctx, code)
+    x.h = None          # destroyed by the library
+    return MPS(ctx, h), info.as_dict()
 
 
 def _fptr(a):

@@ -14,6 +14,9 @@ preconditioner and the bounds of its spectrum (host-side scalars).
   (the spectrum of D on the N-particle space).
 """
 
+import itertools
+import math
+
 import numpy as np
 
 
@@ -88,3 +91,39 @@ def spectrum_bounds(theta, spin, n_up, n_dn, h=None):
         lo += float(np.sum(vals[:n]))
         hi += float(np.sum(vals[-n:]))
     return lo, hi
+
+
+def lowest_determinants(t_diag, spin, n_up, n_dn, D, max_configs=2_000_000):
+    """Occupation strings (D x K, uint8) of the D determinants with the smallest
+    diagonal one-particle energy sum_{i occupied} t_diag[i], the start of the
+    subspace iteration (Sec. 7.1.4 uses e_1, ..., e_D).  Ties: occupation strings
+    compared from site 0, occupied first (so the first string is e_1 when t_diag
+    increases).  Energies are summed over the occupied sites in site order.
+    The sector is enumerated: at most max_configs strings."""
+    t_diag = [float(v) for v in t_diag]
+    K = len(t_diag)
+    species = [(i % 2) if spin else 0 for i in range(K)]
+    want = [n_up, n_dn if spin else 0]
+    pools = [[i for i in range(K) if species[i] == s] for s in (0, 1)]
+    total = 1
+    for s in (0, 1):
+        total *= math.comb(len(pools[s]), want[s])
+    if total > max_configs:
+        raise ValueError(f"sector of {total} determinants is too large to enumerate")
+    if total < D:
+        raise ValueError("sector smaller than D")
+    rows = []
+    for a in itertools.combinations(pools[0], want[0]):
+        for b in itertools.combinations(pools[1], want[1]):
+            occ = bytearray(K)
+            for i in a:
+                occ[i] = 1
+            for i in b:
+                occ[i] = 1
+            e = 0.0
+            for i in range(K):
+                if occ[i]:
+                    e += t_diag[i]
+            rows.append((e, bytes(1 - o for o in occ), bytes(occ)))
+    rows.sort()
+    return np.array([list(r[2]) for r in rows[:D]], dtype=np.uint8)
