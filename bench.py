@@ -218,6 +218,158 @@ def run_reference(args):
     return 0
 
 
+JOINT_WORKLOAD = ("coulomb_1d K=14 N=4 gamma=4 (the simultaneous-eigenvalue experiment of Sec. 7.2), D=4, "
+                  "Alg. 4 on a joint block MPS from the 4 lowest determinants, FP64")
+
+
+def setup_joint(ctx, nat):
+    from paper_2604_16118_gb300 import problem
+    from synth import coulomb_1d
+    with open(os.path.join(ROOT, "tests", "golden", "bench_params_coulomb14_D4.json")) as f:
+        prm = json.load(f)
+    K, N, gamma, D = 14, 4, 4.0, 4
+    wl = coulomb_1d(K=K, N=N, n_grid=8192)
+    th = problem.theta_diagonal(wl.h, wl.eri, 0, N, gamma)
+    tmin, tmax = problem.spectrum_bounds(th, 0, N, 0, h=wl.h)
+    W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, 0, N, gamma)
+    p = nat.make_precond(th, tmin, tmax, prm["c0"], prm["alpha0"])
+    sp = nat.solver_params(prm["c"], prm["delta"], eps_num=prm["eps_num"], t_eig=prm["t_eig"], tau=1e-10)
+    occ = problem.lowest_determinants(np.diag(wl.h), 0, N, 0, D)
+    x = nat.mps_create_joint(ctx, K, 0, N, 0, D, occ=occ)
+    return dict(wl=wl, W=W, p=p, sp=sp, x=x, gamma=gamma, prm=prm, K=K, N=N, D=D, occ=occ)
+
+
+def oracle_joint_step0():
+    """The oracle's first Alg. 4 step of the joint workload (wall seconds, Ritz values)."""
+    from oracle import fermion as OF
+    from oracle import joint as OJ
+    from oracle import mpo as OM
+    from oracle import pinvit as OPI
+    from oracle import precond as OP
+    from synth import coulomb_1d
+    with open(os.path.join(ROOT, "tests", "golden", "bench_params_coulomb14_D4.json")) as f:
+        prm = json.load(f)
+    K, N, gamma, D = 14, 4, 4.0, 4
+    wl = coulomb_1d(K=K, N=N, n_grid=8192)
+    t_so, v_so = OP.spin_orbital_accessors(wl.h, wl.eri, 0)
+    th = OP.theta_diag(t_so, v_so, N, gamma, K)
+    species = OF.site_species(K, 0)
+    tmin, tmax = OP.spectrum_bounds(th, species, (N, 0), t_diag=np.diag(wl.h))
+    prec = OP.Preconditioner(th, tmin, tmax, prm["c0"], prm["alpha0"])
+    W = OM.build_mpo(wl.h, wl.eri, 0, N, gamma)
+    params = OPI.SolverParams(prm["c"], prm["delta"], eps_num=prm["eps_num"], t_eig=prm["t_eig"], tau=1e-10)
+    x = OJ.from_determinants(species, (N, 0), OJ.lowest_determinants(species, (N, 0), np.diag(wl.h), D))
+    t0 = time.perf_counter()
+    x, info = OJ.step(x, W, prec, params, OPI.SolverState())
+    return time.perf_counter() - t0, info["lambda"]
+
+
+def main_joint(args):
+    """Alg. 4 steps of the joint workload: W untimed, K timed (device events,
+    L2 flushed between steps); step 0 is timed separately against the oracle."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_16118_gb300 import build
+    build.build()
+    from paper_2604_16118_gb300 import native as nat
+    stream = torch.cuda.Stream(device=dev)
+    ctx = nat.Context(local, stream.cuda_stream)
+    S = setup_joint(ctx, nat)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = nat.solver_state()
+    x = S["x"]
+
+    def timed(xx):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xx, info = nat.eigensolve_joint_step(ctx, S["W"], S["p"], S["sp"], st, xx)
+        e1.record(stream)
+        e1.synchronize()
+        return xx, info, e0.elapsed_time(e1)
+
+    x, info0, ms0 = timed(x)                      # step 0 (compared with the oracle below)
+    for _ in range(max(args.warmup - 1, 0)):
+        x, _ = nat.eigensolve_joint_step(ctx, S["W"], S["p"], S["sp"], st, x)
+    ctx.sync()
+    x_after_warmup = (x.export(), x.bonds(), st.eta_res, st.n)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    total_ms, total_flops, infos = 0.0, 0.0, []
+    for _ in range(args.steps):
+        x, info, ms = timed(x)
+        total_ms += ms
+        total_flops += info["flops"]
+        infos.append(info)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    clocks = sampler.stop()
+    ctx.profile(True)
+    x, _ = nat.eigensolve_joint_step(ctx, S["W"], S["p"], S["sp"], st, x)
+    stats = ctx.kernel_stats(reset=True)
+    ctx.profile(False)
+    name, (nl, kms, kfl, kby) = max(stats.items(), key=lambda kv: kv[1][1])
+    # end to end through the C ABI with host buffers, from the post-warm-up iterate
+    hx, bonds, st.eta_res, st.n = x_after_warmup
+    pinned = torch.empty(len(hx), dtype=torch.float64).pin_memory()
+    pinned.numpy()[:] = hx
+    h2d = d2h = 0
+    e2e_flops = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xd = nat.mps_import(ctx, S["K"], 0, S["N"], 0, bonds, pinned.numpy())
+        h2d += 8 * len(pinned)
+        xd, info = nat.eigensolve_joint_step(ctx, S["W"], S["p"], S["sp"], st, xd)
+        e2e_flops += info["flops"]
+        out = xd.export()
+        d2h += 8 * len(out)
+        bonds = xd.bonds()
+        pinned = torch.from_numpy(out).pin_memory()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    fp64 = fp64_gemm_peak(torch, dev)
+    lam_exact = S["prm"]["lambda_exact"][:S["D"]]
+    last = infos[-1] if infos else info0
+    out = {
+        "metric": "Alg. 4 step, algorithmic FP64 TFLOP/s", "value": total_flops / (total_ms * 1e-3) / 1e12,
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": JOINT_WORKLOAD, "step": "one Alg. 4 step",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "single"},
+        "gpu_launches": launches, "clocks": clocks,
+        "e2e": {"value": e2e_flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d // max(args.steps, 1),
+                "d2h_bytes_per_step": d2h // max(args.steps, 1), "steps": args.steps},
+        "roofline": {"bound": "alu", "kernel": name, "achieved": (kfl / (kms * 1e-3) / 1e12) if kms else None,
+                     "peak": fp64, "unit": "TFLOP/s", "frac": (kfl / (kms * 1e-3) / 1e12 / fp64) if kms else None,
+                     "traffic": None, "peak_source": "cuBLAS FP64 GEMM 4096^3 measured in this run",
+                     "launches": nl, "kernel_ms": kms},
+        "kernels": {k: {"launches": v[0], "ms": v[1], "flops": v[2], "bytes": v[3]} for k, v in stats.items()},
+        "steps_info": [{"lambda": [float(v) for v in i["lambda"]], "rho1": float(i["rho"][0]),
+                        "eta_tries": i["eta_tries"], "max_rank": i["max_rank"], "flops": i["flops"]}
+                       for i in [info0] + infos],
+        "lambda_exact": lam_exact,
+        "step0_ms": ms0,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        t_or, lam_or = oracle_joint_step0()
+        out["cpu_baseline"] = {"value": info0["flops"] / t_or / 1e12, "unit": "TFLOP/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"step 0 of the same trajectory ({t_or:.1f} s; numpy FP64 oracle, "
+                                         f"BLAS on 1 thread); the GPU's step 0 took {ms0:.1f} ms",
+                               "lambda_match": float(np.max(np.abs(np.asarray(lam_or) - info0["lambda"])))}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,7 +377,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="hubbard", choices=["hubbard", "coulomb14_alg4_D4"],
+                    help="hubbard: the Alg. 2 workload of the JSON contract; coulomb14_alg4_D4: Alg. 4 (D = 4)")
     args = ap.parse_args()
+    if args.workload == "coulomb14_alg4_D4":
+        return main_joint(args)
     if args.impl == "reference":
         return run_reference(args)
 
