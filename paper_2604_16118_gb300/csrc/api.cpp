@@ -227,6 +227,8 @@ bsmps_status bsmps_ctx_destroy(bsmps_ctx ctx) {
         ctx->c.release_ring();
         ctx->c.release_cache();
         ctx->c.sync();
+        if (ctx->c.dev_err) cudaFree(ctx->c.dev_err);
+        ctx->c.dev_err = nullptr;
     });
     delete ctx;
     return s;

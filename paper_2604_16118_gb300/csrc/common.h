@@ -168,9 +168,30 @@ struct Context {
         if (v.empty()) return nullptr;
         return (T*)upload_raw(v.data(), v.size() * sizeof(T));
     }
+    // Device error word of bounded grid-wide waits in kernels whose results the
+    // host does not read back at once; checked (and cleared) by sync().
+    int* dev_err = nullptr;
+    bool dev_err_armed = false;
+    int* err_word() {
+        if (!dev_err) {
+            BSM_CUDA(cudaMalloc(&dev_err, sizeof(int)));
+            BSM_CUDA(cudaMemsetAsync(dev_err, 0, sizeof(int), stream));
+        }
+        dev_err_armed = true;
+        return dev_err;
+    }
     void sync() {
         BSM_CUDA(cudaStreamSynchronize(stream));
         half_pending[0] = half_pending[1] = false;   // every staged copy has completed
+        if (dev_err_armed) {
+            dev_err_armed = false;
+            int h = 0;
+            BSM_CUDA(cudaMemcpy(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (h) {
+                BSM_CUDA(cudaMemset(dev_err, 0, sizeof(int)));
+                throw Error(BSMPS_ERR_TIMEOUT, "a grid-wide wait of a factorisation gave up");
+            }
+        }
     }
 };
 

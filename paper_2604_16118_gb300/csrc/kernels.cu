@@ -172,13 +172,6 @@ constexpr int kSmemJacobiMax = 110;   // 2 k^2 doubles <= 193 KB of shared memor
 
 // One-sided Jacobi task on a k x k matrix G (column-major, overwritten by the
 // rotated columns) with the accumulated rotations in V (column-major).
-struct JacTask {
-    double* G;
-    double* V;
-    double* Sraw;    // column norms of the rotated G (unsorted)
-    int k;
-    int smem;        // 1: iterate in shared memory
-};
 
 // One-sided Jacobi (dev::jacobi), one CTA per matrix, in shared memory when k <= kSmemJacobiMax.
 __global__ void __launch_bounds__(kThreads) k_jacobi(const JacTask* __restrict__ tasks) {
@@ -478,7 +471,9 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
             k_jacobi<<<(unsigned)small.size(), kThreads, smem, ctx->stream>>>(d);
             check_launch(ctx);
         }
-        if (!large.empty()) {
+        // matrices too large for shared memory: one-sided Jacobi across the grid
+        // (one CTA per matrix when the cooperative launch cannot be resident)
+        if (!large.empty() && !launch_jacobi_grid(ctx, large)) {
             JacTask* d = s.up(large);
             k_jacobi<<<(unsigned)large.size(), kThreads, 0, ctx->stream>>>(d);
             check_launch(ctx);

@@ -64,6 +64,24 @@ struct SvdTask {
     int wide;
 };
 
+// One-sided Jacobi of the k x k matrix G (column-major, destroyed): V (k x k,
+// column-major) accumulates the rotations, Sraw receives the column norms of
+// the rotated G (unsorted).
+struct JacTask {
+    double* G;
+    double* V;
+    double* Sraw;
+    int k;
+    int smem;        // 1: iterate in shared memory (one CTA per matrix)
+};
+
+// Jacobi of several large matrices in one cooperative launch: the disjoint
+// column pairs of every round are spread over all warps of the grid, rounds are
+// separated by bounded grid-wide waits (a timeout sets the context's device
+// error word, raised at the next sync).  Returns false when no grid can be
+// resident (the caller then runs one CTA per matrix).
+bool launch_jacobi_grid(Context* ctx, const std::vector<JacTask>& tasks);
+
 void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks);
 // Sets n[i] doubles at ptr[i] to zero, all regions in one launch.
 void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n);

@@ -13,6 +13,7 @@ namespace bsm {
 namespace {
 
 using dev::kThreads;
+constexpr int kSweepThreads = 512;   // block size limit of the kernels sized by block_for()
 using dev::kWarps;
 using dev::nthreads;
 using dev::nwarps;
@@ -161,7 +162,7 @@ __device__ void left_body(const LeftTask& tk, const LeftSrc* __restrict__ srcs, 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kSweepThreads) k_left_site(const LeftTask* __restrict__ tasks,
                                                         const LeftSrc* __restrict__ srcs,
                                                         const LeftX* __restrict__ xs) {
     extern __shared__ double sm[];
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_left_site(const LeftTask* __restri
     left_body<false>(tasks[blockIdx.x], srcs, xs, sm, red, sh);
 }
 
-__global__ void __launch_bounds__(kThreads) k_svd_site(const SvdSiteTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kSweepThreads) k_svd_site(const SvdSiteTask* __restrict__ tasks,
                                                        const SvdPart* __restrict__ parts) {
     extern __shared__ double sm[];
     __shared__ double red[33];
@@ -399,7 +400,7 @@ __device__ void right_body(const DynTask& tk, double* sm, double* red,
     if (threadIdx.x == 0) *tk.kact = k;
 }
 
-__global__ void __launch_bounds__(kThreads) k_right_dyn(const DynTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(kSweepThreads) k_right_dyn(const DynTask* __restrict__ tasks) {
     extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ double sh[2];
@@ -558,7 +559,7 @@ __device__ bool phase_end(GridSync* gs, unsigned int p, int* s_flag) {
     return *s_flag == 2;
 }
 
-__global__ void __launch_bounds__(kThreads) k_left_sweep(const LeftTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kSweepThreads) k_left_sweep(const LeftTask* __restrict__ tasks,
                                                          const LeftSrc* __restrict__ srcs,
                                                          const LeftX* __restrict__ xs,
                                                          const int* __restrict__ phase_beg, int n_phase,
@@ -587,7 +588,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // phase_beg (n_phase + 1 ints) is staged in shared memory behind the body's
 // working set (offset pb_off bytes); the descriptor of a CTA's first task of
 // phase p + 1 is copied asynchronously while phase p runs.
-__global__ void __launch_bounds__(kThreads) k_right_sweep(const DynTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kSweepThreads) k_right_sweep(const DynTask* __restrict__ tasks,
                                                           const int* __restrict__ phase_beg,
                                                           const CutTask* __restrict__ cuts,
                                                           const CutSector* __restrict__ secs, int n_phase,
@@ -668,7 +669,12 @@ unsigned char* upload_pack(Scratch& s, const Pack& p) {
 }
 
 // Warps per CTA: one per Jacobi pair of the largest problem, between 1 and 8.
-int block_for(int kmax) { return 32 * std::max(1, std::min(8, (kmax + 1) / 2)); }
+// One warp per column pair of a Jacobi round (k/2 pairs), at most max_warps
+// (<= kSweepThreads / 32; the block argmax keeps 16 keys in red[]).  The SVD
+// kernels take up to 16 warps; the QR kernels keep 8, where more warps only
+// lengthen the barriers between reflectors.
+int block_for(int kmax, int max_warps = 8) { return 32 * std::max(1, std::min(max_warps, (kmax + 1) / 2)); }
+constexpr int kSvdWarps = kSweepThreads / 32;
 
 // The attributes are per function and per process: set them once per kernel.
 template <class F>
@@ -782,6 +788,151 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_sweep_t(const EnvOutT* __re
         }
 }
 
+
+// ---- one-sided Jacobi of large matrices across the grid ----
+//
+// The cyclic round-robin ordering of dev::jacobi rotates, in every round, k/2
+// disjoint column pairs of a matrix.  Here the pairs of all unfinished
+// matrices of a round are spread over every warp of the grid (one pair per
+// warp at a time), and a grid-wide phase ends each round: columns are disjoint
+// within a round, so nothing else needs ordering.  Same rotation formula and
+// stopping rules as dev::jacobi; G and V live in global memory and are read
+// through L2 (other SMs wrote them in earlier rounds).  A sweep without a
+// rotation finishes a matrix; the flags of a sweep are read after its last
+// round by every CTA, so all CTAs take the same decisions and run the same
+// number of phases.
+constexpr int kJacGridMaxTasks = 64;
+
+__device__ __forceinline__ void jg_locate(const JacTask* tasks, int n_tasks, const unsigned char* done, int round,
+                                          int u, int* t_out, int* pi_out) {
+    int base = 0;
+    for (int t = 0; t < n_tasks; ++t) {
+        const int k = tasks[t].k, n2 = k + (k & 1);
+        if (done[t] || round >= n2 - 1) continue;
+        if (u < base + n2 / 2) {
+            *t_out = t;
+            *pi_out = u - base;
+            return;
+        }
+        base += n2 / 2;
+    }
+    *t_out = -1;
+}
+
+__global__ void __launch_bounds__(kThreads) k_jacobi_grid(const JacTask* __restrict__ tasks, int n_tasks,
+                                                          double* __restrict__ fro, int* __restrict__ rot_flags,
+                                                          GridSync* gs, int* dev_err) {
+    __shared__ int s_flag;
+    __shared__ unsigned char s_done[kJacGridMaxTasks];
+    const int lane = threadIdx.x & 31;
+    const int wpb = kThreads / 32;
+    const int gwarp = (int)blockIdx.x * wpb + (int)(threadIdx.x >> 5);
+    const int nwarp = (int)gridDim.x * wpb;
+    unsigned int ph = 0;
+    // V = I and ||G||_F^2 of every matrix
+    for (int t = 0; t < n_tasks; ++t) {
+        const int k = tasks[t].k;
+        const int64_t kk = (int64_t)k * k;
+        double f = 0.0;
+        for (int64_t e = (int64_t)gwarp * 32 + lane; e < kk; e += (int64_t)nwarp * 32) {
+            const double v = tasks[t].G[e];
+            f += v * v;
+            tasks[t].V[e] = (e % k) == (e / k) ? 1.0 : 0.0;
+        }
+        f = dev::warp_sum(f);
+        if (lane == 0 && f != 0.0) atomicAdd(&fro[t], f);
+    }
+    if ((int)threadIdx.x < n_tasks) s_done[threadIdx.x] = tasks[threadIdx.x].k <= 1;
+    if (!phase_end(gs, ph++, &s_flag)) {
+        if (threadIdx.x == 0) atomicOr(dev_err, 1);
+        return;
+    }
+    int n2max = 0, total_cols = 0;
+    for (int t = 0; t < n_tasks; ++t) {
+        n2max = max(n2max, tasks[t].k + (tasks[t].k & 1));
+        total_cols += tasks[t].k;
+    }
+    for (int sweep = 0; sweep < dev::kMaxSweeps; ++sweep) {
+        for (int round = 0; round < n2max - 1; ++round) {
+            int U = 0;
+            for (int t = 0; t < n_tasks; ++t) {
+                const int n2 = tasks[t].k + (tasks[t].k & 1);
+                if (!s_done[t] && round < n2 - 1) U += n2 / 2;
+            }
+            for (int u = gwarp; u < U; u += nwarp) {
+                int t, pi;
+                jg_locate(tasks, n_tasks, s_done, round, u, &t, &pi);
+                if (t < 0) continue;
+                const int k = tasks[t].k, n2 = k + (k & 1);
+                int p = dev::rr_player(pi, round, n2), q = dev::rr_player(n2 - 1 - pi, round, n2);
+                if (p >= k || q >= k) continue;
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+                double* Gp = tasks[t].G + (int64_t)p * k;
+                double* Gq = tasks[t].G + (int64_t)q * k;
+                double a = 0.0, b = 0.0, g = 0.0;
+                for (int i = lane; i < k; i += 32) {
+                    const double xp = __ldcg(Gp + i), xq = __ldcg(Gq + i);
+                    a += xp * xp;
+                    b += xq * xq;
+                    g += xp * xq;
+                }
+                a = dev::warp_sum(a);
+                b = dev::warp_sum(b);
+                g = dev::warp_sum(g);
+                const double tol = (double)k * DBL_EPSILON;
+                const double tiny2 = tol * tol * __ldcg(&fro[t]);
+                if (g != 0.0 && fabs(g) > tol * sqrt(a * b) && fmin(a, b) > tiny2) {
+                    const double zeta = (b - a) / (2.0 * g);
+                    const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+                    double* Vp = tasks[t].V + (int64_t)p * k;
+                    double* Vq = tasks[t].V + (int64_t)q * k;
+                    for (int i = lane; i < k; i += 32) {
+                        const double xp = __ldcg(Gp + i), xq = __ldcg(Gq + i);
+                        Gp[i] = c * xp - sn * xq;
+                        Gq[i] = sn * xp + c * xq;
+                        const double vp = __ldcg(Vp + i), vq = __ldcg(Vq + i);
+                        Vp[i] = c * vp - sn * vq;
+                        Vq[i] = sn * vp + c * vq;
+                    }
+                    if (lane == 0) rot_flags[t * dev::kMaxSweeps + sweep] = 1;
+                }
+            }
+            if (!phase_end(gs, ph++, &s_flag)) {
+                if (threadIdx.x == 0) atomicOr(dev_err, 1);
+                return;
+            }
+        }
+        if ((int)threadIdx.x < n_tasks && !s_done[threadIdx.x])
+            s_done[threadIdx.x] = __ldcg(&rot_flags[threadIdx.x * dev::kMaxSweeps + sweep]) == 0;
+        __syncthreads();
+        bool all = true;
+        for (int t = 0; t < n_tasks; ++t) all = all && s_done[t];
+        if (all) break;
+    }
+    // column norms of the rotated G
+    for (int u = gwarp; u < total_cols; u += nwarp) {
+        int t = 0, base = 0;
+        while (u >= base + tasks[t].k) {
+            base += tasks[t].k;
+            ++t;
+        }
+        const int k = tasks[t].k, j = u - base;
+        const double* Gj = tasks[t].G + (int64_t)j * k;
+        double a = 0.0;
+        for (int i = lane; i < k; i += 32) {
+            const double x = __ldcg(Gj + i);
+            a += x * x;
+        }
+        a = dev::warp_sum(a);
+        if (lane == 0) tasks[t].Sraw[j] = sqrt(a);
+    }
+}
+
 }  // namespace
 
 bool left_site_fits(int M, int N, int64_t rx_fma) { return left_smem(M, N) <= kSweepSmem && rx_fma <= kFusedGemmMaxFma; }
@@ -843,7 +994,7 @@ void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const 
     allow_smem(k_svd_site);
     int kmax = 1;
     for (const SvdSiteTask& t : tasks) kmax = std::max(kmax, t.k);
-    k_svd_site<<<(unsigned)tasks.size(), block_for(kmax), smem, ctx->stream>>>((const SvdSiteTask*)(d + ot),
+    k_svd_site<<<(unsigned)tasks.size(), block_for(kmax, kSvdWarps), smem, ctx->stream>>>((const SvdSiteTask*)(d + ot),
                                                                        (const SvdPart*)(d + op));
     count_launch(ctx);
     pr.done();
@@ -905,7 +1056,7 @@ int launch_right_dyn(Context* ctx, const std::vector<DynTask>& tasks_in, const s
     unsigned char* d = upload_pack(s, pk);
     Prof pr(ctx, KK_SVD, fl, by);
     allow_smem(k_right_dyn);
-    k_right_dyn<<<(unsigned)tasks.size(), block_for(kmax), smem, ctx->stream>>>((const DynTask*)(d + ot));
+    k_right_dyn<<<(unsigned)tasks.size(), block_for(kmax, kSvdWarps), smem, ctx->stream>>>((const DynTask*)(d + ot));
     count_launch(ctx);
     pr.done();
     return ctx->profiling ? (int)ctx->prof.size() - 1 : -1;
@@ -989,7 +1140,7 @@ bool launch_right_sweep(Context* ctx, const std::vector<DynTask>& tasks_in, cons
     const size_t pb_off = (smem + 15) & ~size_t(15);   // phase_beg staged behind the working set
     smem = pb_off + sizeof(int) * (size_t)(n_phase + 1);
     if (smem > kSweepSmem) return false;
-    const int threads = block_for(kmax);
+    const int threads = block_for(kmax, kSvdWarps);
     allow_smem(k_right_sweep);
     const int cap = coresident_ctas(k_right_sweep, threads, smem);
     if (cap <= 0) return false;
@@ -1087,4 +1238,40 @@ bool launch_env_sweep_t(Context* ctx, const std::vector<EnvOutT>& outs, const st
     return true;
 }
 
+bool launch_jacobi_grid(Context* ctx, const std::vector<JacTask>& tasks_in) {
+    const int cap = coresident_ctas(k_jacobi_grid, kThreads, 0);
+    if (cap <= 0) return false;   // decided before any batch is launched
+    int dev = 0, nsm = 0;
+    BSM_CUDA(cudaGetDevice(&dev));
+    BSM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (size_t b = 0; b < tasks_in.size(); b += kJacGridMaxTasks) {
+        const std::vector<JacTask> tasks(tasks_in.begin() + b,
+                                         tasks_in.begin() + std::min(tasks_in.size(), b + kJacGridMaxTasks));
+        const int n = (int)tasks.size();
+        int pairs = 0;
+        for (const JacTask& t : tasks) pairs += (t.k + (t.k & 1)) / 2;
+        // one warp per pair of the first round, at most one CTA per SM (fewer
+        // arrivals per grid-wide wait)
+        const int grid = std::max(1, std::min({cap, nsm, (pairs + kThreads / 32 - 1) / (kThreads / 32)}));
+        Scratch s(ctx);
+        const JacTask* d_t = s.up(tasks);
+        double* fro = s.dbl((size_t)n);
+        int* flags = (int*)ctx->alloc(sizeof(int) * (size_t)n * dev::kMaxSweeps);
+        s.ptrs.push_back(flags);
+        GridSync* gs = (GridSync*)ctx->alloc(sizeof(GridSync));
+        s.ptrs.push_back(gs);
+        BSM_CUDA(cudaMemsetAsync(fro, 0, sizeof(double) * n, ctx->stream));
+        BSM_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)n * dev::kMaxSweeps, ctx->stream));
+        BSM_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), ctx->stream));
+        int* err = ctx->err_word();
+        int a1 = n;
+        void* args[] = {(void*)&d_t, &a1, &fro, &flags, &gs, &err};
+        BSM_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_grid, dim3(grid), dim3(kThreads), args, 0,
+                                             ctx->stream));
+        count_launch(ctx);
+    }
+    return true;
+}
+
 }  // namespace bsm
+

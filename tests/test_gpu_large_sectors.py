@@ -1,0 +1,77 @@
+"""Truncation of exactly applied MPO x MPS products with sectors of several
+hundred rows (the general-size factorisation path, including the grid-wide
+one-sided Jacobi) on the GPU vs the oracle, through the C ABI.
+
+Kept dimensions are compared bit-exactly; the truncated tensors through their
+Gram matrices (1e-12 relative) and the discarded norms."""
+import numpy as np
+import pytest
+
+from oracle import bsmps as OB
+from synth import random_block_values, spinless_random_chain
+from tests._common import n_random, oracle_mpo, oracle_random, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nat():
+    from paper_2604_16118_gb300 import build, native
+    build.build()
+    return native
+
+
+@pytest.fixture(scope="module")
+def ctx(nat):
+    return nat.Context(0)
+
+
+@pytest.mark.parametrize("eps_rel", [1e-3, 1e-7, 1e-11])
+def test_truncate_large_sectors_matches_oracle(nat, ctx, eps_rel):
+    wl = spinless_random_chain(K=10, N=5, seed=1)
+    r = 16
+    W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, wl.spin, wl.n_particles, 0.0)
+    vals = random_block_values(n_random(wl, r), 3)
+    x = nat.mps_create(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, r, vals)
+    y, _ = nat.apply_H(ctx, W, x)
+    oy = OB.apply_exact(oracle_mpo(wl, 0.0), oracle_random(wl, r, vals))
+    assert y.bonds() == oy.bonds
+    assert max(max(b.values()) for b in oy.bonds if b) > 200      # sectors beyond shared memory
+    nrm = float(np.sqrt(OB.dot(oy, oy)))
+    z, dt, _ = nat.truncate(ctx, y, eps_rel * nrm)
+    oz, odt, _ = OB.truncate(oy, eps_rel * nrm)
+    assert z.bonds() == oz.bonds
+    gz = OB.dot(to_oracle(wl, z), to_oracle(wl, z))
+    assert abs(gz - OB.dot(oz, oz)) <= 1e-12 * OB.dot(oz, oz)
+    assert abs(dt - odt) <= 1e-9 * max(odt, eps_rel * nrm * 1e-3)
+    # the truncation error bound of Sec. 2.2 on the GPU result
+    d = OB.add(to_oracle(wl, z), oy, 1.0, -1.0)
+    assert np.sqrt(max(OB.dot(d, d), 0.0)) <= eps_rel * nrm * (1 + 1e-6) + 1e-12 * nrm
+
+
+@pytest.mark.parametrize("eps_rel", [0.3, 1e-6])
+def test_truncate_with_wide_sector_svds(nat, ctx, eps_rel):
+    """A random spinless K = 20, N = 10 iterate at exact ranks (middle sectors of
+    252): the right sweep's SVDs reach k > 110, beyond shared memory, and run
+    as the grid-wide Jacobi."""
+    from oracle import fermion as OF
+    K, N, r = 20, 10, 1024
+    species = OF.site_species(K, 0)
+    dims = OB.default_dims(species, (N, 0), r)
+    n = OB.BSMPS(species, (N, 0), dims, [dict() for _ in range(K)]).layout()[1]
+    vals = random_block_values(n, 7)
+    x = nat.mps_create(ctx, K, 0, N, 0, r, vals)
+    ox = OB.random_mps(species, (N, 0), r, vals)
+    assert x.bonds() == ox.bonds
+    nrm = float(np.sqrt(OB.dot(ox, ox)))
+    z, dt, _ = nat.truncate(ctx, x, eps_rel * nrm)
+    oz, odt, _ = OB.truncate(ox, eps_rel * nrm)
+    assert z.bonds() == oz.bonds
+    assert max(oz.ranks()) > 110 or eps_rel > 0.1
+    gz = OB.dot(to_oracle_k(z, species, N), to_oracle_k(z, species, N))
+    assert abs(gz - OB.dot(oz, oz)) <= 1e-12 * OB.dot(oz, oz)
+    assert abs(dt - odt) <= 1e-9 * odt
+
+
+def to_oracle_k(z, species, N):
+    return OB.BSMPS.from_flat(species, (N, 0), z.bonds(), z.export())
