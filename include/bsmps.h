@@ -110,10 +110,15 @@ typedef struct {
 } bsmps_solver_params;
 
 /* State carried between steps: eta_res of the previous step (start with
- * +INFINITY as in Alg. 2) and the step counter n. */
+ * +INFINITY as in Alg. 2), the step counter n, and the number of eta_res passes
+ * beyond the first that the previous step needed (start with 0).  The last
+ * field only sizes the next step's first batch of candidate tolerances: the
+ * passes of the eta_res loop are evaluated several at a time (their truncations
+ * share launches), which changes no result. */
 typedef struct {
     double eta_res;
     int n;
+    int last_tries;
 } bsmps_solver_state;
 
 /* Scalars reported by one step. */

@@ -216,11 +216,7 @@ MpsPtr eigensolve_joint_step(Context* ctx, const Mpo& W, const PrecondTerms& P, 
             nprobs.push_back(pr);
         }
     const auto n2 = op_gram_batch(ctx, nprobs);
-    struct Term {
-        double norm;
-        int k, kp;
-    };
-    std::vector<Term> terms;
+    std::vector<ResTerm> terms;
     double sum_norms = 0.0;
     for (int kp = 0; kp < nt; ++kp)
         for (int k = 0; k < nt; ++k) {
@@ -228,54 +224,57 @@ MpsPtr eigensolve_joint_step(Context* ctx, const Mpo& W, const PrecondTerms& P, 
             terms.push_back({nv, k, kp});
             sum_norms += nv;
         }
-    std::sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) {
+    std::sort(terms.begin(), terms.end(), [](const ResTerm& a, const ResTerm& b) {
         if (a.norm != b.norm) return a.norm < b.norm;
         if (a.k != b.k) return a.k < b.k;
         return a.kp < b.kp;
     });
     const double zeta = prm.eps_num / (1.0 + prm.c);
     double eta = std::min(2.0 * st.eta_res, 0.8 * zeta * sum_norms);
+    // the eta_res loop of Alg. 4 (pass t: eta * 0.8^t, accepted when
+    // min_i ||r_i|| >= (1 + 1/zeta) eta or t reaches the cap), in batches of
+    // candidate passes
     int tries = 0;
     MpsPtr R;
     std::vector<double> rn(D, 0.0);
-    while (true) {
-        // res_eta on joint terms (Sec. 5.3.1)
-        double acc = 0.0;
-        size_t j0 = 0;
-        while (j0 < terms.size() && acc + terms[j0].norm <= eta / 3.0) {
-            acc += terms[j0].norm;
-            j0++;
+    int width = first_batch_width(st.last_tries);
+    for (bool done = false; !done;) {
+        std::vector<double> etas;
+        double e = eta;
+        for (int c = 0; c < width && tries + c <= kMaxEtaRetries; ++c) {
+            etas.push_back(e);
+            e *= 0.8;
         }
-        double tail = 0.0;
-        for (size_t j = j0; j < terms.size(); ++j) tail += terms[j].norm;
-        MpsPtr y;
-        for (size_t j = j0; j < terms.size(); ++j) {
-            const Term& tm = terms[j];
-            const double eps_j = tail > 0.0 ? eta * tm.norm / (3.0 * tail) : 0.0;
-            MpsPtr z;
-            if (!y)
-                z = op_scale_sites(ctx, u[tm.kp].get(), P.f0[tm.k], P.f1[tm.k]);
-            else
-                z = op_concat(ctx, {{y.get(), {}, {}}, {u[tm.kp].get(), P.f0[tm.k], P.f1[tm.k]}});
-            y = op_truncate(ctx, z.get(), eps_j, 0, nullptr, nullptr);
-        }
-        double rmin = 0.0;
-        if (y) {
-            R = op_truncate(ctx, y.get(), eta / 3.0, 0, nullptr, nullptr);
-            const auto rg = op_gram_batch(ctx, {EnvProblem{R.get(), R.get(), nullptr, 0.0}});
-            rmin = std::numeric_limits<double>::infinity();
-            for (int i = 0; i < D; ++i) {
-                rn[i] = std::sqrt(std::max(rg[0][(size_t)i * D + i], 0.0));
-                rmin = std::min(rmin, rn[i]);
+        std::vector<MpsPtr> Rs = residual_candidates(ctx, P, u, terms, etas);
+        std::vector<EnvProblem> gp;
+        for (auto& Rc : Rs)
+            if (Rc) gp.push_back({Rc.get(), Rc.get(), nullptr, 0.0});
+        const auto rg = op_gram_batch(ctx, gp);
+        size_t gi = 0;
+        for (size_t c = 0; c < etas.size(); ++c) {
+            std::vector<double> cn(D, 0.0);
+            double rmin = 0.0;
+            if (Rs[c]) {
+                rmin = std::numeric_limits<double>::infinity();
+                for (int i = 0; i < D; ++i) {
+                    cn[i] = std::sqrt(std::max(rg[gi][(size_t)i * D + i], 0.0));
+                    rmin = std::min(rmin, cn[i]);
+                }
+                gi++;
             }
-        } else {
-            R.reset();
-            std::fill(rn.begin(), rn.end(), 0.0);
+            if (rmin >= (1.0 + 1.0 / zeta) * etas[c] || tries >= kMaxEtaRetries) {
+                eta = etas[c];
+                R = std::move(Rs[c]);
+                rn = cn;
+                done = true;
+                break;
+            }
+            tries++;
         }
-        if (rmin >= (1.0 + 1.0 / zeta) * eta || tries >= kMaxEtaRetries) break;
-        eta *= 0.8;
-        tries++;
+        if (!done) eta = e;
+        width = kCandidateBatch;
     }
+    st.last_tries = tries;
     st.eta_res = eta;
     std::vector<double> rho(D);
     for (int i = 0; i < D; ++i) {

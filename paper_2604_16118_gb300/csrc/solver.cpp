@@ -138,6 +138,61 @@ static void check_finite(double v, const char* what) {
     BSM_REQUIRE(std::isfinite(v), BSMPS_ERR_NUMERIC, std::string("non-finite ") + what);
 }
 
+int first_batch_width(int last_tries) { return std::max(1, std::min(kCandidateBatch, last_tries + 1)); }
+
+std::vector<MpsPtr> residual_candidates(Context* ctx, const PrecondTerms& P, const std::vector<MpsPtr>& u,
+                                        const std::vector<ResTerm>& terms, const std::vector<double>& etas) {
+    const int C = (int)etas.size();
+    std::vector<size_t> j0(C, 0);
+    std::vector<double> tail(C, 0.0);
+    size_t jmin = terms.size();
+    for (int c = 0; c < C; ++c) {
+        // drop the smallest terms while their norms sum to at most eta/3
+        double acc = 0.0;
+        while (j0[c] < terms.size() && acc + terms[j0[c]].norm <= etas[c] / 3.0) {
+            acc += terms[j0[c]].norm;
+            j0[c]++;
+        }
+        for (size_t j = j0[c]; j < terms.size(); ++j) tail[c] += terms[j].norm;
+        jmin = std::min(jmin, j0[c]);
+    }
+    std::vector<MpsPtr> y(C);
+    for (size_t j = jmin; j < terms.size(); ++j) {
+        const ResTerm& tm = terms[j];
+        std::vector<MpsPtr> z;
+        std::vector<const Mps*> zs;
+        std::vector<double> eps;
+        std::vector<int> who;
+        for (int c = 0; c < C; ++c) {
+            if (j < j0[c]) continue;
+            // y_j = trunc_{eps_j}(y_{j-1} + s_j), eps_j = eta ||s_j|| / (3 sum_{i > J_0} ||s_i||)
+            if (!y[c])
+                z.push_back(op_scale_sites(ctx, u[tm.kp].get(), P.f0[tm.k], P.f1[tm.k]));
+            else
+                z.push_back(op_concat(ctx, {{y[c].get(), {}, {}}, {u[tm.kp].get(), P.f0[tm.k], P.f1[tm.k]}}));
+            zs.push_back(z.back().get());
+            eps.push_back(tail[c] > 0.0 ? etas[c] * tm.norm / (3.0 * tail[c]) : 0.0);
+            who.push_back(c);
+        }
+        std::vector<MpsPtr> t = op_truncate_batch(ctx, zs, eps, 0);
+        for (size_t i = 0; i < who.size(); ++i) y[who[i]] = std::move(t[i]);
+    }
+    // final trunc_{eta/3}
+    std::vector<const Mps*> ys;
+    std::vector<double> eps;
+    std::vector<int> who;
+    for (int c = 0; c < C; ++c)
+        if (y[c]) {
+            ys.push_back(y[c].get());
+            eps.push_back(etas[c] / 3.0);
+            who.push_back(c);
+        }
+    std::vector<MpsPtr> out(C);
+    std::vector<MpsPtr> t = op_truncate_batch(ctx, ys, eps, 0);
+    for (size_t i = 0; i < who.size(); ++i) out[who[i]] = std::move(t[i]);
+    return out;
+}
+
 MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const bsmps_solver_params& prm,
                        bsmps_solver_state& st, const Mps* x_in, bsmps_step_info& info) {
     const double flops0 = ctx->flops;
@@ -178,11 +233,7 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
             nprobs.push_back(pr);
         }
     const std::vector<double> n2 = op_dot_batch(ctx, nprobs);
-    struct Term {
-        double norm;
-        int k, kp;
-    };
-    std::vector<Term> terms;
+    std::vector<ResTerm> terms;
     double sum_norms = 0.0;
     for (int kp = 0; kp < nt; ++kp)
         for (int k = 0; k < nt; ++k) {
@@ -190,48 +241,43 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
             terms.push_back({nv, k, kp});
             sum_norms += nv;
         }
-    std::sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) {
+    std::sort(terms.begin(), terms.end(), [](const ResTerm& a, const ResTerm& b) {
         if (a.norm != b.norm) return a.norm < b.norm;
         if (a.k != b.k) return a.k < b.k;
         return a.kp < b.kp;
     });
     const double zeta = prm.eps_num / (1.0 + prm.c);
     double eta = std::min(2.0 * st.eta_res, 0.8 * zeta * sum_norms);
+    // the eta_res loop: pass t uses eta * 0.8^t and is accepted when
+    // ||res_eta|| >= (1 + 1/zeta) eta or t reaches the cap; passes are
+    // evaluated in batches of candidates
     int tries = 0;
     MpsPtr r;
     double rnorm = 0.0;
-    while (true) {
-        // res_eta (Sec. 5.3.1)
-        double acc = 0.0;
-        size_t j0 = 0;
-        while (j0 < terms.size() && acc + terms[j0].norm <= eta / 3.0) {
-            acc += terms[j0].norm;
-            j0++;
+    int width = first_batch_width(st.last_tries);
+    for (bool done = false; !done;) {
+        std::vector<double> etas;
+        double e = eta;
+        for (int c = 0; c < width && tries + c <= kMaxEtaRetries; ++c) {
+            etas.push_back(e);
+            e *= 0.8;
         }
-        double tail = 0.0;
-        for (size_t j = j0; j < terms.size(); ++j) tail += terms[j].norm;
-        MpsPtr y;
-        for (size_t j = j0; j < terms.size(); ++j) {
-            const Term& tm = terms[j];
-            const double eps_j = tail > 0.0 ? eta * tm.norm / (3.0 * tail) : 0.0;
-            MpsPtr z;
-            if (!y)
-                z = op_scale_sites(ctx, u[tm.kp].get(), P.f0[tm.k], P.f1[tm.k]);
-            else
-                z = op_concat(ctx, {{y.get(), {}, {}}, {u[tm.kp].get(), P.f0[tm.k], P.f1[tm.k]}});
-            y = op_truncate(ctx, z.get(), eps_j, 0, nullptr, nullptr);
+        std::vector<MpsPtr> Rs = residual_candidates(ctx, P, u, terms, etas);
+        for (size_t c = 0; c < etas.size(); ++c) {
+            const double rn = Rs[c] ? op_core0_norm(ctx, Rs[c].get()) : 0.0;
+            if (rn >= (1.0 + 1.0 / zeta) * etas[c] || tries >= kMaxEtaRetries) {
+                eta = etas[c];
+                r = std::move(Rs[c]);
+                rnorm = rn;
+                done = true;
+                break;
+            }
+            tries++;
         }
-        if (y) {
-            r = op_truncate(ctx, y.get(), eta / 3.0, 0, nullptr, nullptr);
-            rnorm = op_core0_norm(ctx, r.get());
-        } else {
-            r.reset();
-            rnorm = 0.0;
-        }
-        if (rnorm >= (1.0 + 1.0 / zeta) * eta || tries >= kMaxEtaRetries) break;
-        eta *= 0.8;
-        tries++;
+        if (!done) eta = e;
+        width = kCandidateBatch;
     }
+    st.last_tries = tries;
     st.eta_res = eta;
     const double rho = (rnorm + eta) / std::sqrt(1.0 - prm.c);
     check_finite(rho, "rho");
@@ -320,7 +366,7 @@ MpsPtr eigensolve_outer(Context* ctx, const Mpo& W, const PrecondTerms& P, const
         const double tau_m = eta / (2.0 * (1.0 + (1.0 + alpha) * kappa));
         bsmps_solver_params inner = prm;
         inner.tau = tau_m;
-        bsmps_solver_state st{std::numeric_limits<double>::infinity(), 0};
+        bsmps_solver_state st{std::numeric_limits<double>::infinity(), 0, 0};
         bsmps_outer_record rec{};
         const double fl0 = ctx->flops;
         bsmps_step_info info{};

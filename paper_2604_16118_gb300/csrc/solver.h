@@ -18,6 +18,23 @@ struct PrecondTerms {
 };
 
 PrecondTerms make_precond(const bsmps_precond* p);
+
+// One residual term s_{k,k'} = S_k u_k' with its norm (Sec. 5.3.1).
+struct ResTerm {
+    double norm;
+    int k, kp;
+};
+// res_eta for the candidate tolerances etas (consecutive passes of the eta_res
+// loop), computed together: the sequential truncated sums of all candidates
+// advance term by term, the truncations of one term sharing one batch.  Each
+// candidate runs exactly the operations of its own pass.  terms: ascending by
+// (norm, k, k').  Entry c is null when candidate c keeps no term.
+std::vector<MpsPtr> residual_candidates(Context* ctx, const PrecondTerms& P, const std::vector<MpsPtr>& u,
+                                        const std::vector<ResTerm>& terms, const std::vector<double>& etas);
+// Width of the first batch of candidates after a step that needed last_tries
+// extra passes, and of later batches.
+int first_batch_width(int last_tries);
+constexpr int kCandidateBatch = 8;
 std::vector<double> pair_sums(Context* ctx, const PrecondTerms& P,
                               const std::vector<std::tuple<const Mps*, const Mps*, const Mpo*>>& jobs);
 double eigvec_bound(double rho, double delta);

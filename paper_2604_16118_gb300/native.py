@@ -34,7 +34,7 @@ class SolverParams(C.Structure):
 
 
 class SolverState(C.Structure):
-    _fields_ = [("eta_res", C.c_double), ("n", C.c_int)]
+    _fields_ = [("eta_res", C.c_double), ("n", C.c_int), ("last_tries", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -431,7 +431,7 @@ def solver_params(c, delta, eps_num=None, t_eig=0.5, tau=1e-8, r_max=0, u_rel=1e
 
 
 def solver_state():
-    return SolverState(math.inf, 0)
+    return SolverState(math.inf, 0, 0)
 
 
 def eigensolve_step(ctx, mpo, p, params, state, x):
