@@ -22,4 +22,6 @@ Modules (each function cites the part of the paper it follows):
   omegamin) and the a-posteriori bounds (Sec. 5.4).
 * ``joint``    -- joint block MPS of D vectors and the perturbed inverse
   subspace iteration (Alg. 4, Sec. 6).
+* ``ozaki``    -- FP64 matrix product by exact integer slice products (the
+  Ozaki scheme; not in the paper), pinned against exact rational arithmetic.
 """
