@@ -316,6 +316,27 @@ BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const b
                                    bsmps_solver_state* state, bsmps_mps* x,
                                    bsmps_step_info* info);
 
+/* ---- FP64 products on the tensor cores ----------------------------------- */
+
+/* C = A B in float64, emulated on the bf16 tensor cores by the Ozaki scheme
+ * (Ozaki, Ogita, Oishi, Rump 2012; not part of the paper).
+ *   - Scaling: each row of A and each column of B is scaled by a power of two
+ *     below which all its entries lie.
+ *   - Slices: the scaled values are cut into `slices` (1..8) digits of 7 bits
+ *     plus sign, each exact in bf16.
+ *   - Products: slice pairs (p, q) with p + q <= slices + 1 are multiplied
+ *     exactly (FP32 accumulation of integers below 2^24, 128 values of k at a
+ *     time) and summed in float64.
+ * Error bound per entry, in units of K 2^{e_i + f_j}:
+ * 2^{1 - 7 slices} + sum_{d > slices+1} (2 slices - d + 1) 2^{14 - 7d}
+ * + slices 2^{-52}.  With 8 slices this is within a few units of float64
+ * rounding relative to max_k |a_ik| max_k |b_kj| K.
+ * A (M x K, leading dimension lda), B (K x N, ldb) and C (M x N, ldc) are
+ * row-major DEVICE pointers.  The work is ordered on the context stream and the
+ * call does not synchronise.  Errors: INVALID_ARG, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda,
+                                        const double* B, int ldb, double* C, int ldc, int slices);
+
 /* ---- joint block MPS and the subspace iteration (Alg. 4, Sec. 6) -------- */
 
 /* A joint block MPS holds D vectors x_1..x_D in one MPS whose last bond (the

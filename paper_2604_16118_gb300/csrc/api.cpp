@@ -287,6 +287,17 @@ bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset, int64_t*
     });
 }
 
+bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda, const double* B,
+                              int ldb, double* Cm, int ldc, int slices) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(M >= 0 && N >= 0 && K >= 0 && lda >= K && ldb >= N && ldc >= N, BSMPS_ERR_INVALID_ARG,
+                    "emulated GEMM: need sizes >= 0 and leading dimensions >= row lengths");
+        BSM_REQUIRE(M == 0 || N == 0 || (Cm && (K == 0 || (A && B))), BSMPS_ERR_INVALID_ARG, "null matrix");
+        bsm::launch_gemm_ozaki(c, M, N, K, A, lda, B, ldb, Cm, ldc, slices);
+    });
+}
+
 bsmps_status bsmps_mps_joint_random_size(int n_orb, int spin, int n_up, int n_dn, int r_max, int D,
                                          int64_t* n_values) {
     return guarded(nullptr, [&] {

@@ -82,6 +82,12 @@ struct JacTask {
 // resident (the caller then runs one CTA per matrix).
 bool launch_jacobi_grid(Context* ctx, const std::vector<JacTask>& tasks);
 
+// C (M x N) = A (M x K) B (K x N), all row-major FP64 on the device with
+// leading dimensions, emulated by S (1..8) bf16 integer slices per factor on the
+// tensor cores (Ozaki scheme); stream-ordered, no synchronisation.
+void launch_gemm_ozaki(Context* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                       double* C, int ldc, int S);
+
 void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks);
 // Sets n[i] doubles at ptr[i] to zero, all regions in one launch.
 void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n);

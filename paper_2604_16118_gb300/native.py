@@ -136,6 +136,7 @@ _SIGS = {
     "bsmps_mlp_destroy": (_i, [_vp]),
     "bsmps_eigensolve_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
                                    C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(StepInfo)]),
+    "bsmps_gemm_ozaki": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _i, _vp, _i, _i]),
     "bsmps_mps_joint_random_size": (_i, [_i, _i, _i, _i, _i, _i, _pi64]),
     "bsmps_mps_create_joint": (_i, [_vp, _i, _i, _i, _i, _i, _i, C.POINTER(C.c_ubyte), _i, _pd, _i64,
                                     C.POINTER(_vp)]),
@@ -455,6 +456,16 @@ def eigensolve_outer(ctx, mpo, p, params, x, tau, alpha=1.0, max_outer=20, max_i
                                              max_inner, C.byref(h), recs, C.byref(n), C.byref(ok)))
     x.h = None          # destroyed by the library
     return MPS(ctx, h), [recs[i].as_dict() for i in range(n.value)], bool(ok.value)
+
+
+def gemm_ozaki(ctx, A, B, C, slices=8):
+    """C = A B (row-major float64 device tensors, e.g. torch CUDA tensors with
+    data_ptr()), emulated on the tensor cores; stream-ordered on ctx's stream."""
+    M, K = A.shape
+    N = B.shape[1]
+    _check(ctx, lib().bsmps_gemm_ozaki(ctx.h, M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                       C.data_ptr(), C.stride(0), slices))
+    return C
 
 
 def mps_joint_random_size(n_orb, spin, n_up, n_dn, r_max, D):
