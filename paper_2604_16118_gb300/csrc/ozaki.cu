@@ -22,7 +22,6 @@ namespace {
 
 constexpr int kOzTile = 64;      // output tile per CTA (64 x 64)
 constexpr int kOzChunk = 128;    // k values per exact FP32 accumulation
-constexpr int kOzThreads = 128;  // 4 warps, 2 x 2 warp tiles of 32 x 32
 
 void launched(Context* ctx) {
     ctx->launches++;
@@ -81,93 +80,163 @@ __global__ void k_oz_split(const double* __restrict__ X, int rows, int cols, int
     }
 }
 
-__device__ __forceinline__ unsigned ld_pair(const __nv_bfloat16* base, int64_t off, bool ok) {
-    return ok ? *reinterpret_cast<const unsigned*>(base + off) : 0u;
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+__device__ __forceinline__ void mma_bf16(float c[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+    // a pure function of registers: the compiler may schedule it freely
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void ldsm_x4(unsigned r[4], const void* smem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros.
+__device__ __forceinline__ void cp16(void* smem, const void* gmem, int src_bytes) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(a), "l"(gmem), "r"(src_bytes));
+}
+
+constexpr int kOzPitch = 24;                                // bf16 per staged row (48 B: ldmatrix rows on distinct banks)
+constexpr int kOzMaxS = 8;
+constexpr int kOzStage = 2 * kOzMaxS * kOzTile * kOzPitch;  // bf16 of A and B slices for one k16 step
+constexpr int kOzWarps = 16;                                // 4 x 4 warp tiles of 16 x 16
+
 // C (M x N, row-major, ldc) = sum_d 2^{e_i + f_j - 7d} sum_{p + q = d} A_p B_q.
-// Fragment layouts of m16n8k16 (g = lane / 4, t = lane % 4): A rows g and g+8,
-// k pairs 2t and 2t+8; B columns g, k pairs 2t and 2t+8; C rows g and g+8,
+// Per k16 step all slices of the CTA's 64 x 64 tile are staged in shared memory
+// (double-buffered cp.async); each warp owns a 16 x 16 output tile and keeps
+// one FP32 accumulator per d, flushed to FP64 every kOzChunk values of k.
+// Fragment layouts of m16n8k16 (g = lane / 4, t = lane % 4): C rows g, g+8,
 // columns 2t, 2t+1.
-__global__ void __launch_bounds__(kOzThreads) k_oz_gemm(const __nv_bfloat16* __restrict__ As,
-                                                        const __nv_bfloat16* __restrict__ Bs, int64_t sa,
-                                                        int64_t sb, const int* __restrict__ e,
-                                                        const int* __restrict__ f, int M, int N, int Kp, int S,
-                                                        double* __restrict__ C, int ldc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * kOzTile + (warp >> 1) * 32;
-    const int n0 = blockIdx.x * kOzTile + (warp & 1) * 32;
-    double acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[i][j][v] = 0.0;
-    for (int d = 2; d <= S + 1; ++d) {
-        const int p_lo = d - S > 1 ? d - S : 1, p_hi = d - 1 < S ? d - 1 : S;
-        const double w = ldexp(1.0, -7 * d);
-        for (int k0 = 0; k0 < Kp; k0 += kOzChunk) {
-            float c32[2][4][4];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) c32[i][j][v] = 0.f;
-            const int k1 = k0 + kOzChunk < Kp ? k0 + kOzChunk : Kp;
-            for (int kk = k0; kk < k1; kk += 16) {
-                for (int p = p_lo; p <= p_hi; ++p) {
-                    const __nv_bfloat16* Ap = As + (int64_t)(p - 1) * sa;
-                    const __nv_bfloat16* Bq = Bs + (int64_t)(d - p - 1) * sb;
-                    unsigned a[2][4], b[4][2];
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const int r0 = m0 + i * 16 + g, r1 = r0 + 8;
-                        a[i][0] = ld_pair(Ap, (int64_t)r0 * Kp + kk + 2 * t, r0 < M);
-                        a[i][1] = ld_pair(Ap, (int64_t)r1 * Kp + kk + 2 * t, r1 < M);
-                        a[i][2] = ld_pair(Ap, (int64_t)r0 * Kp + kk + 2 * t + 8, r0 < M);
-                        a[i][3] = ld_pair(Ap, (int64_t)r1 * Kp + kk + 2 * t + 8, r1 < M);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int cn = n0 + j * 8 + g;
-                        b[j][0] = ld_pair(Bq, (int64_t)cn * Kp + kk + 2 * t, cn < N);
-                        b[j][1] = ld_pair(Bq, (int64_t)cn * Kp + kk + 2 * t + 8, cn < N);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 2; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) mma_bf16(c32[i][j], a[i], b[j]);
-                }
+// Slice pairs (p, q), p + q <= S + 1, in order of d = p + q: pair i of the
+// flattened list.
+template <int S>
+struct OzPairs {
+    int p[S * (S + 1) / 2], q[S * (S + 1) / 2];
+    constexpr OzPairs() : p(), q() {
+        int i = 0;
+        for (int d = 2; d <= S + 1; ++d)
+            for (int pp = 1; pp <= d - 1; ++pp) {
+                p[i] = pp;
+                q[i] = d - pp;
+                ++i;
             }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[i][j][v] += (double)c32[i][j][v] * w;
+    }
+};
+
+template <int S>
+__global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const __nv_bfloat16* __restrict__ As,
+                                                           const __nv_bfloat16* __restrict__ Bs, int64_t sa,
+                                                           int64_t sb, const int* __restrict__ e,
+                                                           const int* __restrict__ f, int M, int N, int Kp,
+                                                           double* __restrict__ C, int ldc) {
+    constexpr int NP = S * (S + 1) / 2;
+    constexpr OzPairs<S> PR{};
+    extern __shared__ __align__(16) __nv_bfloat16 sm_oz[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int mt = blockIdx.y * kOzTile, nt = blockIdx.x * kOzTile;
+    const int wm = (warp >> 2) * 16, wn = (warp & 3) * 16;
+    // staging of the k16 step starting at kk into buffer b
+    auto stage = [&](int b, int kk) {
+        __nv_bfloat16* base = sm_oz + b * kOzStage;
+        constexpr int n_copies = 2 * S * kOzTile * 2;
+        for (int i = tid; i < n_copies; i += kOzWarps * 32) {
+            const int which = i / (S * kOzTile * 2);            // 0: A, 1: B
+            const int rem = i - which * S * kOzTile * 2;
+            const int p = rem / (kOzTile * 2), r = (rem >> 1) % kOzTile, half = rem & 1;
+            const int row = (which ? nt : mt) + r;
+            const bool ok = row < (which ? N : M);
+            const __nv_bfloat16* src = (which ? Bs + p * sb : As + p * sa) + (ok ? (int64_t)row * Kp + kk + half * 8 : 0);
+            __nv_bfloat16* dst = base + ((which * kOzMaxS + p) * kOzTile + r) * kOzPitch + half * 8;
+            cp16(dst, src, ok ? 16 : 0);
         }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+    float c32[S][2][4];
+    double acc[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[j][v] = 0.0;
+#pragma unroll
+    for (int d = 0; d < S; ++d)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) c32[d][j][v] = 0.f;
+    const int nk = Kp / 16;
+    // ldmatrix row addresses: A rows wm + lane % 16, k half lane / 16;
+    // B rows (columns of B) wn + lane % 8 + (lane / 16) 8, k half (lane / 8) % 2
+    const int a_off = (wm + (lane & 15)) * kOzPitch + (lane >> 4) * 8;
+    const int b_off = (wn + (lane & 7) + (lane >> 4) * 8) * kOzPitch + ((lane >> 3) & 1) * 8;
+    stage(0, 0);
+    for (int step = 0; step < nk; ++step) {
+        if (step + 1 < nk) {
+            stage((step + 1) & 1, (step + 1) * 16);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();
+        const __nv_bfloat16* base = sm_oz + (step & 1) * kOzStage;
+        // fragments of pair i + 1 are loaded before the products of pair i
+        unsigned a[2][4], b[2][4];
+        ldsm_x4(a[0], base + (PR.p[0] - 1) * kOzTile * kOzPitch + a_off);
+        ldsm_x4(b[0], base + (kOzMaxS + PR.q[0] - 1) * kOzTile * kOzPitch + b_off);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const int cur = i & 1, nxt = cur ^ 1;
+            if (i + 1 < NP) {
+                ldsm_x4(a[nxt], base + (PR.p[i + 1] - 1) * kOzTile * kOzPitch + a_off);
+                ldsm_x4(b[nxt], base + (kOzMaxS + PR.q[i + 1] - 1) * kOzTile * kOzPitch + b_off);
+            }
+            const int d = PR.p[i] + PR.q[i] - 2;
+            mma_bf16(c32[d][0], a[cur][0], a[cur][1], a[cur][2], a[cur][3], b[cur][0], b[cur][1]);
+            mma_bf16(c32[d][1], a[cur][0], a[cur][1], a[cur][2], a[cur][3], b[cur][2], b[cur][3]);
+        }
+        // exact FP32 sums cover at most kOzChunk values of k: flush to FP64
+        if ((step + 1) % (kOzChunk / 16) == 0 || step + 1 == nk) {
+#pragma unroll
+            for (int d = 0; d < S; ++d) {
+                const double w = ldexp(1.0, -7 * (d + 2));
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        acc[j][v] = fma((double)c32[d][j][v], w, acc[j][v]);
+                        c32[d][j][v] = 0.f;
+                    }
+            }
+        }
+        __syncthreads();   // the buffer read here is refilled by the next step's stage
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int r = m0 + i * 16 + g + (v >= 2 ? 8 : 0);
-                const int c = n0 + j * 8 + 2 * t + (v & 1);
-                if (r < M && c < N) C[(int64_t)r * ldc + c] = ldexp(ldexp(acc[i][j][v], e[r]), f[c]);
-            }
+        for (int v = 0; v < 4; ++v) {
+            const int r = mt + wm + g + (v >= 2 ? 8 : 0);
+            const int c = nt + wn + j * 8 + 2 * t + (v & 1);
+            if (r < M && c < N) C[(int64_t)r * ldc + c] = ldexp(ldexp(acc[j][v], e[r]), f[c]);
+        }
+}
+
+template <int S>
+void launch_oz_gemm(Context* ctx, dim3 grid, size_t smem, const __nv_bfloat16* As, const __nv_bfloat16* Bs,
+                    int64_t sa, int64_t sb, const int* e, const int* f, int M, int N, int Kp, double* C, int ldc) {
+    static bool attr = false;
+    if (!attr) {
+        BSM_CUDA(cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BSM_CUDA(cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+        attr = true;
+    }
+    k_oz_gemm<S><<<grid, kOzWarps * 32, smem, ctx->stream>>>(As, Bs, sa, sb, e, f, M, N, Kp, C, ldc);
 }
 
 }  // namespace
@@ -203,7 +272,17 @@ void launch_gemm_ozaki(Context* ctx, int M, int N, int K, const double* A, int l
     k_oz_split<<<blocks_b, 256, 0, ctx->stream>>>(B, K, N, ldb, 1, f, S, Kp, Bs, sb);
     launched(ctx);
     dim3 grid((N + kOzTile - 1) / kOzTile, (M + kOzTile - 1) / kOzTile);
-    k_oz_gemm<<<grid, kOzThreads, 0, ctx->stream>>>(As, Bs, sa, sb, e, f, M, N, Kp, S, C, ldc);
+    const size_t smem = sizeof(__nv_bfloat16) * 2 * (size_t)kOzStage;
+    switch (S) {
+        case 1: launch_oz_gemm<1>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        case 2: launch_oz_gemm<2>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        case 3: launch_oz_gemm<3>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        case 4: launch_oz_gemm<4>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        case 5: launch_oz_gemm<5>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        case 6: launch_oz_gemm<6>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        case 7: launch_oz_gemm<7>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        default: launch_oz_gemm<8>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+    }
     launched(ctx);
     ctx->flops += 2.0 * M * (double)N * K;
 }
