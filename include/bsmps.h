@@ -334,6 +334,16 @@ BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const b
  * A (M x K, leading dimension lda), B (K x N, ldb) and C (M x N, ldc) are
  * row-major DEVICE pointers.  The work is ordered on the context stream and the
  * call does not synchronise.  Errors: INVALID_ARG, OOM, CUDA. */
+/* Block products of at least 2^min_log2_flops flops with a single contribution
+ * (the large R X and U S X products of sweeps over wide sectors) run as
+ * bsmps_gemm_ozaki with 8 slices, all such products of one grouped launch
+ * together; 0 (the default) keeps every product on the FP64 units.  The
+ * emulation's error is relative to row and column maxima, so on graded factors
+ * it can move truncation decisions at the level of the truncation tolerance
+ * (the iteration stays within its error control, but the trajectory is not the
+ * FP64 one).  Errors: INVALID_ARG (negative or above 60). */
+BSMPS_API bsmps_status bsmps_ctx_set_gemm_emulation(bsmps_ctx ctx, int min_log2_flops);
+
 BSMPS_API bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda,
                                         const double* B, int ldb, double* C, int ldc, int slices);
 

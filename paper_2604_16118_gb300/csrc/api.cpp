@@ -287,6 +287,14 @@ bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset, int64_t*
     });
 }
 
+bsmps_status bsmps_ctx_set_gemm_emulation(bsmps_ctx ctx, int min_log2_flops) {
+    return guarded(ctx, [&] {
+        BSM_REQUIRE(ctx && min_log2_flops >= 0 && min_log2_flops <= 60, BSMPS_ERR_INVALID_ARG,
+                    "need a context and 0 <= min_log2_flops <= 60");
+        ctx->c.gemm_emulation_log2 = min_log2_flops;
+    });
+}
+
 bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda, const double* B,
                               int ldb, double* Cm, int ldc, int slices) {
     return guarded(ctx, [&] {
@@ -294,7 +302,7 @@ bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* 
         BSM_REQUIRE(M >= 0 && N >= 0 && K >= 0 && lda >= K && ldb >= N && ldc >= N, BSMPS_ERR_INVALID_ARG,
                     "emulated GEMM: need sizes >= 0 and leading dimensions >= row lengths");
         BSM_REQUIRE(M == 0 || N == 0 || (Cm && (K == 0 || (A && B))), BSMPS_ERR_INVALID_ARG, "null matrix");
-        bsm::launch_gemm_ozaki(c, M, N, K, A, lda, B, ldb, Cm, ldc, slices);
+        bsm::launch_gemm_ozaki(c, M, N, K, A, lda, B, ldb, Cm, ldc, slices, 0, 1.0);
     });
 }
 

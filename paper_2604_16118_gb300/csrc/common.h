@@ -134,6 +134,7 @@ struct Context {
     int64_t launches = 0;
     double flops = 0.0;              // algorithmic FP64 flops issued (running total)
     bool profiling = false;
+    int gemm_emulation_log2 = 0;     // block products >= 2^this flops on the tensor cores (0: never)
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;
     cudaEvent_t take_event();

@@ -333,14 +333,22 @@ void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
     ps.done();
 }
 
+
 void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins) {
     if (outs.empty()) return;
     configure_carveout();
     std::vector<GemmTile> tiles;
-    std::vector<int> small;
+    std::vector<int> small, emulated;
     double fl = 0.0, by = 0.0;
     for (int o = 0; o < (int)outs.size(); ++o) {
         const GemmOut& g = outs[o];
+        // outputs of at least 2^gemm_emulation_log2 flops with one contribution
+        // (overwritten) go to the tensor-core FP64 emulation
+        if (ctx->gemm_emulation_log2 > 0 && g.end == g.beg + 1 && g.beta == 0.0 &&
+            2.0 * g.M * (double)g.N * ins[g.beg].K >= std::ldexp(1.0, ctx->gemm_emulation_log2)) {
+            emulated.push_back(o);
+            continue;
+        }
         if (g.M <= kTile && g.N <= kTile) {
             if (g.M > 0 && g.N > 0) small.push_back(o);
         } else {
@@ -352,6 +360,19 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
             by += 8.0 * ((double)g.M * ins[c].K + (double)ins[c].K * g.N);
         }
         by += 8.0 * g.M * (double)g.N * (g.beta == 0.0 ? 1.0 : 2.0);
+    }
+    if (!emulated.empty()) {
+        std::vector<OzGemm> og;
+        double efl = 0.0;
+        for (int o : emulated) {
+            const GemmOut& g = outs[o];
+            const GemmIn& in = ins[g.beg];
+            og.push_back({in.A, in.B, g.C, g.M, g.N, in.K, in.lda, in.ldb, g.ldc, in.transA, in.alpha});
+            efl += 2.0 * g.M * (double)g.N * in.K;
+        }
+        ProfScope pe(ctx, KK_GEMM, efl, 0.0);
+        launch_gemm_ozaki_group(ctx, og, 8);
+        pe.done();
     }
     if (tiles.empty() && small.empty()) return;
     ctx->flops += fl;

@@ -82,11 +82,22 @@ struct JacTask {
 // resident (the caller then runs one CTA per matrix).
 bool launch_jacobi_grid(Context* ctx, const std::vector<JacTask>& tasks);
 
-// C (M x N) = A (M x K) B (K x N), all row-major FP64 on the device with
-// leading dimensions, emulated by S (1..8) bf16 integer slices per factor on the
-// tensor cores (Ozaki scheme); stream-ordered, no synchronisation.
+// C (M x N) = alpha op(A) B, op(A) = A (M x K) or A^T (A stored K x M), B
+// (K x N), all row-major FP64 on the device with leading dimensions, emulated by
+// S (1..8) bf16 integer slices per factor on the tensor cores (Ozaki scheme);
+// stream-ordered, no synchronisation.
 void launch_gemm_ozaki(Context* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                       double* C, int ldc, int S);
+                       double* C, int ldc, int S, int transA = 0, double alpha = 1.0);
+// Several such products in one exponent/split launch and one GEMM launch
+// (a tile list over all products).
+struct OzGemm {
+    const double* A;
+    const double* B;
+    double* C;
+    int M, N, K, lda, ldb, ldc, transA;
+    double alpha;
+};
+void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S);
 
 void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks);
 // Sets n[i] doubles at ptr[i] to zero, all regions in one launch.

@@ -28,54 +28,36 @@ void launched(Context* ctx) {
     BSM_CUDA(cudaGetLastError());
 }
 
-// e_i of every row of the row-major M x K matrix A: one warp per row.
-__global__ void k_oz_row_exp(const double* __restrict__ A, int M, int K, int lda, int* __restrict__ e) {
+// One row of op(A) or one column of B: its exponent and its digit slices.
+struct OzRow {
+    const double* src;
+    int64_t stride;        // element k at src[k * stride]
+    int len, Kp;           // K and K rounded up to 16
+    int* exp;
+    __nv_bfloat16* dst;    // slice 0 of the row; slice p at dst + p * slice_stride
+    int64_t slice_stride;
+};
+
+// One warp per row: e = the smallest integer with max |x| < 2^e, then the S
+// digits of x 2^-e (d = trunc(r 2^7), r <- r 2^7 - d, exact), zeros for k >= K.
+__global__ void k_oz_rows(const OzRow* __restrict__ rows, int n_rows, int S) {
     const int lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= M) return;
+    const int w = (int)blockIdx.x * (blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    if (w >= n_rows) return;
+    const OzRow rw = rows[w];
     double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(A[(int64_t)row * lda + k]));
+    for (int k = lane; k < rw.len; k += 32) mx = fmax(mx, fabs(rw.src[(int64_t)k * rw.stride]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) {
-        int ex = 0;
-        if (mx > 0.0) frexp(mx, &ex);   // mx = m 2^ex, 0.5 <= m < 1
-        e[row] = ex;
-    }
-}
-
-// f_j of every column of the row-major K x N matrix B: one thread per column.
-__global__ void k_oz_col_exp(const double* __restrict__ B, int K, int N, int ldb, int* __restrict__ f) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= N) return;
-    double mx = 0.0;
-    for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(B[(int64_t)k * ldb + col]));
     int ex = 0;
-    if (mx > 0.0) frexp(mx, &ex);
-    f[col] = ex;
-}
-
-// Digits of A (row scale e) into S bf16 slices, each M x Kp row-major; or of B
-// (column scale f) into S slices stored transposed, N x Kp.  k >= K: zeros.
-__global__ void k_oz_split(const double* __restrict__ X, int rows, int cols, int ld, int trans,
-                           const int* __restrict__ ex, int S, int Kp, __nv_bfloat16* __restrict__ out,
-                           int64_t slice_stride) {
-    // output element (r, k): r < rows_out, k < Kp (rows_out = rows of A or columns of B)
-    const int64_t n = (int64_t)(trans ? cols : rows) * Kp;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / Kp), k = (int)(idx % Kp);
-        double v = 0.0;
-        if (!trans) {
-            if (k < cols) v = X[(int64_t)r * ld + k];   // A: row r, column k
-        } else {
-            if (k < rows) v = X[(int64_t)k * ld + r];   // B: row k, column r
-        }
-        double rem = ldexp(v, -ex[r]);
+    if (mx > 0.0) frexp(mx, &ex);   // mx = m 2^ex, 0.5 <= m < 1
+    if (lane == 0) *rw.exp = ex;
+    for (int k = lane; k < rw.Kp; k += 32) {
+        double rem = k < rw.len ? ldexp(rw.src[(int64_t)k * rw.stride], -ex) : 0.0;
         for (int p = 0; p < S; ++p) {
             rem *= 128.0;                 // exact (power of two)
             const double d = trunc(rem);
             rem -= d;                     // exact
-            out[p * slice_stride + idx] = __double2bfloat16(d);   // |d| <= 127: exact
+            rw.dst[p * rw.slice_stride + k] = __double2bfloat16(d);   // |d| <= 127: exact
         }
     }
 }
@@ -129,18 +111,41 @@ struct OzPairs {
     }
 };
 
+// One product of a group, C = alpha op(A) B, with its slices and exponents.
+struct OzProd {
+    double* C;
+    int M, N, Kp, ldc;
+    double alpha;
+    int64_t a_off, b_off;   // slice 0 of op(A) (M x Kp) and of B^T (N x Kp) in the slice buffers
+    int e_off, f_off;       // row exponents of op(A), column exponents of B
+};
+
+struct OzTile {
+    int prod, m0, n0;
+};
+
 template <int S>
-__global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const __nv_bfloat16* __restrict__ As,
-                                                           const __nv_bfloat16* __restrict__ Bs, int64_t sa,
-                                                           int64_t sb, const int* __restrict__ e,
-                                                           const int* __restrict__ f, int M, int N, int Kp,
-                                                           double* __restrict__ C, int ldc) {
+__global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const OzProd* __restrict__ prods,
+                                                           const OzTile* __restrict__ tiles,
+                                                           const __nv_bfloat16* __restrict__ Aslices,
+                                                           const __nv_bfloat16* __restrict__ Bslices,
+                                                           const int* __restrict__ exps) {
     constexpr int NP = S * (S + 1) / 2;
     constexpr OzPairs<S> PR{};
     extern __shared__ __align__(16) __nv_bfloat16 sm_oz[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
-    const int mt = blockIdx.y * kOzTile, nt = blockIdx.x * kOzTile;
+    const OzTile tl = tiles[blockIdx.x];
+    const OzProd pd = prods[tl.prod];
+    const int M = pd.M, N = pd.N, Kp = pd.Kp, ldc = pd.ldc;
+    const double alpha = pd.alpha;
+    double* __restrict__ C = pd.C;
+    const __nv_bfloat16* As = Aslices + pd.a_off;
+    const __nv_bfloat16* Bs = Bslices + pd.b_off;
+    const int64_t sa = (int64_t)M * Kp, sb = (int64_t)N * Kp;
+    const int* e = exps + pd.e_off;
+    const int* f = exps + pd.f_off;
+    const int mt = tl.m0, nt = tl.n0;
     const int wm = (warp >> 2) * 16, wn = (warp & 3) * 16;
     // staging of the k16 step starting at kk into buffer b
     auto stage = [&](int b, int kk) {
@@ -175,7 +180,7 @@ __global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const __nv_bfloat16* 
     // B rows (columns of B) wn + lane % 8 + (lane / 16) 8, k half (lane / 8) % 2
     const int a_off = (wm + (lane & 15)) * kOzPitch + (lane >> 4) * 8;
     const int b_off = (wn + (lane & 7) + (lane >> 4) * 8) * kOzPitch + ((lane >> 3) & 1) * 8;
-    stage(0, 0);
+    if (nk > 0) stage(0, 0);
     for (int step = 0; step < nk; ++step) {
         if (step + 1 < nk) {
             stage((step + 1) & 1, (step + 1) * 16);
@@ -222,13 +227,13 @@ __global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const __nv_bfloat16* 
         for (int v = 0; v < 4; ++v) {
             const int r = mt + wm + g + (v >= 2 ? 8 : 0);
             const int c = nt + wn + j * 8 + 2 * t + (v & 1);
-            if (r < M && c < N) C[(int64_t)r * ldc + c] = ldexp(ldexp(acc[j][v], e[r]), f[c]);
+            if (r < M && c < N) C[(int64_t)r * ldc + c] = alpha * ldexp(ldexp(acc[j][v], e[r]), f[c]);
         }
 }
 
 template <int S>
-void launch_oz_gemm(Context* ctx, dim3 grid, size_t smem, const __nv_bfloat16* As, const __nv_bfloat16* Bs,
-                    int64_t sa, int64_t sb, const int* e, const int* f, int M, int N, int Kp, double* C, int ldc) {
+void launch_oz_gemm(Context* ctx, int n_tiles, size_t smem, const OzProd* prods, const OzTile* tiles,
+                    const __nv_bfloat16* As, const __nv_bfloat16* Bs, const int* exps) {
     static bool attr = false;
     if (!attr) {
         BSM_CUDA(cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -236,55 +241,76 @@ void launch_oz_gemm(Context* ctx, dim3 grid, size_t smem, const __nv_bfloat16* A
                                       (int)cudaSharedmemCarveoutMaxShared));
         attr = true;
     }
-    k_oz_gemm<S><<<grid, kOzWarps * 32, smem, ctx->stream>>>(As, Bs, sa, sb, e, f, M, N, Kp, C, ldc);
+    k_oz_gemm<S><<<n_tiles, kOzWarps * 32, smem, ctx->stream>>>(prods, tiles, As, Bs, exps);
 }
 
 }  // namespace
 
-void launch_gemm_ozaki(Context* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                       double* C, int ldc, int S) {
-    BSM_REQUIRE(M >= 0 && N >= 0 && K >= 0 && S >= 1 && S <= 8, BSMPS_ERR_INVALID_ARG,
-                "emulated GEMM: sizes >= 0 and 1 <= slices <= 8");
-    if (M == 0 || N == 0) return;
-    const int Kp = (K + 15) / 16 * 16;
+void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S) {
+    BSM_REQUIRE(S >= 1 && S <= kOzMaxS, BSMPS_ERR_INVALID_ARG, "emulated GEMM: 1 <= slices <= 8");
+    std::vector<OzProd> prods;
+    std::vector<OzTile> tiles;
+    int64_t a_tot = 0, b_tot = 0;
+    int ex_tot = 0;
+    double fl = 0.0;
+    for (const OzGemm& g : gs) {
+        BSM_REQUIRE(g.M >= 0 && g.N >= 0 && g.K >= 0, BSMPS_ERR_INVALID_ARG, "emulated GEMM: sizes >= 0");
+        if (g.M == 0 || g.N == 0) continue;
+        const int Kp = (g.K + 15) / 16 * 16;
+        OzProd pd{g.C, g.M, g.N, Kp, g.ldc, g.alpha, a_tot, b_tot, ex_tot, ex_tot + g.M};
+        a_tot += (int64_t)S * g.M * Kp;
+        b_tot += (int64_t)S * g.N * Kp;
+        ex_tot += g.M + g.N;
+        for (int m0 = 0; m0 < g.M; m0 += kOzTile)
+            for (int n0 = 0; n0 < g.N; n0 += kOzTile) tiles.push_back({(int)prods.size(), m0, n0});
+        prods.push_back(pd);
+        fl += 2.0 * g.M * (double)g.N * g.K;
+    }
+    if (prods.empty()) return;
     Scratch s(ctx);
-    int* e = (int*)ctx->alloc(sizeof(int) * (size_t)M);
-    s.ptrs.push_back(e);
-    int* f = (int*)ctx->alloc(sizeof(int) * (size_t)N);
-    s.ptrs.push_back(f);
-    const int64_t sa = (int64_t)M * Kp, sb = (int64_t)N * Kp;
-    __nv_bfloat16* As = (__nv_bfloat16*)ctx->alloc(sizeof(__nv_bfloat16) * (size_t)(sa * S + 2));
+    __nv_bfloat16* As = (__nv_bfloat16*)ctx->alloc(sizeof(__nv_bfloat16) * (size_t)(a_tot + 8));
     s.ptrs.push_back(As);
-    __nv_bfloat16* Bs = (__nv_bfloat16*)ctx->alloc(sizeof(__nv_bfloat16) * (size_t)(sb * S + 2));
+    __nv_bfloat16* Bs = (__nv_bfloat16*)ctx->alloc(sizeof(__nv_bfloat16) * (size_t)(b_tot + 8));
     s.ptrs.push_back(Bs);
-    if (K == 0) {
-        for (int r = 0; r < M; ++r) BSM_CUDA(cudaMemsetAsync(C + (int64_t)r * ldc, 0, sizeof(double) * N, ctx->stream));
-        return;
+    int* exps = (int*)ctx->alloc(sizeof(int) * (size_t)ex_tot);
+    s.ptrs.push_back(exps);
+    // rows of op(A) and columns of B, with their exponent slots and slice rows
+    std::vector<OzRow> rows;
+    size_t pi = 0;
+    for (const OzGemm& g : gs) {
+        if (g.M == 0 || g.N == 0) continue;
+        const OzProd& pd = prods[pi++];
+        for (int r = 0; r < g.M; ++r)
+            rows.push_back({g.transA ? g.A + r : g.A + (int64_t)r * g.lda, g.transA ? (int64_t)g.lda : 1, g.K, pd.Kp,
+                            exps + pd.e_off + r, As + pd.a_off + (int64_t)r * pd.Kp, (int64_t)g.M * pd.Kp});
+        for (int c = 0; c < g.N; ++c)
+            rows.push_back({g.B + c, (int64_t)g.ldb, g.K, pd.Kp, exps + pd.f_off + c, Bs + pd.b_off + (int64_t)c * pd.Kp,
+                            (int64_t)g.N * pd.Kp});
     }
-    k_oz_row_exp<<<(M + 7) / 8, 256, 0, ctx->stream>>>(A, M, K, lda, e);
+    const OzRow* d_rows = s.up(rows);
+    const OzProd* d_prods = s.up(prods);
+    const OzTile* d_tiles = s.up(tiles);
+    k_oz_rows<<<((int)rows.size() + 7) / 8, 256, 0, ctx->stream>>>(d_rows, (int)rows.size(), S);
     launched(ctx);
-    k_oz_col_exp<<<(N + 127) / 128, 128, 0, ctx->stream>>>(B, K, N, ldb, f);
-    launched(ctx);
-    const int blocks_a = (int)std::min<int64_t>((sa + 255) / 256, 152 * 16);
-    k_oz_split<<<blocks_a, 256, 0, ctx->stream>>>(A, M, K, lda, 0, e, S, Kp, As, sa);
-    launched(ctx);
-    const int blocks_b = (int)std::min<int64_t>((sb + 255) / 256, 152 * 16);
-    k_oz_split<<<blocks_b, 256, 0, ctx->stream>>>(B, K, N, ldb, 1, f, S, Kp, Bs, sb);
-    launched(ctx);
-    dim3 grid((N + kOzTile - 1) / kOzTile, (M + kOzTile - 1) / kOzTile);
     const size_t smem = sizeof(__nv_bfloat16) * 2 * (size_t)kOzStage;
+    const int nt = (int)tiles.size();
     switch (S) {
-        case 1: launch_oz_gemm<1>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
-        case 2: launch_oz_gemm<2>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
-        case 3: launch_oz_gemm<3>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
-        case 4: launch_oz_gemm<4>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
-        case 5: launch_oz_gemm<5>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
-        case 6: launch_oz_gemm<6>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
-        case 7: launch_oz_gemm<7>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
-        default: launch_oz_gemm<8>(ctx, grid, smem, As, Bs, sa, sb, e, f, M, N, Kp, C, ldc); break;
+        case 1: launch_oz_gemm<1>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
+        case 2: launch_oz_gemm<2>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
+        case 3: launch_oz_gemm<3>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
+        case 4: launch_oz_gemm<4>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
+        case 5: launch_oz_gemm<5>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
+        case 6: launch_oz_gemm<6>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
+        case 7: launch_oz_gemm<7>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
+        default: launch_oz_gemm<8>(ctx, nt, smem, d_prods, d_tiles, As, Bs, exps); break;
     }
     launched(ctx);
-    ctx->flops += 2.0 * M * (double)N * K;
+    ctx->flops += fl;
+}
+
+void launch_gemm_ozaki(Context* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                       double* C, int ldc, int S, int transA, double alpha) {
+    launch_gemm_ozaki_group(ctx, {OzGemm{A, B, C, M, N, K, lda, ldb, ldc, transA, alpha}}, S);
 }
 
 }  // namespace bsm

@@ -137,6 +137,7 @@ _SIGS = {
     "bsmps_eigensolve_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
                                    C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(StepInfo)]),
     "bsmps_gemm_ozaki": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _i, _vp, _i, _i]),
+    "bsmps_ctx_set_gemm_emulation": (_i, [_vp, _i]),
     "bsmps_mps_joint_random_size": (_i, [_i, _i, _i, _i, _i, _i, _pi64]),
     "bsmps_mps_create_joint": (_i, [_vp, _i, _i, _i, _i, _i, _i, C.POINTER(C.c_ubyte), _i, _pd, _i64,
                                     C.POINTER(_vp)]),
@@ -203,6 +204,11 @@ class Context:
         return int(lib().bsmps_ctx_launch_count(self.h))
 
     KERNELS = ("copy", "gemm", "qr", "svd", "sumsq")
+
+    def set_gemm_emulation(self, min_log2_flops=0):
+        """Block products of at least 2^min_log2_flops flops on the tensor cores
+        (0: none), see bsmps_ctx_set_gemm_emulation."""
+        _check(self, lib().bsmps_ctx_set_gemm_emulation(self.h, int(min_log2_flops)))
 
     def profile(self, enable=True):
         _check(self, lib().bsmps_ctx_profile(self.h, 1 if enable else 0))

@@ -75,3 +75,31 @@ def test_truncate_with_wide_sector_svds(nat, ctx, eps_rel):
 
 def to_oracle_k(z, species, N):
     return OB.BSMPS.from_flat(species, (N, 0), z.bonds(), z.export())
+
+
+@pytest.mark.parametrize("min_log2", [16, 0])
+def test_truncate_with_emulated_block_products(nat, ctx, min_log2):
+    """Sectors of up to 560 rows (K = 12, N = 6, r = 24, exact apply), with the
+    emulation threshold lowered to 2^16 flops so that the sweeps' block products
+    run on the tensor cores (0: all on the FP64 units); both match the oracle."""
+    wl = spinless_random_chain(K=12, N=6, seed=1)
+    r = 24
+    W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, wl.spin, wl.n_particles, 0.0)
+    vals = random_block_values(n_random(wl, r), 3)
+    x = nat.mps_create(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, r, vals)
+    ctx.set_gemm_emulation(min_log2)
+    try:
+        y, _ = nat.apply_H(ctx, W, x)
+        oy = OB.apply_exact(oracle_mpo(wl, 0.0), oracle_random(wl, r, vals))
+        assert max(max(b.values()) for b in oy.bonds if b) > 500
+        nrm = float(np.sqrt(OB.dot(oy, oy)))
+        for eps_rel in (1e-4, 1e-10):
+            z, dt, _ = nat.truncate(ctx, y, eps_rel * nrm)
+            oz, odt, _ = OB.truncate(oy, eps_rel * nrm)
+            assert z.bonds() == oz.bonds
+            gz = OB.dot(to_oracle(wl, z), to_oracle(wl, z))
+            assert abs(gz - OB.dot(oz, oz)) <= 1e-12 * OB.dot(oz, oz)
+            d = OB.add(to_oracle(wl, z), oy, 1.0, -1.0)
+            assert np.sqrt(max(OB.dot(d, d), 0.0)) <= eps_rel * nrm * (1 + 1e-6) + 1e-12 * nrm
+    finally:
+        ctx.set_gemm_emulation(0)
