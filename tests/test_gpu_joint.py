@@ -197,3 +197,30 @@ def test_joint_iteration_reaches_exact_eigenvalues(nat, ctx):
     ox = to_oracle(wl, x)
     GA = OJ.gram_sums(ox, ox, prec, oracle_mpo(wl, gamma))
     assert np.abs(GA - np.eye(D)).max() < 1e-9
+
+
+def test_joint_error_paths(nat, ctx):
+    """Calls that need one column reject joint MPS; the joint step rejects more
+    than BSMPS_MAX_COLUMNS columns; occupations outside the sector are rejected."""
+    wl = spinless_random_chain(K=6, N=3, seed=4)
+    gamma, th, prec, c, delta, W, p = _solver_setup(nat, ctx, wl)
+    x, _ = joint_pair(nat, ctx, wl, 6, 3, 31)
+    with pytest.raises(nat.BsmpsError) as e:
+        nat.dot(ctx, x, x)
+    assert "INVALID_ARG" in str(e.value)
+    with pytest.raises(nat.BsmpsError):
+        nat.eigensolve_step(ctx, W, p, nat.solver_params(c, delta), nat.solver_state(), x)
+    # the rejected step left the handle alive
+    assert nat.num_columns(x) == 3
+    big, _ = joint_pair(nat, ctx, wl, 20, nat.MAX_COLUMNS + 1, 32)
+    with pytest.raises(nat.BsmpsError):
+        nat.eigensolve_joint_step(ctx, W, p, nat.solver_params(c, delta), nat.solver_state(), big)
+    bad = np.zeros((1, 6), dtype=np.uint8)
+    bad[0, :2] = 1                     # two particles where three are required
+    with pytest.raises(nat.BsmpsError) as e:
+        nat.mps_create_joint(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, 1, occ=bad)
+    assert "CHARGE" in str(e.value)
+    # a Gram matrix of a joint MPS with itself is symmetric positive definite
+    G = nat.gram(ctx, x, x)
+    assert np.allclose(G, G.T, rtol=0, atol=1e-12 * np.abs(G).max())
+    assert np.linalg.eigvalsh(G).min() > 0
