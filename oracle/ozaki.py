@@ -2,8 +2,8 @@
 Ozaki scheme: Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
 multiplication by using fast routines of matrix multiplication and its
 applications", Numer. Algorithms 59 (2012); integer-slice form as in Uchino,
-Ozaki, Imamura 2024).  Not part of the paper; the survey's NEXT item for the
-FP64 contractions of the solver.
+Ozaki, Imamura 2024).  Not part of the paper: an FP64 path on tensor cores for
+the contractions of the solver.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 

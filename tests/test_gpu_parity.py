@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, through the C ABI.
 
-Tolerances (spec: energies 1e-10 relative, block Frobenius norms 1e-12
+Tolerances (required: energies 1e-10 relative, block Frobenius norms 1e-12
 relative, block structure bit-exact):
 * index / structure: bit-exact;
 * exact application and block copies: 1e-14 relative per element (a single
