@@ -95,17 +95,19 @@ constexpr int kOzWarps = 16;                                // 4 x 4 warp tiles 
 // one FP32 accumulator per d, flushed to FP64 every kOzChunk values of k.
 // Fragment layouts of m16n8k16 (g = lane / 4, t = lane % 4): C rows g, g+8,
 // columns 2t, 2t+1.
-// Slice pairs (p, q), p + q <= S + 1, in order of d = p + q: pair i of the
-// flattened list.
+// Slice pairs (p, q), p + q <= S + 1, ordered by p then q: consecutive pairs
+// accumulate into different d = p + q (independent tensor-core chains) and share
+// the fragment of A_p.  abuf: which of two A fragment registers holds A_p.
 template <int S>
 struct OzPairs {
-    int p[S * (S + 1) / 2], q[S * (S + 1) / 2];
-    constexpr OzPairs() : p(), q() {
+    int p[S * (S + 1) / 2], q[S * (S + 1) / 2], abuf[S * (S + 1) / 2];
+    constexpr OzPairs() : p(), q(), abuf() {
         int i = 0;
-        for (int d = 2; d <= S + 1; ++d)
-            for (int pp = 1; pp <= d - 1; ++pp) {
+        for (int pp = 1; pp <= S; ++pp)
+            for (int qq = 1; pp + qq <= S + 1; ++qq) {
                 p[i] = pp;
-                q[i] = d - pp;
+                q[i] = qq;
+                abuf[i] = (pp - 1) & 1;
                 ++i;
             }
     }
@@ -190,20 +192,22 @@ __global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const OzProd* __restr
         }
         __syncthreads();
         const __nv_bfloat16* base = sm_oz + (step & 1) * kOzStage;
-        // fragments of pair i + 1 are loaded before the products of pair i
+        // fragments of pair i + 1 are loaded before the products of pair i; the
+        // fragment of A_p is loaded once per p
         unsigned a[2][4], b[2][4];
-        ldsm_x4(a[0], base + (PR.p[0] - 1) * kOzTile * kOzPitch + a_off);
+        ldsm_x4(a[PR.abuf[0]], base + (PR.p[0] - 1) * kOzTile * kOzPitch + a_off);
         ldsm_x4(b[0], base + (kOzMaxS + PR.q[0] - 1) * kOzTile * kOzPitch + b_off);
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            const int cur = i & 1, nxt = cur ^ 1;
+            const int bc = i & 1, ac = PR.abuf[i];
             if (i + 1 < NP) {
-                ldsm_x4(a[nxt], base + (PR.p[i + 1] - 1) * kOzTile * kOzPitch + a_off);
-                ldsm_x4(b[nxt], base + (kOzMaxS + PR.q[i + 1] - 1) * kOzTile * kOzPitch + b_off);
+                if (PR.p[i + 1] != PR.p[i])
+                    ldsm_x4(a[PR.abuf[i + 1]], base + (PR.p[i + 1] - 1) * kOzTile * kOzPitch + a_off);
+                ldsm_x4(b[bc ^ 1], base + (kOzMaxS + PR.q[i + 1] - 1) * kOzTile * kOzPitch + b_off);
             }
             const int d = PR.p[i] + PR.q[i] - 2;
-            mma_bf16(c32[d][0], a[cur][0], a[cur][1], a[cur][2], a[cur][3], b[cur][0], b[cur][1]);
-            mma_bf16(c32[d][1], a[cur][0], a[cur][1], a[cur][2], a[cur][3], b[cur][2], b[cur][3]);
+            mma_bf16(c32[d][0], a[ac][0], a[ac][1], a[ac][2], a[ac][3], b[bc][0], b[bc][1]);
+            mma_bf16(c32[d][1], a[ac][0], a[ac][1], a[ac][2], a[ac][3], b[bc][2], b[bc][3]);
         }
         // exact FP32 sums cover at most kOzChunk values of k: flush to FP64
         if ((step + 1) % (kOzChunk / 16) == 0 || step + 1 == nk) {
