@@ -84,9 +84,10 @@ __device__ __forceinline__ void cp16(void* smem, const void* gmem, int src_bytes
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(a), "l"(gmem), "r"(src_bytes));
 }
 
-constexpr int kOzPitch = 24;                                // bf16 per staged row (48 B: ldmatrix rows on distinct banks)
+constexpr int kOzKStep = 32;                                // values of k per staged buffer (two k16 steps)
+constexpr int kOzPitch = 40;                                // bf16 per staged row (80 B: ldmatrix rows on distinct banks)
 constexpr int kOzMaxS = 8;
-constexpr int kOzStage = 2 * kOzMaxS * kOzTile * kOzPitch;  // bf16 of A and B slices for one k16 step
+constexpr int kOzStage = 2 * kOzMaxS * kOzTile * kOzPitch;  // bf16 of A and B slices for one staged step
 constexpr int kOzWarps = 16;                                // 4 x 4 warp tiles of 16 x 16
 
 // C (M x N, row-major, ldc) = sum_d 2^{e_i + f_j - 7d} sum_{p + q = d} A_p B_q.
@@ -149,18 +150,19 @@ __global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const OzProd* __restr
     const int* f = exps + pd.f_off;
     const int mt = tl.m0, nt = tl.n0;
     const int wm = (warp >> 2) * 16, wn = (warp & 3) * 16;
-    // staging of the k16 step starting at kk into buffer b
+    // staging of the kOzKStep values of k starting at kk into buffer b
+    constexpr int kChunks = kOzKStep / 8;   // 16-byte pieces per staged row
     auto stage = [&](int b, int kk) {
         __nv_bfloat16* base = sm_oz + b * kOzStage;
-        constexpr int n_copies = 2 * S * kOzTile * 2;
+        constexpr int n_copies = 2 * S * kOzTile * kChunks;
         for (int i = tid; i < n_copies; i += kOzWarps * 32) {
-            const int which = i / (S * kOzTile * 2);            // 0: A, 1: B
-            const int rem = i - which * S * kOzTile * 2;
-            const int p = rem / (kOzTile * 2), r = (rem >> 1) % kOzTile, half = rem & 1;
+            const int which = i / (S * kOzTile * kChunks);            // 0: A, 1: B
+            const int rem = i - which * S * kOzTile * kChunks;
+            const int p = rem / (kOzTile * kChunks), r = (rem / kChunks) % kOzTile, piece = rem % kChunks;
             const int row = (which ? nt : mt) + r;
             const bool ok = row < (which ? N : M);
-            const __nv_bfloat16* src = (which ? Bs + p * sb : As + p * sa) + (ok ? (int64_t)row * Kp + kk + half * 8 : 0);
-            __nv_bfloat16* dst = base + ((which * kOzMaxS + p) * kOzTile + r) * kOzPitch + half * 8;
+            const __nv_bfloat16* src = (which ? Bs + p * sb : As + p * sa) + (ok ? (int64_t)row * Kp + kk + piece * 8 : 0);
+            __nv_bfloat16* dst = base + ((which * kOzMaxS + p) * kOzTile + r) * kOzPitch + piece * 8;
             cp16(dst, src, ok ? 16 : 0);
         }
         asm volatile("cp.async.commit_group;\n" ::);
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const OzProd* __restr
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int v = 0; v < 4; ++v) c32[d][j][v] = 0.f;
-    const int nk = Kp / 16;
+    const int nk = Kp / kOzKStep;
     // ldmatrix row addresses: A rows wm + lane % 16, k half lane / 16;
     // B rows (columns of B) wn + lane % 8 + (lane / 16) 8, k half (lane / 8) % 2
     const int a_off = (wm + (lane & 15)) * kOzPitch + (lane >> 4) * 8;
@@ -185,13 +187,15 @@ __global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const OzProd* __restr
     if (nk > 0) stage(0, 0);
     for (int step = 0; step < nk; ++step) {
         if (step + 1 < nk) {
-            stage((step + 1) & 1, (step + 1) * 16);
+            stage((step + 1) & 1, (step + 1) * kOzKStep);
             asm volatile("cp.async.wait_group 1;\n" ::);
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::);
         }
         __syncthreads();
-        const __nv_bfloat16* base = sm_oz + (step & 1) * kOzStage;
+#pragma unroll 1
+        for (int kh = 0; kh < kOzKStep / 16; ++kh) {
+        const __nv_bfloat16* base = sm_oz + (step & 1) * kOzStage + kh * 16;
         // fragments of pair i + 1 are loaded before the products of pair i; the
         // fragment of A_p is loaded once per p
         unsigned a[2][4], b[2][4];
@@ -209,8 +213,9 @@ __global__ void __launch_bounds__(kOzWarps * 32) k_oz_gemm(const OzProd* __restr
             mma_bf16(c32[d][0], a[ac][0], a[ac][1], a[ac][2], a[ac][3], b[bc][0], b[bc][1]);
             mma_bf16(c32[d][1], a[ac][0], a[ac][1], a[ac][2], a[ac][3], b[bc][2], b[bc][3]);
         }
+        }
         // exact FP32 sums cover at most kOzChunk values of k: flush to FP64
-        if ((step + 1) % (kOzChunk / 16) == 0 || step + 1 == nk) {
+        if ((step + 1) % (kOzChunk / kOzKStep) == 0 || step + 1 == nk) {
 #pragma unroll
             for (int d = 0; d < S; ++d) {
                 const double w = ldexp(1.0, -7 * (d + 2));
@@ -260,7 +265,7 @@ void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S)
     for (const OzGemm& g : gs) {
         BSM_REQUIRE(g.M >= 0 && g.N >= 0 && g.K >= 0, BSMPS_ERR_INVALID_ARG, "emulated GEMM: sizes >= 0");
         if (g.M == 0 || g.N == 0) continue;
-        const int Kp = (g.K + 15) / 16 * 16;
+        const int Kp = (g.K + kOzKStep - 1) / kOzKStep * kOzKStep;
         OzProd pd{g.C, g.M, g.N, Kp, g.ldc, g.alpha, a_tot, b_tot, ex_tot, ex_tot + g.M};
         a_tot += (int64_t)S * g.M * Kp;
         b_tot += (int64_t)S * g.N * Kp;
