@@ -342,9 +342,9 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
     double fl = 0.0, by = 0.0;
     for (int o = 0; o < (int)outs.size(); ++o) {
         const GemmOut& g = outs[o];
-        // outputs of at least 2^gemm_emulation_log2 flops with one contribution
-        // (overwritten) go to the tensor-core FP64 emulation
-        if (ctx->gemm_emulation_log2 > 0 && g.end == g.beg + 1 && g.beta == 0.0 &&
+        // outputs of at least 2^gemm_emulation_log2 flops with one untransposed
+        // contribution (overwritten) go to the tensor-core FP64 emulation
+        if (ctx->gemm_emulation_log2 > 0 && g.end == g.beg + 1 && g.beta == 0.0 && !ins[g.beg].transA &&
             2.0 * g.M * (double)g.N * ins[g.beg].K >= std::ldexp(1.0, ctx->gemm_emulation_log2)) {
             emulated.push_back(o);
             continue;

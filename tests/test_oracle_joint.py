@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import bsmps as B
+from oracle import fermion as OF
 from oracle import joint as J
 from oracle import pinvit as PI
 from tests.test_oracle_pinvit import small_problem
@@ -172,3 +173,35 @@ def test_joint_iteration_reaches_the_lowest_eigenvalues(joint_run):
     # the returned columns are A-orthonormal
     GA = J.gram_sums(x, x, prob["prec"], prob["mpo"])
     assert np.abs(GA - np.eye(3)).max() < 1e-10
+
+
+def test_joint_iteration_spinful_hubbard():
+    """Alg. 4 with two spin species (Hubbard L = 3, (n_up, n_dn) = (2, 1), D = 2)
+    from the two lowest determinants: Ritz values above the exact eigenvalues at
+    every step, and the first one certified by the bound at convergence."""
+    from oracle import mpo as M
+    from oracle import precond as P
+    from synth import hubbard_chain
+    wl = hubbard_chain(L=3, n_up=2, n_dn=1, U=2.0)
+    H0, _ = OF.sector_hamiltonian(wl.h, wl.eri, 1, 2, 1)
+    ev0 = np.linalg.eigvalsh(H0)
+    gamma = 0.5 - ev0[0]
+    lam = ev0 + gamma
+    species = OF.site_species(3, 1)
+    t_so, v_so = P.spin_orbital_accessors(wl.h, wl.eri, 1)
+    th = P.theta_diag(t_so, v_so, 3, gamma, 6)
+    tmin, tmax = P.spectrum_bounds(th, species, (2, 1))
+    prec = P.Preconditioner(th, tmin, tmax, 0.1, 0.6)
+    mpo = M.build_mpo(wl.h, wl.eri, 1, 3, gamma)
+    delta = lam[1] / (lam[1] - lam[0])
+    params = PI.SolverParams(0.6, delta, tau=1e-8)
+    x = J.from_determinants(species, (2, 1), J.lowest_determinants(species, (2, 1), np.repeat(np.diag(wl.h), 2), 2))
+    st = PI.SolverState()
+    for _ in range(80):
+        x, info = J.step(x, mpo, prec, params, st)
+        assert np.all(info["lambda"] >= lam[:2] - 1e-12 * lam[:2])
+        if info["converged"]:
+            break
+    assert info["converged"]
+    assert (info["lambda"][0] - lam[0]) / lam[0] <= info["releig_bound"] * (1 + 1e-6) + 1e-13
+    assert abs(info["lambda"][1] - lam[1]) <= 1e-4 * lam[1]
