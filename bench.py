@@ -148,12 +148,11 @@ def oracle_steps(n_steps, L=32, r_max=256):
     from oracle import mpo as OM
     from oracle import pinvit as OPI
     from oracle import precond as OP
-    from paper_2604_16118_gb300 import problem
     from synth import hubbard_chain
     prm = load_params(L)
     wl = hubbard_chain(L=L, r_max=r_max)
     n = L // 2
-    gamma = problem.hubbard_shift(wl.h, n, n, margin=1.0)
+    gamma = 1.0 - OP.energy_lower_bound(wl.h, wl.eri, 1, n, n, cholesky=False)
     W = OM.build_mpo(wl.h, wl.eri, 1, 2 * n, gamma)
     t_so, v_so = OP.spin_orbital_accessors(wl.h, wl.eri, 1)
     species = OF.site_species(L, 1)

@@ -154,6 +154,9 @@ BSMPS_API bsmps_status bsmps_ctx_sync(bsmps_ctx ctx);
 BSMPS_API const char* bsmps_last_error(bsmps_ctx ctx);
 /* Number of kernel launches issued by the context so far. */
 BSMPS_API int64_t bsmps_ctx_launch_count(bsmps_ctx ctx);
+/* Number of device-memory requests the context's allocator has served so far
+ * (from its cache or from the stream-ordered pool). */
+BSMPS_API int64_t bsmps_ctx_alloc_count(bsmps_ctx ctx);
 
 /* Kernel profiler.  enable != 0 brackets every launch with CUDA events on the
  * context stream and records its kind and algorithmic flops / bytes (this
@@ -175,6 +178,57 @@ BSMPS_API bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset
  * *timed_out = 1; the context stays usable.  Errors: INVALID_ARG (skip_cta >
  * 1), CUDA. */
 BSMPS_API bsmps_status bsmps_check_grid_wait(bsmps_ctx ctx, int skip_cta, int* timed_out);
+
+/* ---- problem set-up (host only, no device needed) ----------------------- */
+
+/* theta[i] = gamma/N + t_ii + sum_{j=k_i+1}^{k_i+N} (v_ijji - v_ijij),
+ * k_i = max(0, i - N) (1-based i, j; Sec. 7.1.1): the diagonal coefficients
+ * d_i of D = sum_i d_i a_i^* a_i that the preconditioner approximates
+ * D^{-1/2} of.  N = n_particles; the spin-orbital integrals are
+ * t_{p s, q s'} = h_pq delta_ss' and v_ijkl = 1/2 (il|jk) with matching spins
+ * (Eq. (tvdef)).  h: n_orb x n_orb row-major; eri: (pq|rs) chemist order,
+ * n_orb^4 row-major; theta: K = n_orb (spin = 0) or 2 n_orb (spin = 1)
+ * entries, written.  Errors: INVALID_ARG. */
+BSMPS_API bsmps_status bsmps_precond_theta(int n_orb, const double* h, const double* eri, int spin,
+                                           int n_particles, double gamma, double* theta);
+
+/* [t_min, t_max] enclosing the spectrum of D on the sector (Sec. 4.3, Cor.
+ * lrprecond).  Per species s with n_s particles: when h is given and the
+ * one-body diagonal h_pp increases strictly along that species' sites (the
+ * orbital basis of the paper's Sec. 7.2, where t_min is D at e_1), the sums of
+ * theta over the species' first / last n_s sites; otherwise the sums of the
+ * n_s smallest / largest theta (the exact range of the spectrum of D).
+ * theta: K entries; h: n_orb x n_orb or NULL.  Errors: INVALID_ARG, CHARGE. */
+BSMPS_API bsmps_status bsmps_precond_interval(int n_orb, int spin, const double* theta, const double* h,
+                                              int n_up, int n_dn, double* t_min, double* t_max);
+
+/* A rigorous lower bound e_lb of the ground energy, for a shift
+ * gamma = margin - e_lb that makes H_gamma = H + gamma I positive definite
+ * (Sec. 3.1).  cholesky = 0: the interaction is nonnegative (on-site U >= 0),
+ * e_lb is the ground energy of the one-body part.  cholesky = 1: (pq|rs) is
+ * positive semidefinite (a sum of products of symmetric Cholesky vectors), and
+ * normal ordering gives H >= the one-body operator h_pq - 1/2 sum_r (pr|rq).
+ * The ground energy of a one-body operator is the sum of the n_up (and, with
+ * spin = 1, n_dn) lowest eigenvalues of its matrix.  eri may be NULL when
+ * cholesky = 0.  Errors: INVALID_ARG. */
+BSMPS_API bsmps_status bsmps_energy_lower_bound(int n_orb, const double* h, const double* eri, int spin,
+                                                int n_up, int n_dn, int cholesky, double* e_lb);
+
+/* alpha_0 of Eq. (Sdef) and the spectral equivalence constant c of Eq.
+ * (precondcdef) from c0 (Thm. expsum), t_min and C_lower, C_upper of Eq.
+ * (lowerupper).  Errors: INVALID_ARG (c0 outside (0, 1), t_min <= 0, or
+ * C_lower, C_upper not positive). */
+BSMPS_API bsmps_status bsmps_precond_alpha0(double c0, double t_min, double c_lower, double c_upper,
+                                            double* alpha0, double* c);
+
+/* The D occupation strings (occ: D x K bytes, written; row i = determinant
+ * i) of smallest one-particle energy sum_{i occupied} t_diag[i], the start
+ * e_1, ..., e_D of the subspace iteration (Sec. 7.1.4).  Ties: strings
+ * compared from site 0, occupied first (so the first is e_1 when t_diag
+ * increases).  The sector is enumerated.  Errors: INVALID_ARG (sector
+ * smaller than D), CHARGE, RANK_CAP (more than max_configs strings). */
+BSMPS_API bsmps_status bsmps_lowest_determinants(int K, const double* t_diag, int spin, int n_up, int n_dn,
+                                                 int D, int64_t max_configs, unsigned char* occ);
 
 /* ---- MPS ----------------------------------------------------------------- */
 
@@ -334,8 +388,9 @@ BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const b
  * A (M x K, leading dimension lda), B (K x N, ldb) and C (M x N, ldc) are
  * row-major DEVICE pointers.  The work is ordered on the context stream and the
  * call does not synchronise.  Errors: INVALID_ARG, OOM, CUDA. */
-/* Block products of at least 2^min_log2_flops flops with a single contribution
- * (the large R X and U S X products of sweeps over wide sectors) run as
+/* Block products of at least 2^min_log2_flops flops with a single untransposed
+ * contribution (the large R X and U S X products of sweeps over wide sectors;
+ * transposed products stay on the FP64 units) run as
  * bsmps_gemm_ozaki with 8 slices, all such products of one grouped launch
  * together; 0 (the default) keeps every product on the FP64 units.  The
  * emulation's error is relative to row and column maxima, so on graded factors

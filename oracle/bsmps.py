@@ -573,3 +573,97 @@ def truncate(x, eps, r_max=0):
                     y.cores[t - 1][(pn, psg)] = y.cores[t - 1][(pn, psg)] @ US
         _set_bond(y, t, newdims)
     return y, float(np.sqrt(tot_tol)), float(np.sqrt(tot_cap))
+
+
+def _exact_segments(mpo, x):
+    """Per bond b and valid sector m of y = (H + s) x: the channel segments
+    [(a, n, offset, rho_x(n))] of y's exact basis (channel-major, n = m - Delta_a)
+    and its total dimension (Sec. 2.4; the bond basis of apply_exact)."""
+    K = x.K
+    ranges = valid_ranges(x.species, x.target)
+    segs = []
+    for b in range(K + 1):
+        seg = {}
+        for m in ranges[b]:
+            lst = []
+            off = 0
+            for a, d in enumerate(mpo.charges[b]):
+                n = sub_charge(m, d)
+                if n in x.bonds[b]:
+                    lst.append((a, n, off, x.bonds[b][n]))
+                    off += x.bonds[b][n]
+            if off > 0:
+                seg[m] = (lst, off)
+        segs.append(seg)
+    return segs
+
+
+def apply_zipup(mpo, x, shift=0.0):
+    """y = (H + shift I) x in left-orthogonal form, contracted site by site
+    (Sec. 2.4 with the left-to-right QR sweep of Sec. 2.3) without forming the
+    exact cores of apply_exact.
+
+    The carry C_t[m] (rho_y(m) x rho_exact(m)) maps y's orthogonalised bond-t
+    basis to the exact basis (channel a, x's sector n = m - Delta_a).  At site t
+        T[(m, s')][:, seg_b] = sum_{(a, s): W_t(a, b, s', s) != 0}
+                               w C_t[m][:, seg_a] X_t(n_a, s),
+    and for every sector m' of bond t+1 the blocks (m, s') with m + delta(s') = m'
+    are stacked in layout order (m ascending, then s') and factorised S = Q R:
+    Q gives y's core-t blocks, R = C_{t+1}[m'].  A stack with no more rows than
+    columns takes Q = I, R = S (an exact orthogonalisation; its rank is the row
+    count); otherwise Householder QR with diag(R) >= 0.  At the last site the
+    blocks T are y's last core.  Equal to left_orthogonalize(apply_exact(...))
+    in exact arithmetic up to the gauge of the bond bases."""
+    K = x.K
+    segs = _exact_segments(mpo, x)
+    C = {m: np.eye(v[1]) for m, v in segs[0].items()}
+    bonds = [{m: v[1] for m, v in segs[0].items()}]
+    cores = []
+    for t in range(K):
+        sp = x.species[t]
+        ents = mpo.entries(t, shift)
+        T = {}
+        for m in sorted(C):
+            Cm = C[m]
+            rowseg = {a: (n, off, d) for (a, n, off, d) in segs[t][m][0]}
+            for so in (0, 1):
+                m2 = add_charge(m, delta(sp, so))
+                if m2 not in segs[t + 1]:
+                    continue
+                colseg = {b: (n, off, d) for (b, n, off, d) in segs[t + 1][m2][0]}
+                Tb = np.zeros((Cm.shape[0], segs[t + 1][m2][1]))
+                for (a, b, eo, ei, w) in ents:
+                    if eo != so or a not in rowseg or b not in colseg:
+                        continue
+                    n_a, r0, rd = rowseg[a]
+                    _, c0, cd = colseg[b]
+                    if (n_a, ei) not in x.cores[t]:
+                        continue
+                    Tb[:, c0:c0 + cd] += w * (Cm[:, r0:r0 + rd] @ x.cores[t][(n_a, ei)])
+                T[(m, so)] = Tb
+        if t == K - 1:
+            cores.append(T)
+            bonds.append({m: v[1] for m, v in segs[K].items()})
+            break
+        core = {}
+        newC = {}
+        for m2 in sorted(segs[t + 1]):
+            keys = [(m, so) for (m, so) in sorted(T) if add_charge(m, delta(sp, so)) == m2]
+            if not keys:
+                continue
+            S = np.vstack([T[k] for k in keys])
+            rows, cols = S.shape
+            if rows <= cols:
+                Q, R = np.eye(rows), S
+            else:
+                Q, R = _sign_fix_qr(*np.linalg.qr(S, mode="reduced"))
+            r0 = 0
+            for k in keys:
+                rr = T[k].shape[0]
+                core[k] = Q[r0:r0 + rr, :]
+                r0 += rr
+            newC[m2] = R
+        cores.append(core)
+        bonds.append({m2: R.shape[0] for m2, R in sorted(newC.items())})
+        C = newC
+    return BSMPS(x.species, x.target, bonds, cores)

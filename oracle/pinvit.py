@@ -13,8 +13,9 @@ Readings of the paper used here:
 * Residual terms s_{k,k'} = S_k (H_gamma - lambda) S_{k'} x are formed from
   u_{k'} = (H_gamma - lambda) S_{k'} x, applied exactly and then compressed
   once with trunc at U_REL ||u_{k'}|| (U_REL = 1e-13, far below any eta_res
-  the iteration reaches, so the terms stay exact to working precision); ties in
-  the norm sort are broken by (k, k') ascending.
+  the iteration reaches, so the terms stay exact to working precision; U_REL = 0
+  keeps the exactly applied terms); ties in the norm sort are broken by (k, k')
+  ascending.
 * The iterate truncation x^{n+1} = trunc_{eta_in}(x*) is capped at r_max ranks
   when r_max > 0 (the workload's maximal MPS rank); the cap's discarded norm
   is reported separately.
@@ -80,7 +81,8 @@ def residual_terms(x, lam, prec, mpo):
     for kp in range(prec.n_terms):
         f0, f1 = prec.factors(kp)
         u = B.apply_exact(mpo, B.scale_sites(x, f0, f1), shift=-lam)
-        u, _, _ = B.truncate(u, U_REL * B.norm(u))
+        if U_REL > 0.0:
+            u, _, _ = B.truncate(u, U_REL * B.norm(u))
         for k in range(prec.n_terms):
             g0, g1 = prec.factors(k)
             s = B.scale_sites(u, g0, g1)

@@ -139,3 +139,28 @@ class Preconditioner:
         occ = np.asarray(occupations, dtype=np.float64)
         Dv = occ @ self.d
         return self.alpha0 * expsum(Dv / self.t_min, self.h, self.m_minus, self.m_plus)
+
+
+def energy_lower_bound(h, eri, spin, n_up, n_dn, cholesky):
+    """A rigorous lower bound E_lb of the ground energy, for the shift
+    gamma = margin - E_lb that makes H_gamma positive definite (Sec. 3.1).
+
+    * On-site interactions U >= 0 (cholesky False): the interaction is
+      nonnegative, so H >= the one-body part and E_lb is its ground energy.
+    * (pq|rs) = sum_g L^g_pq L^g_rs positive semidefinite (cholesky True):
+      normal ordering gives V = 1/2 sum_g (sum_pq L^g_pq a_p^* a_q)^2
+      - 1/2 sum_pq (sum_r (pr|rq)) a_p^* a_q, so H >= the one-body operator with
+      matrix h_pq - 1/2 sum_r (pr|rq).
+    The ground energy of a one-body operator with n_s particles of species s is
+    the sum of the n_s lowest eigenvalues of its matrix, per species (both
+    species see the spatial matrix when spin = 1)."""
+    hh = np.array(h, dtype=np.float64)
+    if cholesky:
+        n = hh.shape[0]
+        for p in range(n):
+            for q in range(n):
+                hh[p, q] -= 0.5 * sum(eri[p, r, r, q] for r in range(n))
+    ev = np.sort(np.linalg.eigvalsh(hh))
+    if spin:
+        return float(ev[:n_up].sum() + ev[:n_dn].sum())
+    return float(ev[:n_up].sum())

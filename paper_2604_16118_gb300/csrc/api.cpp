@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "kernels.h"
+#include "problem.h"
 #include "solver.h"
 
 struct bsmps_ctx_s {
@@ -27,6 +28,7 @@ Context* context_of(bsmps_ctx c) {
 
 void* Context::alloc(size_t bytes) {
     if (bytes == 0) return nullptr;
+    ++alloc_calls;
 #ifdef BSM_NO_ALLOC_CACHE   // host-side checking builds: every block goes back to the pool
     {
         void* q = nullptr;
@@ -249,6 +251,8 @@ const char* bsmps_last_error(bsmps_ctx ctx) { return ctx ? ctx->c.last_error.c_s
 
 int64_t bsmps_ctx_launch_count(bsmps_ctx ctx) { return ctx ? ctx->c.launches : 0; }
 
+int64_t bsmps_ctx_alloc_count(bsmps_ctx ctx) { return ctx ? ctx->c.alloc_calls : 0; }
+
 bsmps_status bsmps_ctx_profile(bsmps_ctx ctx, int enable) {
     return guarded(ctx, [&] {
         bsm::Context* c = C(ctx);
@@ -302,7 +306,7 @@ bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* 
         BSM_REQUIRE(M >= 0 && N >= 0 && K >= 0 && lda >= K && ldb >= N && ldc >= N, BSMPS_ERR_INVALID_ARG,
                     "emulated GEMM: need sizes >= 0 and leading dimensions >= row lengths");
         BSM_REQUIRE(M == 0 || N == 0 || (Cm && (K == 0 || (A && B))), BSMPS_ERR_INVALID_ARG, "null matrix");
-        bsm::launch_gemm_ozaki(c, M, N, K, A, lda, B, ldb, Cm, ldc, slices, 0, 1.0);
+        bsm::launch_gemm_ozaki(c, M, N, K, A, lda, B, ldb, Cm, ldc, slices, 1.0);
     });
 }
 
@@ -383,6 +387,53 @@ bsmps_status bsmps_mix_columns(bsmps_ctx ctx, bsmps_mps x, const double* Wm, int
         bsm::MpsPtr r = bsm::op_concat(c, {t});
         c->sync();
         *y = wrap(std::move(r));
+    });
+}
+
+bsmps_status bsmps_precond_theta(int n_orb, const double* h, const double* eri, int spin, int n_particles,
+                                 double gamma, double* theta) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(n_orb > 0 && h && eri && theta && n_particles > 0, BSMPS_ERR_INVALID_ARG,
+                    "n_orb, n_particles > 0 and h, eri, theta required");
+        const std::vector<double> th = bsm::precond_theta(n_orb, h, eri, spin ? 1 : 0, n_particles, gamma);
+        std::memcpy(theta, th.data(), th.size() * sizeof(double));
+    });
+}
+
+bsmps_status bsmps_precond_interval(int n_orb, int spin, const double* theta, const double* h, int n_up, int n_dn,
+                                    double* t_min, double* t_max) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(n_orb > 0 && theta && t_min && t_max && n_up >= 0 && n_dn >= 0, BSMPS_ERR_INVALID_ARG,
+                    "n_orb > 0, theta, t_min, t_max required");
+        bsm::precond_interval(n_orb, spin ? 1 : 0, theta, h, n_up, spin ? n_dn : 0, t_min, t_max);
+    });
+}
+
+bsmps_status bsmps_energy_lower_bound(int n_orb, const double* h, const double* eri, int spin, int n_up, int n_dn,
+                                      int cholesky, double* e_lb) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(n_orb > 0 && h && e_lb && (eri || !cholesky), BSMPS_ERR_INVALID_ARG,
+                    "n_orb > 0, h, e_lb (and eri when cholesky) required");
+        BSM_REQUIRE(n_up >= 0 && n_up <= n_orb && n_dn >= 0 && n_dn <= n_orb, BSMPS_ERR_INVALID_ARG,
+                    "particle numbers out of range");
+        *e_lb = bsm::energy_lower_bound(n_orb, h, eri, spin ? 1 : 0, n_up, n_dn, cholesky);
+    });
+}
+
+bsmps_status bsmps_precond_alpha0(double c0, double t_min, double c_lower, double c_upper, double* alpha0,
+                                  double* c) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(c0 > 0.0 && c0 < 1.0 && t_min > 0.0 && c_lower > 0.0 && c_upper > 0.0 && alpha0 && c,
+                    BSMPS_ERR_INVALID_ARG, "need c0 in (0, 1), t_min > 0, C_lower, C_upper > 0");
+        bsm::precond_alpha0(c0, t_min, c_lower, c_upper, alpha0, c);
+    });
+}
+
+bsmps_status bsmps_lowest_determinants(int K, const double* t_diag, int spin, int n_up, int n_dn, int D,
+                                       int64_t max_configs, unsigned char* occ) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(K > 0 && t_diag && occ && D > 0, BSMPS_ERR_INVALID_ARG, "K, D > 0, t_diag, occ required");
+        bsm::lowest_determinants(K, t_diag, spin ? 1 : 0, n_up, spin ? n_dn : 0, D, max_configs, occ);
     });
 }
 

@@ -132,6 +132,7 @@ struct Context {
     cudaStream_t stream = nullptr;
     std::string last_error;
     int64_t launches = 0;
+    int64_t alloc_calls = 0;         // requests served by alloc()
     double flops = 0.0;              // algorithmic FP64 flops issued (running total)
     bool profiling = false;
     int gemm_emulation_log2 = 0;     // block products >= 2^this flops on the tensor cores (0: never)

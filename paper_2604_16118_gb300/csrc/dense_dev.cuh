@@ -18,6 +18,52 @@ constexpr int kMaxSweeps = 40;
 __device__ __forceinline__ int nthreads() { return (int)blockDim.x; }
 __device__ __forceinline__ int nwarps() { return (int)(blockDim.x >> 5); }
 
+// One 32 x 32 output tile of a grouped FP64 GEMM, accumulated over one
+// contribution alpha op(A) B (op(A): M x K, transA selects A^T stored K x M):
+// the thread (ty, tx) of a 256-thread CTA owns rows m0 + ty + 8 r (r < 4) and
+// column n0 + tx.  The K loop stages 32 x 32 chunks of op(A) and B in shared
+// memory (As[k][m], Bs[k][n]); only the valid part of a chunk and the rows
+// below M issue FP64 instructions.  In: any struct with A, B, K, lda, ldb,
+// transA and alpha.
+constexpr int kGemmTile = 32;
+template <class In>
+__device__ __forceinline__ void gemm_tile_accumulate(const In& in, int M, int N, int m0, int n0,
+                                                     double (*As)[kGemmTile + 1], double (*Bs)[kGemmTile + 1],
+                                                     double acc[4]) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int k0 = 0; k0 < in.K; k0 += kGemmTile) {
+        for (int idx = threadIdx.x; idx < kGemmTile * kGemmTile; idx += kThreads) {
+            int mm, kk;
+            if (in.transA) {
+                kk = idx / kGemmTile;
+                mm = idx % kGemmTile;
+            } else {
+                mm = idx / kGemmTile;
+                kk = idx % kGemmTile;
+            }
+            const int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < M && gk < in.K)
+                v = in.transA ? in.A[(int64_t)gk * in.lda + gm] : in.A[(int64_t)gm * in.lda + gk];
+            As[kk][mm] = in.alpha * v;
+        }
+        for (int idx = threadIdx.x; idx < kGemmTile * kGemmTile; idx += kThreads) {
+            const int kk = idx / kGemmTile, nn = idx % kGemmTile;
+            const int gk = k0 + kk, gn = n0 + nn;
+            Bs[kk][nn] = (gk < in.K && gn < N) ? in.B[(int64_t)gk * in.ldb + gn] : 0.0;
+        }
+        __syncthreads();
+        const int kk_end = min(kGemmTile, in.K - k0);
+        for (int kk = 0; kk < kk_end; ++kk) {
+            const double b = Bs[kk][tx];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (m0 + ty + 8 * r < M) acc[r] = fma(As[kk][ty + 8 * r], b, acc[r]);
+        }
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

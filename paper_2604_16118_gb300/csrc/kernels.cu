@@ -43,7 +43,7 @@ struct GemmTile {
     int out, m0, n0;
 };
 
-constexpr int kTile = 32;
+constexpr int kTile = dev::kGemmTile;
 constexpr int kSmallGemmThreads = 128;
 
 // 32 x 32 output tile per CTA; thread (ty, tx) owns rows ty + 8 r (r < 4), column tx.
@@ -56,42 +56,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const GemmOut* __restrict__ o
     const GemmOut o = outs[tl.out];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c = o.beg; c < o.end; ++c) {
-        const GemmIn in = ins[c];
-        for (int k0 = 0; k0 < in.K; k0 += kTile) {
-            for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-                int mm, kk;
-                if (in.transA) {
-                    kk = idx / kTile;
-                    mm = idx % kTile;
-                } else {
-                    mm = idx / kTile;
-                    kk = idx % kTile;
-                }
-                const int gm = tl.m0 + mm, gk = k0 + kk;
-                double v = 0.0;
-                if (gm < o.M && gk < in.K)
-                    v = in.transA ? in.A[(int64_t)gk * in.lda + gm] : in.A[(int64_t)gm * in.lda + gk];
-                As[kk][mm] = in.alpha * v;
-            }
-            for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
-                const int kk = idx / kTile, nn = idx % kTile;
-                const int gk = k0 + kk, gn = tl.n0 + nn;
-                Bs[kk][nn] = (gk < in.K && gn < o.N) ? in.B[(int64_t)gk * in.ldb + gn] : 0.0;
-            }
-            __syncthreads();
-            // only the valid part of the K chunk and the warps that own rows
-            // below M issue FP64 instructions
-            const int kk_end = min(kTile, in.K - k0);
-            for (int kk = 0; kk < kk_end; ++kk) {
-                const double b = Bs[kk][tx];
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (tl.m0 + ty + 8 * r < o.M) acc[r] = fma(As[kk][ty + 8 * r], b, acc[r]);
-            }
-            __syncthreads();
-        }
-    }
+    for (int c = o.beg; c < o.end; ++c) dev::gemm_tile_accumulate(ins[c], o.M, o.N, tl.m0, tl.n0, As, Bs, acc);
     const int gn = tl.n0 + tx;
     if (gn >= o.N) return;
 #pragma unroll
@@ -343,7 +308,9 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
     for (int o = 0; o < (int)outs.size(); ++o) {
         const GemmOut& g = outs[o];
         // outputs of at least 2^gemm_emulation_log2 flops with one untransposed
-        // contribution (overwritten) go to the tensor-core FP64 emulation
+        // contribution (overwritten) go to the tensor-core FP64 emulation; the
+        // emulation takes untransposed operands only (the sweeps' large R X and
+        // U S X products are untransposed)
         if (ctx->gemm_emulation_log2 > 0 && g.end == g.beg + 1 && g.beta == 0.0 && !ins[g.beg].transA &&
             2.0 * g.M * (double)g.N * ins[g.beg].K >= std::ldexp(1.0, ctx->gemm_emulation_log2)) {
             emulated.push_back(o);
@@ -367,7 +334,7 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
         for (int o : emulated) {
             const GemmOut& g = outs[o];
             const GemmIn& in = ins[g.beg];
-            og.push_back({in.A, in.B, g.C, g.M, g.N, in.K, in.lda, in.ldb, g.ldc, in.transA, in.alpha});
+            og.push_back({in.A, in.B, g.C, g.M, g.N, in.K, in.lda, in.ldb, g.ldc, in.alpha});
             efl += 2.0 * g.M * (double)g.N * in.K;
         }
         ProfScope pe(ctx, KK_GEMM, efl, 0.0);

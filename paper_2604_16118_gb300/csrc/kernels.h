@@ -87,14 +87,15 @@ bool launch_jacobi_grid(Context* ctx, const std::vector<JacTask>& tasks);
 // S (1..8) bf16 integer slices per factor on the tensor cores (Ozaki scheme);
 // stream-ordered, no synchronisation.
 void launch_gemm_ozaki(Context* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                       double* C, int ldc, int S, int transA = 0, double alpha = 1.0);
+                       double* C, int ldc, int S, double alpha = 1.0);
 // Several such products in one exponent/split launch and one GEMM launch
 // (a tile list over all products).
+// One untransposed product C = alpha A B (row-major, leading dimensions given).
 struct OzGemm {
     const double* A;
     const double* B;
     double* C;
-    int M, N, K, lda, ldb, ldc, transA;
+    int M, N, K, lda, ldb, ldc;
     double alpha;
 };
 void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S);

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "dense_dev.cuh"
 #include "ops.h"
 
 namespace bsm {
@@ -20,8 +21,8 @@ namespace {
 constexpr size_t kNaBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
 
-constexpr int kNaThreads = 256;
-constexpr int kNaTile = 32;
+constexpr int kNaThreads = dev::kThreads;
+constexpr int kNaTile = dev::kGemmTile;
 
 struct NaOut {
     int64_t c;         // output offset (doubles) into the scratch
@@ -40,8 +41,9 @@ struct NaTile {
     int out, m0, n0;
 };
 
-// Grouped GEMM variant whose outputs and task lists live in the scratch:
-// C = sum over contributions alpha op(A) B, C row-major M x N (ld N).
+// The grouped GEMM of the environment sweep with its outputs and task lists in
+// the scratch: C = sum over contributions alpha op(A) B, C row-major M x N
+// (ld N); the tile loop is the one of the library's grouped GEMM.
 __global__ void __launch_bounds__(kNaThreads) k_gemm_noalloc(double* __restrict__ base,
                                                             const NaOut* __restrict__ outs,
                                                             const NaIn* __restrict__ ins,
@@ -52,32 +54,7 @@ __global__ void __launch_bounds__(kNaThreads) k_gemm_noalloc(double* __restrict_
     const NaOut o = outs[tl.out];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c = o.beg; c < o.end; ++c) {
-        const NaIn in = ins[c];
-        for (int k0 = 0; k0 < in.K; k0 += kNaTile) {
-            for (int idx = threadIdx.x; idx < kNaTile * kNaTile; idx += kNaThreads) {
-                const int mm = in.transA ? idx % kNaTile : idx / kNaTile;
-                const int kk = in.transA ? idx / kNaTile : idx % kNaTile;
-                const int gm = tl.m0 + mm, gk = k0 + kk;
-                double v = 0.0;
-                if (gm < o.M && gk < in.K)
-                    v = in.transA ? in.A[(int64_t)gk * in.lda + gm] : in.A[(int64_t)gm * in.lda + gk];
-                As[kk][mm] = in.alpha * v;
-            }
-            for (int idx = threadIdx.x; idx < kNaTile * kNaTile; idx += kNaThreads) {
-                const int kk = idx / kNaTile, nn = idx % kNaTile;
-                const int gk = k0 + kk, gn = tl.n0 + nn;
-                Bs[kk][nn] = (gk < in.K && gn < o.N) ? in.B[(int64_t)gk * in.ldb + gn] : 0.0;
-            }
-            __syncthreads();
-            for (int kk = 0; kk < kNaTile; ++kk) {
-                const double b = Bs[kk][tx];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r] = fma(As[kk][ty + 8 * r], b, acc[r]);
-            }
-            __syncthreads();
-        }
-    }
+    for (int c = o.beg; c < o.end; ++c) dev::gemm_tile_accumulate(ins[c], o.M, o.N, tl.m0, tl.n0, As, Bs, acc);
     const int gn = tl.n0 + tx;
     if (gn >= o.N) return;
     for (int r = 0; r < 4; ++r) {
@@ -295,20 +272,18 @@ double op_dot_noalloc(Context* ctx, const Mps* a, const Mps* b, const Mpo* W, do
                 for (int n0 = 0; n0 < c; n0 += kNaTile) t2.push_back({(int)o2.size(), m0, n0});
             o2.push_back({(int64_t)(off / 8), r, c, beg, (int)i2.size()});
         }
-        // task lists into the scratch (after the T blocks of this site)
-        auto put = [&](const void* src, size_t by) -> size_t {
-            if (by == 0) return take(0);
-            const size_t off = take(by);
-            BSM_CUDA(cudaMemcpyAsync(bytes + off, src, by, cudaMemcpyHostToDevice, ctx->stream));
-            return off;
-        };
-        const size_t po1 = put(o1.data(), o1.size() * sizeof(NaOut));
-        const size_t pi1 = put(i1.data(), i1.size() * sizeof(NaIn));
-        const size_t pt1 = put(t1.data(), t1.size() * sizeof(NaTile));
-        const size_t po2 = put(o2.data(), o2.size() * sizeof(NaOut));
-        const size_t pi2 = put(i2.data(), i2.size() * sizeof(NaIn));
-        const size_t pt2 = put(t2.data(), t2.size() * sizeof(NaTile));
+        // task lists into the scratch (after the T blocks of this site): every
+        // offset is laid out and checked against the site region before any copy
+        const void* srcs[6] = {o1.data(), i1.data(), t1.data(), o2.data(), i2.data(), t2.data()};
+        const size_t lens[6] = {o1.size() * sizeof(NaOut), i1.size() * sizeof(NaIn), t1.size() * sizeof(NaTile),
+                                o2.size() * sizeof(NaOut), i2.size() * sizeof(NaIn), t2.size() * sizeof(NaTile)};
+        size_t offs[6];
+        for (int q = 0; q < 6; ++q) offs[q] = take(lens[q]);
         BSM_REQUIRE(cursor <= site_off + need_site, BSMPS_ERR_RANK_CAP, "bsmps_dot_noalloc: site region overflow");
+        for (int q = 0; q < 6; ++q)
+            if (lens[q] > 0)
+                BSM_CUDA(cudaMemcpyAsync(bytes + offs[q], srcs[q], lens[q], cudaMemcpyHostToDevice, ctx->stream));
+        const size_t po1 = offs[0], pi1 = offs[1], pt1 = offs[2], po2 = offs[3], pi2 = offs[4], pt2 = offs[5];
         if (!t1.empty()) {
             k_gemm_noalloc<<<(unsigned)t1.size(), kNaThreads, 0, ctx->stream>>>(
                 base, (const NaOut*)(bytes + po1), (const NaIn*)(bytes + pi1), (const NaTile*)(bytes + pt1));

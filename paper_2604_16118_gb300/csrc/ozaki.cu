@@ -290,7 +290,7 @@ void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S)
         if (g.M == 0 || g.N == 0) continue;
         const OzProd& pd = prods[pi++];
         for (int r = 0; r < g.M; ++r)
-            rows.push_back({g.transA ? g.A + r : g.A + (int64_t)r * g.lda, g.transA ? (int64_t)g.lda : 1, g.K, pd.Kp,
+            rows.push_back({g.A + (int64_t)r * g.lda, 1, g.K, pd.Kp,
                             exps + pd.e_off + r, As + pd.a_off + (int64_t)r * pd.Kp, (int64_t)g.M * pd.Kp});
         for (int c = 0; c < g.N; ++c)
             rows.push_back({g.B + c, (int64_t)g.ldb, g.K, pd.Kp, exps + pd.f_off + c, Bs + pd.b_off + (int64_t)c * pd.Kp,
@@ -318,8 +318,8 @@ void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S)
 }
 
 void launch_gemm_ozaki(Context* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
-                       double* C, int ldc, int S, int transA, double alpha) {
-    launch_gemm_ozaki_group(ctx, {OzGemm{A, B, C, M, N, K, lda, ldb, ldc, transA, alpha}}, S);
+                       double* C, int ldc, int S, double alpha) {
+    launch_gemm_ozaki_group(ctx, {OzGemm{A, B, C, M, N, K, lda, ldb, ldc, alpha}}, S);
 }
 
 }  // namespace bsm

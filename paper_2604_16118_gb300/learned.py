@@ -52,9 +52,7 @@ def setup(ctx, wl, c0, margin, r_max=64):
     tmin, tmax = problem.spectrum_bounds(th, wl.spin, wl.n_up, wl.n_dn)
     if not (tmin > 0.0):
         raise ValueError("t_min <= 0: the shift margin is too small for this problem")
-    lo = SOLVER["C_lower"] * (1.0 - c0) ** 2
-    hi = SOLVER["C_upper"] * (1.0 + c0) ** 2
-    alpha0 = math.sqrt(2.0 / (tmin * (lo + hi)))             # Eq. (Sdef)
+    alpha0, _ = problem.alpha0_and_c(c0, tmin, SOLVER["C_lower"], SOLVER["C_upper"])   # Eq. (Sdef)
     W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, wl.spin, wl.n_particles, gamma)
     p = nat.make_precond(th, tmin, tmax, c0, alpha0)
     sp = nat.solver_params(SOLVER["c"], SOLVER["delta"], t_eig=SOLVER["t_eig"], tau=1e-14, r_max=r_max)

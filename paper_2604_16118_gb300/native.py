@@ -98,8 +98,14 @@ _SIGS = {
     "bsmps_ctx_sync": (_i, [_vp]),
     "bsmps_last_error": (C.c_char_p, [_vp]),
     "bsmps_ctx_launch_count": (_i64, [_vp]),
+    "bsmps_ctx_alloc_count": (_i64, [_vp]),
     "bsmps_ctx_profile": (_i, [_vp, _i]),
     "bsmps_ctx_kernel_stats": (_i, [_vp, _i, _i, _pi64, _pd, _pd, _pd]),
+    "bsmps_precond_theta": (_i, [_i, _pd, _pd, _i, _i, _d, _pd]),
+    "bsmps_precond_interval": (_i, [_i, _i, _pd, _pd, _i, _i, _pd, _pd]),
+    "bsmps_energy_lower_bound": (_i, [_i, _pd, _pd, _i, _i, _i, _i, _pd]),
+    "bsmps_precond_alpha0": (_i, [_d, _d, _d, _d, _pd, _pd]),
+    "bsmps_lowest_determinants": (_i, [_i, _pd, _i, _i, _i, _i, _i64, C.POINTER(C.c_ubyte)]),
     "bsmps_mps_random_size": (_i, [_i, _i, _i, _i, _i, _pi64]),
     "bsmps_mps_create": (_i, [_vp, _i, _i, _i, _i, _i, _i, _pd, _i64, C.POINTER(_vp)]),
     "bsmps_mps_import": (_i, [_vp, _i, _i, _i, _i, _pi, _pi, _pd, _i64, C.POINTER(_vp)]),
@@ -202,6 +208,10 @@ class Context:
 
     def launch_count(self):
         return int(lib().bsmps_ctx_launch_count(self.h))
+
+    def alloc_count(self):
+        """Device-memory requests served by the context's allocator so far."""
+        return int(lib().bsmps_ctx_alloc_count(self.h))
 
     KERNELS = ("copy", "gemm", "qr", "svd", "sumsq")
 
@@ -320,6 +330,59 @@ class MPO:
         p = np.zeros(2 * max(width, 1), dtype=np.int32)
         _check(self.ctx, lib().bsmps_mpo_channel_charges(self.h, bond, _iptr(p)))
         return [(int(p[2 * i]), int(p[2 * i + 1])) for i in range(width)]
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def precond_theta(h, eri, spin, n_particles, gamma):
+    """theta_i of Sec. 7.1.1 (bsmps_precond_theta)."""
+    h, eri = _c64(h), _c64(eri)
+    n = h.shape[0]
+    th = np.zeros(2 * n if spin else n)
+    _check(None, lib().bsmps_precond_theta(n, _dptr(h), _dptr(eri), int(spin), int(n_particles), float(gamma),
+                                           _dptr(th)))
+    return th
+
+
+def precond_interval(theta, spin, n_up, n_dn, h=None):
+    """[t_min, t_max] (bsmps_precond_interval); h given: the orbital-order rule."""
+    theta = _c64(theta)
+    n_orb = len(theta) // 2 if spin else len(theta)
+    hp = None if h is None else _c64(h)
+    lo, hi = C.c_double(), C.c_double()
+    _check(None, lib().bsmps_precond_interval(n_orb, int(spin), _dptr(theta), None if hp is None else _dptr(hp),
+                                              int(n_up), int(n_dn), C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def energy_lower_bound(h, eri, spin, n_up, n_dn, cholesky):
+    """A rigorous lower bound of the ground energy (bsmps_energy_lower_bound)."""
+    h = _c64(h)
+    e = None if eri is None else _c64(eri)
+    out = C.c_double()
+    _check(None, lib().bsmps_energy_lower_bound(h.shape[0], _dptr(h), None if e is None else _dptr(e), int(spin),
+                                                int(n_up), int(n_dn), int(bool(cholesky)), C.byref(out)))
+    return out.value
+
+
+def precond_alpha0(c0, t_min, c_lower, c_upper):
+    """(alpha_0, c) of Eq. (Sdef) / Eq. (precondcdef) (bsmps_precond_alpha0)."""
+    a, c = C.c_double(), C.c_double()
+    _check(None, lib().bsmps_precond_alpha0(float(c0), float(t_min), float(c_lower), float(c_upper), C.byref(a),
+                                            C.byref(c)))
+    return a.value, c.value
+
+
+def lowest_determinants(t_diag, spin, n_up, n_dn, D, max_configs=2_000_000):
+    """D x K occupation strings of the lowest determinants (bsmps_lowest_determinants)."""
+    t = _c64(t_diag)
+    K = len(t)
+    occ = np.zeros((D, K), dtype=np.uint8)
+    _check(None, lib().bsmps_lowest_determinants(K, _dptr(t), int(spin), int(n_up), int(n_dn), int(D),
+                                                 int(max_configs), occ.ctypes.data_as(C.POINTER(C.c_ubyte))))
+    return occ
 
 
 def mps_random_size(n_orb, spin, n_up, n_dn, r_max):

@@ -34,9 +34,10 @@ def test_lowest_determinants_ties_follow_site_order():
 
 
 def test_lowest_determinants_rejects_bad_requests():
-    with pytest.raises(ValueError):
+    from paper_2604_16118_gb300.native import BsmpsError
+    with pytest.raises(BsmpsError):
         problem.lowest_determinants(np.zeros(4), 0, 2, 0, 7)       # C(4,2) = 6 < 7
-    with pytest.raises(ValueError):
+    with pytest.raises(BsmpsError):
         problem.lowest_determinants(np.zeros(40), 0, 20, 0, 2, max_configs=1000)
 
 

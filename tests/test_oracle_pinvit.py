@@ -137,3 +137,59 @@ def test_iteration_decrease_bounds_and_convergence(prob_dominant):
             assert b["lambda"] <= a["lambda_star"] + 0.5 * (a["lambda"] - a["lambda_star"]) + 1e-10
     assert infos[-1]["converged"]
     assert infos[-1]["lambda"] - lam1 < 1e-9
+
+
+def _bisect_delta(rho, q):
+    """Root of g(D) = sqrt(1 - D^2) - rho D - q on [0, 1] by bisection (g decreases)."""
+    lo, hi = 0.0, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if math.sqrt(1.0 - mid * mid) - rho * mid - q > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("rho", [1e-8, 1e-3, 0.1, 0.5, 1.0, 3.0])
+@pytest.mark.parametrize("q", [1e-3, 0.3, 0.7, 0.99, 1.0])
+def test_delta_A_solves_its_defining_equation(rho, q):
+    # Sec. 5.3.2: Delta_A is the solution in [0, 1] of sqrt(1 - Delta^2) - rho Delta = q
+    # (checked in the squared form 1 - D^2 = (q + rho D)^2 with q + rho D >= 0, which
+    # is well conditioned also where D is close to 1, plus an independent bisection)
+    d = PI.delta_A(rho, q)
+    assert 0.0 <= d <= 1.0
+    assert q + rho * d >= 0.0
+    assert abs((1.0 - d * d) - (q + rho * d) ** 2) <= 4e-16 * (1.0 + rho) ** 2
+    assert abs(d - _bisect_delta(rho, q)) <= 1e-13
+
+
+@pytest.mark.parametrize("rho", [1e-3, 0.5])
+@pytest.mark.parametrize("q", [1.0 + 1e-12, 1.2])
+def test_delta_A_clamped_when_q_exceeds_one(rho, q):
+    # q > 1 (lambda_* above lambda^n at machine precision) has no root in [0, 1]:
+    # the tolerance is clamped to 0
+    assert PI.delta_A(rho, q) == 0.0
+
+
+def test_compression_of_u_keeps_the_step(prob, monkeypatch):
+    # reading of Sec. 5.3.1: u_k' compressed at U_REL ||u_k'|| = 1e-13 ||u_k'|| gives the
+    # same iteration as the exactly applied terms (U_REL = 0) to 1e-12
+    params = PI.SolverParams(prob["c"], prob["delta"], tau=1e-14, r_max=8)
+    runs = []
+    for u_rel in (0.0, 1e-13):
+        monkeypatch.setattr(PI, "U_REL", u_rel)
+        st = PI.SolverState()
+        x = prob["x0"]
+        infos = []
+        for _ in range(3):
+            x, info = PI.step(x, prob["mpo"], prob["prec"], params, st)
+            infos.append(info)
+        runs.append((infos, x))
+    (ia, xa), (ib, xb) = runs
+    for a, b in zip(ia, ib):
+        assert abs(a["lambda"] - b["lambda"]) <= 1e-12 * abs(a["lambda"])
+        assert abs(a["lambda_star"] - b["lambda_star"]) <= 1e-12 * abs(a["lambda_star"])
+        assert a["eta_tries"] == b["eta_tries"] and a["ranks"] == b["ranks"]
+    da, db = B.to_dense(xa), B.to_dense(xb)
+    assert np.linalg.norm(da - db) <= 1e-12 * np.linalg.norm(da)

@@ -1,4 +1,4 @@
-"""The allocation-free inner product agrees with bsmps_dot.
+"""The allocation-free inner product agrees with bsmps_dot and with the oracle.
 
 bsmps_dot_noalloc keeps every temporary in a fixed 32 MiB device array so that
 callers which cannot allocate device memory can still take inner products.
@@ -45,8 +45,28 @@ def test_noalloc_dot_matches_dot_twice(nat, ctx, wl, r, gamma):
     for (x, y, op, sh, scale) in [(a, b, W, 0.3, na * nhb), (b, a, None, 0.0, na * nb),
                                   (a, b, W, 0.3, na * nhb)]:
         ref = nat.dot(ctx, x, y, op, sh)
+        n_alloc = ctx.alloc_count()
         got = nat.dot_noalloc(ctx, x, y, op, sh)
+        assert ctx.alloc_count() == n_alloc          # no request reached the allocator
         assert abs(got - ref) <= 1e-12 * scale
+
+
+def test_noalloc_dot_matches_oracle(nat, ctx):
+    # the same inner products against the FP64 oracle (Sec. 2.4 environment recursion)
+    from oracle import bsmps as OB
+    from tests._common import oracle_mpo, oracle_random
+    wl, r, gamma = spinless_random_chain(K=10, N=5, seed=4), 16, 2.0
+    va, vb = random_block_values(n_random(wl, r), 7), random_block_values(n_random(wl, 8), 8)
+    a = nat.mps_create(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, r, va)
+    b = nat.mps_create(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, 8, vb)
+    W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, wl.spin, wl.n_particles, gamma)
+    oa, ob = oracle_random(wl, r, va), oracle_random(wl, 8, vb)
+    oW = oracle_mpo(wl, gamma)
+    na, nb = math.sqrt(OB.dot(oa, oa)), math.sqrt(OB.dot(ob, ob))
+    nhb = math.sqrt(OB.dot(OB.apply_exact(oW, ob, 0.3), OB.apply_exact(oW, ob, 0.3)))
+    for _ in range(2):
+        assert abs(nat.dot_noalloc(ctx, a, b, W, 0.3) - OB.dot(oa, ob, oW, 0.3)) <= 1e-12 * na * nhb
+        assert abs(nat.dot_noalloc(ctx, a, b) - OB.dot(oa, ob)) <= 1e-12 * na * nb
 
 
 def test_noalloc_rejects_contractions_beyond_the_scratch(nat, ctx):
