@@ -74,6 +74,14 @@ typedef enum {
     BSMPS_ERR_CUDA = 8         /* any other CUDA runtime error */
 } bsmps_status;
 
+/* Arithmetic of the contraction stage of the zip-up MPO application. */
+typedef enum {
+    BSMPS_PREC_FP64 = 0,   /* FP64 grouped GEMM on the FP64 units */
+    BSMPS_PREC_TF32X3 = 1  /* split precision on the tensor cores: operands split into two TF32
+                              parts, three products accumulated in FP32 (relative error of an entry
+                              a few 2^-21 of sum_k |a_ik||b_kj|); results stored in FP64 */
+} bsmps_precision;
+
 /* Exponential-sum preconditioner data (Sec. 4.2-4.3, Cor. lrprecond).
  * d: the K diagonal coefficients d_i of D = sum_i d_i a_i^* a_i (theta_i of
  * Sec. 7.1.1), host array of length K, read during the calls that take it.
@@ -114,11 +122,16 @@ typedef struct {
  * beyond the first that the previous step needed (start with 0).  The last
  * field only sizes the next step's first batch of candidate tolerances: the
  * passes of the eta_res loop are evaluated several at a time (their truncations
- * share launches), which changes no result. */
+ * share launches), which changes no result.  The last two fields drive the
+ * split-precision policy of bsmps_ctx_set_precision (start with 0, 0): the
+ * previous step's sum of residual-term norms sum_j ||s_j|| (Sec. 5.3.1), and
+ * 1 once the iteration has fallen back to FP64 contractions. */
 typedef struct {
     double eta_res;
     int n;
     int last_tries;
+    double last_sum_norms;
+    int fp64_locked;
 } bsmps_solver_state;
 
 /* Scalars reported by one step. */
@@ -138,6 +151,7 @@ typedef struct {
     int max_rank;         /* largest bond dimension of the returned iterate */
     double flops;         /* algorithmic FP64 flops issued by the step */
     double cap_discarded; /* norm discarded by the r_max cap of the iterate */
+    int precision;        /* arithmetic of the step's apply contraction (bsmps_precision) */
 } bsmps_step_info;
 
 BSMPS_API const char* bsmps_status_string(bsmps_status s);
@@ -162,7 +176,8 @@ BSMPS_API int64_t bsmps_ctx_alloc_count(bsmps_ctx ctx);
  * context stream and records its kind and algorithmic flops / bytes (this
  * adds two event records per launch); enable = 0 stops recording.
  * bsmps_ctx_kernel_stats synchronises the stream and returns, for kernel kind
- * `kind` (0 copy, 1 grouped GEMM, 2 QR, 3 SVD, 4 sum of squares), the number
+ * `kind` (0 copy, 1 grouped GEMM, 2 QR, 3 SVD, 4 sum of squares, 5 the
+ * contraction stage of the zip-up MPO application), the number
  * of recorded launches, their summed device time in ms and summed
  * algorithmic FP64 flops and bytes; `reset` != 0 clears the records after
  * reading.  Errors: INVALID_ARG (kind out of range), CUDA. */
@@ -296,11 +311,29 @@ BSMPS_API bsmps_status bsmps_mpo_destroy(bsmps_mpo W);
 /* y = (H_gamma + shift I) x (Sec. 2.4).  tol = 0 and r_max = 0: exact
  * application, bond basis = MPO channel x x's basis, grouped by sector
  * (channel-major), sectors that no complete path reaches dropped.  Otherwise
- * y = trunc_tol of that result capped at r_max (see bsmps_truncate).
+ * y = trunc_tol of that result capped at r_max (see bsmps_truncate), computed
+ * as the zip-up application of bsmps_apply_zipup followed by the right SVD
+ * sweep of the truncation (the zip-up result is already left-orthogonal).
  * flops (may be NULL): algorithmic FP64 flops issued.
- * Errors: INVALID_ARG (mismatched sites/species), OOM, CUDA. */
+ * Errors: INVALID_ARG (mismatched sites/species), OOM, CUDA, TIMEOUT. */
 BSMPS_API bsmps_status bsmps_apply_H(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift,
                            double tol, int r_max, bsmps_mps* y, double* flops);
+
+/* y = (H_gamma + shift I) x in left-orthogonal form by the zip-up application
+ * (Sec. 2.4 fused with the left-to-right QR sweep of Sec. 2.3), never forming
+ * the exact cores.  The carry C_t[m] maps y's orthogonalised bond-t basis of
+ * sector m to the exact basis (MPO channel a, x's sector m - Delta_a); site t
+ * forms every block T(m, s')[:, seg_b] = sum over MPO entries (a, b, s', s)
+ * of w C_t[m][:, seg_a] X_t(m - Delta_a, s) in one grouped GEMM (the
+ * contraction stage, profiled as kernel kind 5), then per sector m' of bond
+ * t+1 stacks the blocks (m, s') -> m' in layout order (m ascending, then s')
+ * and takes Q = I, C_{t+1} = stack when the stack has no more rows than
+ * columns, else Householder QR with diag(R) >= 0 (Q into y's core t,
+ * C_{t+1} = R).  Bond t+1 of y has, per sector, min(stacked rows, exact
+ * columns); the last core holds the norm.  D = 1 MPS only.  flops (may be
+ * NULL): algorithmic FP64 flops issued.  Errors: INVALID_ARG, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_apply_zipup(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift, bsmps_mps* y,
+                                         double* flops);
 
 /* trunc_eps (Sec. 2.2, Eq. (ttsvdquasiopt)): QR sweep left to right (diag R
  * >= 0), then right to left SVD of [X_b(n,0) | X_b(n,1)] per left sector;
@@ -388,6 +421,31 @@ BSMPS_API bsmps_status bsmps_eigensolve_step(bsmps_ctx ctx, bsmps_mpo W, const b
  * A (M x K, leading dimension lda), B (K x N, ldb) and C (M x N, ldc) are
  * row-major DEVICE pointers.  The work is ordered on the context stream and the
  * call does not synchronise.  Errors: INVALID_ARG, OOM, CUDA. */
+/* C = A B (M x N) on the tensor cores in split precision (BSMPS_PREC_TF32X3):
+ * every entry of A and B is split into two TF32 values, the three products
+ * A_hi B_hi + A_hi B_lo + A_lo B_hi are accumulated in FP32 in tensor memory
+ * (tcgen05.mma kind::tf32, 128 x 64 tiles), and C is stored in FP64.  The error
+ * of C_ij is a few units of 2^-21 times sum_k |a_ik| |b_kj| plus the FP32
+ * accumulation error.  The paper has no counterpart: this is the contraction
+ * kernel of the split-precision MPO application, exposed for testing.  A
+ * (M x K, lda), B (K x N, ldb) and C (M x N, ldc) are row-major DEVICE
+ * pointers; stream-ordered on the context stream, no synchronisation.  A bounded
+ * wait that gives up is reported as TIMEOUT at the context's next
+ * synchronising call.  Errors: INVALID_ARG, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_gemm_tf32x3(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda,
+                                         const double* B, int ldb, double* C, int ldc);
+
+/* Arithmetic of the contraction stage of the zip-up MPO application
+ * (bsmps_apply_zipup, bsmps_apply_H with a tolerance, and the residual terms
+ * of bsmps_eigensolve_step): BSMPS_PREC_FP64 (the default) or
+ * BSMPS_PREC_TF32X3.  Factorisations, inner products, the Rayleigh quotient and
+ * norms stay FP64.  In the eigensolver step the split precision is used only
+ * while its error estimate stays below a tenth of the previous step's residual
+ * tolerance eta_res (the budget of Lemma truncr); after that the step falls
+ * back to FP64 for the rest of the iteration (bsmps_step_info.precision
+ * reports the choice).  Errors: INVALID_ARG. */
+BSMPS_API bsmps_status bsmps_ctx_set_precision(bsmps_ctx ctx, int precision);
+
 /* Block products of at least 2^min_log2_flops flops with a single untransposed
  * contribution (the large R X and U S X products of sweeps over wide sectors;
  * transposed products stay on the FP64 units) run as

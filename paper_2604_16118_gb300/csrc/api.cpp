@@ -310,6 +310,30 @@ bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* 
     });
 }
 
+bsmps_status bsmps_gemm_tf32x3(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda, const double* B,
+                              int ldb, double* Cm, int ldc) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(M >= 0 && N >= 0 && K >= 0 && lda >= K && ldb >= N && ldc >= N, BSMPS_ERR_INVALID_ARG,
+                    "split-precision GEMM: need sizes >= 0 and leading dimensions >= row lengths");
+        BSM_REQUIRE(M == 0 || N == 0 || (Cm && (K == 0 || (A && B))), BSMPS_ERR_INVALID_ARG, "null matrix");
+        if (M == 0 || N == 0) return;
+        std::vector<bsm::GemmOut> outs{{Cm, M, N, ldc, 0, K > 0 ? 1 : 0, 0.0}};
+        std::vector<bsm::GemmIn> ins;
+        if (K > 0) ins.push_back({A, B, K, lda, ldb, 0, 1.0});
+        bsm::launch_gemm_tf32x3(c, outs, ins, bsm::KK_GEMM);
+    });
+}
+
+bsmps_status bsmps_ctx_set_precision(bsmps_ctx ctx, int precision) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(precision == BSMPS_PREC_FP64 || precision == BSMPS_PREC_TF32X3, BSMPS_ERR_INVALID_ARG,
+                    "precision must be BSMPS_PREC_FP64 or BSMPS_PREC_TF32X3");
+        c->apply_precision = precision;
+    });
+}
+
 bsmps_status bsmps_mps_joint_random_size(int n_orb, int spin, int n_up, int n_dn, int r_max, int D,
                                          int64_t* n_values) {
     return guarded(nullptr, [&] {
@@ -626,11 +650,30 @@ bsmps_status bsmps_apply_H(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift
         BSM_REQUIRE(W && y, BSMPS_ERR_INVALID_ARG, "null argument");
         BSM_REQUIRE(tol >= 0.0 && r_max >= 0, BSMPS_ERR_INVALID_ARG, "tol >= 0 and r_max >= 0 required");
         const double f0 = c->flops;
-        bsm::MpsPtr r = bsm::op_apply_exact(c, W->W, M(x), shift);
-        if (tol > 0.0 || r_max > 0) r = bsm::op_truncate(c, r.get(), tol, r_max, nullptr, nullptr);
+        bsm::MpsPtr r;
+        if (tol == 0.0 && r_max == 0) {
+            r = bsm::op_apply_exact(c, W->W, M(x), shift);
+        } else {
+            // zip-up application (left-orthogonal result), then the right SVD sweep of trunc_tol
+            std::vector<bsm::MpsPtr> u = bsm::op_apply_zipup_scaled(c, W->W, M(x), shift, {{}}, {{}});
+            std::vector<bsm::MpsPtr> t = bsm::op_truncate_batch_left_orthogonal(c, {u[0].get()}, {tol}, r_max);
+            r = std::move(t[0]);
+        }
         c->sync();
         if (flops) *flops = c->flops - f0;
         *y = wrap(std::move(r));
+    });
+}
+
+bsmps_status bsmps_apply_zipup(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift, bsmps_mps* y, double* flops) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(W && y, BSMPS_ERR_INVALID_ARG, "null argument");
+        const double f0 = c->flops;
+        std::vector<bsm::MpsPtr> u = bsm::op_apply_zipup_scaled(c, W->W, M(x), shift, {{}}, {{}});
+        c->sync();
+        if (flops) *flops = c->flops - f0;
+        *y = wrap(std::move(u[0]));
     });
 }
 

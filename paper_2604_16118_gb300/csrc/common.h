@@ -125,7 +125,8 @@ struct ProfRec {
     cudaEvent_t e0, e1;
 };
 
-enum KernelKind { KK_COPY = 0, KK_GEMM = 1, KK_QR = 2, KK_SVD = 3, KK_SUMSQ = 4, KK_COUNT = 5 };
+// KK_APPLY: the contraction stage of the zip-up MPO application (grouped GEMM)
+enum KernelKind { KK_COPY = 0, KK_GEMM = 1, KK_QR = 2, KK_SVD = 3, KK_SUMSQ = 4, KK_APPLY = 5, KK_COUNT = 6 };
 
 struct Context {
     int device = 0;
@@ -136,6 +137,7 @@ struct Context {
     double flops = 0.0;              // algorithmic FP64 flops issued (running total)
     bool profiling = false;
     int gemm_emulation_log2 = 0;     // block products >= 2^this flops on the tensor cores (0: never)
+    int apply_precision = BSMPS_PREC_FP64;   // arithmetic of the zip-up contraction stage
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;
     cudaEvent_t take_event();
@@ -194,6 +196,20 @@ struct Context {
                 throw Error(BSMPS_ERR_TIMEOUT, "a grid-wide wait of a factorisation gave up");
             }
         }
+    }
+};
+
+// RAII bracket of one launch for the optional profiler.
+struct ProfScope {
+    Context* ctx;
+    int kind;
+    double flops, bytes;
+    cudaEvent_t e0 = nullptr;
+    ProfScope(Context* c, int k, double f, double b) : ctx(c), kind(k), flops(f), bytes(b) {
+        if (ctx->profiling) ctx->prof_begin(&e0);
+    }
+    void done() {
+        if (ctx->profiling) ctx->prof_end(kind, flops, bytes, e0);
     }
 };
 

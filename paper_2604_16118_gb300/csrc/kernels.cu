@@ -192,10 +192,6 @@ __global__ void __launch_bounds__(kThreads) k_sumsq(const double* const* __restr
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-void check_launch(Context* ctx) {
-    ctx->launches++;
-    BSM_CUDA(cudaGetLastError());
-}
 
 // Every kernel of the library prefers the same L1/shared-memory split (maximum
 // shared memory), so consecutive launches never wait for the SM to re-partition.
@@ -212,21 +208,12 @@ void configure_carveout() {
     done = true;
 }
 
-// RAII bracket of one launch for the optional profiler
-struct ProfScope {
-    Context* ctx;
-    int kind;
-    double flops, bytes;
-    cudaEvent_t e0 = nullptr;
-    ProfScope(Context* c, int k, double f, double b) : ctx(c), kind(k), flops(f), bytes(b) {
-        if (ctx->profiling) ctx->prof_begin(&e0);
-    }
-    void done() {
-        if (ctx->profiling) ctx->prof_end(kind, flops, bytes, e0);
-    }
-};
-
 }  // namespace
+
+void check_launch(Context* ctx) {
+    ctx->launches++;
+    BSM_CUDA(cudaGetLastError());
+}
 
 cudaEvent_t Context::take_event() {
     cudaEvent_t e;
@@ -299,8 +286,12 @@ void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
 }
 
 
-void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins) {
+void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins, int kind) {
     if (outs.empty()) return;
+    if (kind == KK_APPLY && ctx->apply_precision == BSMPS_PREC_TF32X3 && gemm_tf32x3_eligible(outs, ins)) {
+        launch_gemm_tf32x3(ctx, outs, ins, kind);
+        return;
+    }
     configure_carveout();
     std::vector<GemmTile> tiles;
     std::vector<int> small, emulated;
@@ -337,7 +328,7 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
             og.push_back({in.A, in.B, g.C, g.M, g.N, in.K, in.lda, in.ldb, g.ldc, in.alpha});
             efl += 2.0 * g.M * (double)g.N * in.K;
         }
-        ProfScope pe(ctx, KK_GEMM, efl, 0.0);
+        ProfScope pe(ctx, kind, efl, 0.0);
         launch_gemm_ozaki_group(ctx, og, 8);
         pe.done();
     }
@@ -359,7 +350,7 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
     unsigned char* d = s.up(pack);
     const GemmOut* d_o = (const GemmOut*)(d + oo);
     const GemmIn* d_i = (const GemmIn*)(d + oi);
-    ProfScope ps(ctx, KK_GEMM, fl, by);
+    ProfScope ps(ctx, kind, fl, by);
     if (!small.empty()) {
         k_gemm_small<<<(unsigned)small.size(), kSmallGemmThreads, 0, ctx->stream>>>(d_o, d_i, (const int*)(d + os));
         check_launch(ctx);
@@ -433,34 +424,44 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
         qr.push_back({t.G, Q[i], R[i], s.dbl((size_t)k), t.wide ? t.N : t.M, t.wide ? t.M : t.N});
     }
     launch_qr(ctx, qr);
-    // 2. one-sided Jacobi on G = R^T (the row-major R is G column-major)
-    std::vector<JacTask> small, large;
-    int kmax_small = 1;
+    // 2. one-sided Jacobi on G = R^T (the row-major R is G column-major): one
+    // thread-block cluster per matrix for kClusterJacobiMin <= k <= kClusterJacobiMax
+    // (the FP64 units of several SMs on one matrix); one CTA in shared memory for
+    // smaller k (and for k <= kSmemJacobiMax when no cluster can be scheduled);
+    // beyond, across the grid (one CTA per matrix when the cooperative launch
+    // cannot be resident)
+    std::vector<JacTask> small, mid, large;
     double fl = 0.0, by = 0.0;
     for (size_t i = 0; i < tasks.size(); ++i) {
         const int k = std::min(tasks[i].M, tasks[i].N);
-        JacTask jt{R[i], V[i], Sraw[i], k, k <= kSmemJacobiMax ? 1 : 0};
-        if (jt.smem) {
+        JacTask jt{R[i], V[i], Sraw[i], k, 0};
+        if (k >= kClusterJacobiMin && k <= kClusterJacobiMax)
+            mid.push_back(jt);
+        else if (k <= kSmemJacobiMax)
             small.push_back(jt);
-            kmax_small = std::max(kmax_small, k);
-        } else {
+        else
             large.push_back(jt);
-        }
         fl += 54.0 * (double)k * k * k;   // nominal: 6 sweeps of k^2/2 pairs x 18k flops
         by += 8.0 * 3.0 * k * (double)k;
     }
     ctx->flops += fl;
     {
         ProfScope ps(ctx, KK_SVD, fl, by);
+        if (!mid.empty() && !launch_jacobi_cluster(ctx, mid)) {
+            for (const JacTask& t : mid) (t.k <= kSmemJacobiMax ? small : large).push_back(t);
+        }
         if (!small.empty()) {
+            int kmax_small = 1;
+            for (JacTask& t : small) {
+                t.smem = 1;
+                kmax_small = std::max(kmax_small, t.k);
+            }
             JacTask* d = s.up(small);
             const size_t smem = sizeof(double) * 2 * (size_t)kmax_small * kmax_small;
             BSM_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             k_jacobi<<<(unsigned)small.size(), kThreads, smem, ctx->stream>>>(d);
             check_launch(ctx);
         }
-        // matrices too large for shared memory: one-sided Jacobi across the grid
-        // (one CTA per matrix when the cooperative launch cannot be resident)
         if (!large.empty() && !launch_jacobi_grid(ctx, large)) {
             JacTask* d = s.up(large);
             k_jacobi<<<(unsigned)large.size(), kThreads, 0, ctx->stream>>>(d);

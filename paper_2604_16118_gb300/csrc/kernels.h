@@ -81,6 +81,15 @@ struct JacTask {
 // error word, raised at the next sync).  Returns false when no grid can be
 // resident (the caller then runs one CTA per matrix).
 bool launch_jacobi_grid(Context* ctx, const std::vector<JacTask>& tasks);
+// Jacobi of matrices with k <= kClusterJacobiMax, one thread-block cluster of 8
+// CTAs per matrix with G and V in the CTAs' distributed shared memory and a
+// cluster barrier per round (csrc/jacobi_cluster.cu).  Returns false, with
+// nothing launched, when such a cluster cannot be scheduled.
+constexpr int kClusterJacobiMax = 336;
+// Jacobi problems from this size on go to the cluster kernel: below it one SM's
+// FP64 units suffice for the latency of a round.
+constexpr int kClusterJacobiMin = 32;
+bool launch_jacobi_cluster(Context* ctx, const std::vector<JacTask>& tasks);
 
 // C (M x N) = alpha op(A) B, op(A) = A (M x K) or A^T (A stored K x M), B
 // (K x N), all row-major FP64 on the device with leading dimensions, emulated by
@@ -103,7 +112,17 @@ void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S)
 void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks);
 // Sets n[i] doubles at ptr[i] to zero, all regions in one launch.
 void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n);
-void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins);
+// Counts a launch and raises the launch error, if any.
+void check_launch(Context* ctx);
+// The same grouped GEMM on the tensor cores in split precision (3xTF32, FP32
+// accumulation in tensor memory; csrc/tc_gemm.cu); untransposed operands only.
+bool gemm_tf32x3_eligible(const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins);
+void launch_gemm_tf32x3(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins, int kind);
+// kind: the profiler's record of the launch (KK_GEMM, or KK_APPLY for the zip-up
+// contraction, which runs as launch_gemm_tf32x3 when the context's apply
+// precision is BSMPS_PREC_TF32X3)
+void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins,
+                 int kind = KK_GEMM);
 void launch_qr(Context* ctx, const std::vector<QrTask>& tasks);
 void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks);
 // out[i] = sum of squares of x[0..n) for a list of (x, n) segments

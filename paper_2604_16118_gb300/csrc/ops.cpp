@@ -554,14 +554,20 @@ void right_sweep_sitewise(Context* ctx, TruncJob& J) {
             stot += kk[ni];
         }
         double* S_all = s.dbl((size_t)std::max<int64_t>(stot, 1));
-        bool fused = true;
-        for (int ni = 0; ni < nn && fused; ++ni)
-            if (kk[ni] > 0) fused = svd_site_fits(bn.dim[ni], c0[ni] + c1[ni]);
-        if (fused) {
+        // sectors of this bond: small ones in the fused one-CTA kernel, the others
+        // (k >= kClusterJacobiMin, or too large for it) by QR + Jacobi on clusters
+        std::vector<int> site_sec, gen_sec;
+        for (int ni = 0; ni < nn; ++ni) {
+            if (kk[ni] == 0) continue;
+            if (kk[ni] < kClusterJacobiMin && svd_site_fits(bn.dim[ni], c0[ni] + c1[ni]))
+                site_sec.push_back(ni);
+            else
+                gen_sec.push_back(ni);
+        }
+        if (!site_sec.empty()) {
             std::vector<SvdSiteTask> st;
             std::vector<SvdPart> parts;
-            for (int ni = 0; ni < nn; ++ni) {
-                if (kk[ni] == 0) continue;
+            for (int ni : site_sec) {
                 const int M = bn.dim[ni], N = c0[ni] + c1[ni], k = kk[ni];
                 US[ni] = s.dbl((size_t)M * k);
                 Vt[ni] = s.dbl((size_t)k * N);
@@ -577,11 +583,11 @@ void right_sweep_sitewise(Context* ctx, TruncJob& J) {
                 st.push_back(task);
             }
             launch_svd_site(ctx, st, parts);
-        } else {
+        }
+        if (!gen_sec.empty()) {
             std::vector<CopyTask> gather;
             std::vector<SvdTask> svd;
-            for (int ni = 0; ni < nn; ++ni) {
-                if (kk[ni] == 0) continue;
+            for (int ni : gen_sec) {
                 const int M = bn.dim[ni], N = c0[ni] + c1[ni], k = kk[ni];
                 const int wide = M < N ? 1 : 0;
                 double* G = s.dbl((size_t)M * N);
@@ -860,6 +866,11 @@ struct RightPlan {
     double* disc = nullptr;
 };
 
+// Jobs with a sector of this many kept columns or more leave the persistent
+// right sweep (one CTA per sector) for the per-site sweep, whose larger SVDs run
+// on thread-block clusters: one SM's FP64 rate bounds a one-CTA Jacobi.
+constexpr int kPersistentSvdMax = 40;
+
 bool plan_right_sizes(const TruncJob& J, RightPlan& rp) {
     const Layout& L = J.L;
     const int K = L.K;
@@ -879,7 +890,7 @@ bool plan_right_sizes(const TruncJob& J, RightPlan& rp) {
             const int kp = std::min(bn.dim[n], rp.cpad[b][n]);
             rp.kpad[b][n] = kp;
             total += kp;
-            if (kp > 96 || dyn_svd_smem(bn.dim[n], rp.cpad[b][n]) > 220 * 1024) return false;
+            if (kp >= kPersistentSvdMax || dyn_svd_smem(bn.dim[n], rp.cpad[b][n]) > 220 * 1024) return false;
             int64_t fma = 0;
             for (const Block& bk : L.blocks[b])
                 if (bk.li == (int)n && b + 1 < K) fma += (int64_t)bk.rows * bk.cols * rp.kpad[b + 1][bk.ri];
@@ -1121,7 +1132,8 @@ bool right_sweep_batch(Context* ctx, const std::vector<TruncJob*>& jobs, GridSyn
 
 // trunc_eps of several MPS of the same sites (Sec. 2.2): the fused sweeps of
 // all of them share launches.
-std::vector<MpsPtr> truncate_jobs(Context* ctx, std::vector<std::unique_ptr<TruncJob>>& jobs) {
+std::vector<MpsPtr> truncate_jobs(Context* ctx, std::vector<std::unique_ptr<TruncJob>>& jobs,
+                                  bool left_orthogonal = false) {
     std::vector<TruncJob*> all;
     for (auto& j : jobs) all.push_back(j.get());
     // phase bookkeeping of the two persistent sweeps; err is read back with
@@ -1132,8 +1144,9 @@ std::vector<MpsPtr> truncate_jobs(Context* ctx, std::vector<std::unique_ptr<Trun
     BSM_CUDA(cudaMemsetAsync(gs, 0, 2 * sizeof(GridSync), ctx->stream));
     bool gs_checked = false;
     std::vector<TruncJob*> left_rest;
-    const bool left_done = left_sweep_batch(ctx, all, gs, &left_rest);
-    for (TruncJob* J : left_rest) left_sweep_sitewise(ctx, *J);
+    const bool left_done = !left_orthogonal && left_sweep_batch(ctx, all, gs, &left_rest);
+    if (!left_orthogonal)
+        for (TruncJob* J : left_rest) left_sweep_sitewise(ctx, *J);
     std::vector<TruncJob*> right_rest;
     right_sweep_batch(ctx, all, gs, &gs_checked, &right_rest);
     for (TruncJob* J : right_rest) right_sweep_sitewise(ctx, *J);
@@ -1149,6 +1162,42 @@ std::vector<MpsPtr> truncate_jobs(Context* ctx, std::vector<std::unique_ptr<Trun
 }
 
 }  // namespace
+
+std::vector<MpsPtr> op_truncate_batch_left_orthogonal(Context* ctx, const std::vector<const Mps*>& xs,
+                                                      const std::vector<double>& eps, int r_max) {
+    BSM_REQUIRE(xs.size() == eps.size(), BSMPS_ERR_INVALID_ARG, "one tolerance per MPS");
+    if (xs.empty()) return {};
+    std::vector<std::unique_ptr<TruncJob>> jobs;
+    for (size_t i = 0; i < xs.size(); ++i) {
+        BSM_REQUIRE(same_space(xs[i]->lay, xs[0]->lay), BSMPS_ERR_INVALID_ARG,
+                    "batched truncation of MPS on different sites");
+        jobs.emplace_back(new TruncJob(ctx, xs[i], eps[i], r_max));
+    }
+    return truncate_jobs(ctx, jobs, true);
+}
+
+std::vector<double> op_last_core_norms(Context* ctx, const std::vector<const Mps*>& xs) {
+    std::vector<double> out(xs.size(), 0.0);
+    std::vector<const double*> ptr;
+    std::vector<int64_t> n;
+    std::vector<int> who;
+    for (size_t i = 0; i < xs.size(); ++i) {
+        const int K = xs[i]->lay.K;
+        if (K == 0 || xs[i]->lay.core_size[K - 1] == 0) continue;
+        ptr.push_back(xs[i]->core[K - 1]);
+        n.push_back(xs[i]->lay.core_size[K - 1]);
+        who.push_back((int)i);
+    }
+    if (ptr.empty()) return out;
+    Scratch s(ctx);
+    double* d = s.dbl(ptr.size());
+    launch_sumsq(ctx, ptr, n, d);
+    std::vector<double> h(ptr.size());
+    BSM_CUDA(cudaMemcpyAsync(h.data(), d, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->sync();
+    for (size_t q = 0; q < who.size(); ++q) out[who[q]] = std::sqrt(h[q]);
+    return out;
+}
 
 MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol, double* disc_cap) {
     std::vector<std::unique_ptr<TruncJob>> jobs;

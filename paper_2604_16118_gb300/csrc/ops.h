@@ -43,6 +43,21 @@ std::vector<MpsPtr> op_apply_exact_scaled(Context* ctx, const Mpo& W, const Mps*
                                           const std::vector<std::vector<double>>& f1,
                                           const std::vector<double>* col_shift = nullptr);
 
+// u_i = (H_gamma + shift I) S_i x in left-orthogonal form by the zip-up
+// application (Sec. 2.4 fused with the QR sweep of Sec. 2.3, csrc/zipup.cpp):
+// per site one grouped GEMM for all i (the contraction, profiled as KK_APPLY),
+// then per sector Q = I (no more rows than columns) or Householder QR.
+std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
+                                          const std::vector<std::vector<double>>& f0,
+                                          const std::vector<std::vector<double>>& f1);
+
+// trunc_eps of left-orthogonal MPS: the right SVD sweep alone (the left QR
+// sweep of a truncation leaves such an MPS as it is, up to the bond gauge).
+std::vector<MpsPtr> op_truncate_batch_left_orthogonal(Context* ctx, const std::vector<const Mps*>& xs,
+                                                      const std::vector<double>& eps, int r_max);
+// Frobenius norms of the last cores (the norms of left-orthogonal MPS), one sync.
+std::vector<double> op_last_core_norms(Context* ctx, const std::vector<const Mps*>& xs);
+
 // trunc_eps with rank cap (Sec. 2.2); discarded norms are returned.
 MpsPtr op_truncate(Context* ctx, const Mps* x, double eps, int r_max, double* disc_tol,
                    double* disc_cap);

@@ -198,6 +198,7 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
     const double flops0 = ctx->flops;
     const int nt = P.n_terms();
     info = bsmps_step_info{};
+    info.precision = BSMPS_PREC_FP64;
     // lambda^n and ||x||_A^2 (Eq. (exactrq))
     const auto ps = pair_sums(ctx, P, {{x_in, x_in, &W}, {x_in, x_in, nullptr}});
     const double num = ps[0], den = ps[1];
@@ -208,22 +209,34 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
     std::vector<double> s0(x_in->lay.K, 1.0), s1(x_in->lay.K, 1.0);
     s0[0] = s1[0] = 1.0 / std::sqrt(num);
     MpsPtr x = op_scale_sites(ctx, x_in, s0, s1);
-    // residual terms: u_k' = (H_gamma - lambda) S_k' x, s_{k,k'} = S_k u_k'
-    std::vector<MpsPtr> u = op_apply_exact_scaled(ctx, W, x.get(), -lam, P.f0, P.f1);
-    if (prm.u_rel > 0.0) {
-        // one near-lossless compression per exactly applied term (trunc at u_rel ||u||)
-        std::vector<EnvProblem> up;
-        for (int kp = 0; kp < nt; ++kp) up.push_back({u[kp].get(), u[kp].get(), nullptr, 0.0});
-        const std::vector<double> un2 = op_dot_batch(ctx, up);
-        std::vector<const Mps*> ux;
-        std::vector<double> ueps;
-        for (int kp = 0; kp < nt; ++kp) {
-            ux.push_back(u[kp].get());
-            ueps.push_back(prm.u_rel * std::sqrt(std::max(un2[kp], 0.0)));
-        }
-        std::vector<MpsPtr> uc = op_truncate_batch(ctx, ux, ueps, 0);
-        for (int kp = 0; kp < nt; ++kp) u[kp] = std::move(uc[kp]);
+    // residual terms: u_k' = (H_gamma - lambda) S_k' x, s_{k,k'} = S_k u_k'.
+    // Split-precision contractions while their error estimate, kSplitRel sum_j ||s_j||
+    // of the previous step, stays below a tenth of the previous eta_res (the
+    // residual error budget of Lemma truncr); FP64 from then on.
+    const int prec_saved = ctx->apply_precision;
+    bool split = prec_saved != BSMPS_PREC_FP64 && !st.fp64_locked;
+    if (split && std::isfinite(st.eta_res) && kSplitRel * st.last_sum_norms > 0.1 * st.eta_res) {
+        split = false;
+        st.fp64_locked = 1;
     }
+    info.precision = split ? prec_saved : BSMPS_PREC_FP64;
+    ctx->apply_precision = info.precision;
+    std::vector<MpsPtr> u;
+    if (prm.u_rel > 0.0) {
+        // zip-up application (left-orthogonal u_k', norm in the last core), then one
+        // near-lossless compression per term: the right sweep of trunc at u_rel ||u||
+        u = op_apply_zipup_scaled(ctx, W, x.get(), -lam, P.f0, P.f1);
+        std::vector<const Mps*> ux;
+        for (int kp = 0; kp < nt; ++kp) ux.push_back(u[kp].get());
+        const std::vector<double> un = op_last_core_norms(ctx, ux);
+        std::vector<double> ueps;
+        for (int kp = 0; kp < nt; ++kp) ueps.push_back(prm.u_rel * un[kp]);
+        std::vector<MpsPtr> uc = op_truncate_batch_left_orthogonal(ctx, ux, ueps, 0);
+        for (int kp = 0; kp < nt; ++kp) u[kp] = std::move(uc[kp]);
+    } else {
+        u = op_apply_exact_scaled(ctx, W, x.get(), -lam, P.f0, P.f1);   // exactly applied terms
+    }
+    ctx->apply_precision = prec_saved;
     std::vector<EnvProblem> nprobs;
     for (int kp = 0; kp < nt; ++kp)
         for (int k = 0; k < nt; ++k) {
@@ -279,6 +292,7 @@ MpsPtr eigensolve_step(Context* ctx, const Mpo& W, const PrecondTerms& P, const 
     }
     st.last_tries = tries;
     st.eta_res = eta;
+    st.last_sum_norms = sum_norms;
     const double rho = (rnorm + eta) / std::sqrt(1.0 - prm.c);
     check_finite(rho, "rho");
     info.lambda = lam;
@@ -366,7 +380,7 @@ MpsPtr eigensolve_outer(Context* ctx, const Mpo& W, const PrecondTerms& P, const
         const double tau_m = eta / (2.0 * (1.0 + (1.0 + alpha) * kappa));
         bsmps_solver_params inner = prm;
         inner.tau = tau_m;
-        bsmps_solver_state st{std::numeric_limits<double>::infinity(), 0, 0};
+        bsmps_solver_state st{std::numeric_limits<double>::infinity(), 0, 0, 0.0, 0};
         bsmps_outer_record rec{};
         const double fl0 = ctx->flops;
         bsmps_step_info info{};

@@ -9,6 +9,10 @@
 namespace bsm {
 
 constexpr int kMaxEtaRetries = 60;
+// Relative error estimate of the residual terms computed with split-precision
+// (3xTF32) contractions, against sum_j ||s_j||: the per-entry bound of a few
+// units of 2^-21 of the summed magnitudes, with room for cancellation.
+constexpr double kSplitRel = 1.0 / 262144.0;   // 2^-18
 
 struct PrecondTerms {
     double h = 0.0;

@@ -1,0 +1,283 @@
+// Grouped FP64-in / FP64-out GEMM on the 5th-generation tensor cores in split
+// precision (3xTF32): every operand value v (scaled by its contribution's alpha)
+// is split into v_hi = tf32(v) and v_lo = tf32(v - v_hi), and a tile accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 in tensor memory (the A_lo B_lo term,
+// below 2^-21 relative, is dropped).  The relative error of an entry is a few
+// units of 2^-21 times sum_k |a_ik| |b_kj| plus the FP32 accumulation error.
+//
+// One CTA computes one 128 x 64 output tile of one grouped-GEMM output: 4 warps
+// stage 32-wide k chunks of every contribution in shared memory (FP64 loads,
+// split, canonical K-major layout without swizzle), one thread issues the
+// tcgen05.mma instructions and commits them to an mbarrier, and at the end the
+// four warps read their 32 accumulator lanes with tcgen05.ld.  Every wait on the
+// mbarrier is bounded by the global timer; a CTA that gives up sets the device
+// error word, waits (bounded) for its own MMAs, frees its tensor memory and
+// returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace bsm {
+namespace {
+
+constexpr int kTcM = 128;         // rows of a tile: the M of one tcgen05.mma (cta_group::1)
+constexpr int kTcN = 64;          // columns of a tile: the N of one tcgen05.mma, also the TMEM columns
+constexpr int kTcK = 32;          // k values per staged chunk (4 MMAs of K = 8 for tf32)
+constexpr int kTcThreads = 128;   // warp w reads TMEM lanes 32 w .. 32 w + 31
+constexpr int kTcOperandBytes = (2 * kTcM + 2 * kTcN) * kTcK * 4;   // A_hi, A_lo, B_hi, B_lo
+constexpr unsigned long long kTcWaitNs = 1000000000ull;              // 1 s
+
+struct TcTile {
+    int out, m0, n0;
+};
+
+// Byte offset of element (row r, k) of a K-major operand tile in the canonical
+// layout without swizzle: 8-row x 16-byte core matrices, the 8 core matrices
+// of a row group along k contiguous (leading byte offset 128), row groups 1024
+// bytes apart (stride byte offset).
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (in 16-byte units), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: D in FP32, A and B TF32 and K-major,
+// N = kTcN, M = kTcM.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+// Round to the nearest TF32 value (10 mantissa bits), ties away from zero.
+__device__ __forceinline__ uint32_t tf32_bits(float f) { return (__float_as_uint(f) + 0x1000u) & 0xFFFFE000u; }
+
+__device__ __forceinline__ void tf32_split(double v, uint32_t* hi, uint32_t* lo) {
+    const uint32_t h = tf32_bits((float)v);
+    *hi = h;
+    *lo = tf32_bits((float)(v - (double)__uint_as_float(h)));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase with the given parity; false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kTcWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate));
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __restrict__ outs,
+                                                           const GemmIn* __restrict__ ins,
+                                                           const TcTile* __restrict__ tiles, int* err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int gave_up;
+    unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+    unsigned char* a_hi = base;
+    unsigned char* a_lo = a_hi + kTcM * kTcK * 4;
+    unsigned char* b_hi = a_lo + kTcM * kTcK * 4;
+    unsigned char* b_lo = b_hi + kTcN * kTcK * 4;
+    const TcTile tl = tiles[blockIdx.x];
+    const GemmOut o = outs[tl.out];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar_a = smem_addr(&bar);
+
+    if (threadIdx.x == 0) {
+        gave_up = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(kTcN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+
+    uint32_t n_commits = 0;
+    for (int c = o.beg; c < o.end; ++c) {
+        const GemmIn in = ins[c];
+        for (int k0 = 0; k0 < in.K; k0 += kTcK) {
+            // the chunk before this one must have been consumed by the tensor cores
+            if (n_commits > 0) {
+                if (!mbar_wait(bar_a, (n_commits - 1) & 1)) {
+                    if (threadIdx.x == 0) atomicExch(&gave_up, 1);
+                }
+                __syncthreads();
+                if (gave_up) goto finish;
+            }
+            // A: rows m0 .. m0 + 127, k0 .. k0 + 31 (alpha folded in), split into hi / lo
+            for (int idx = threadIdx.x; idx < kTcM * kTcK; idx += kTcThreads) {
+                const int r = idx / kTcK, k = idx % kTcK;
+                const int gm = tl.m0 + r, gk = k0 + k;
+                const double v = (gm < o.M && gk < in.K) ? in.alpha * in.A[(int64_t)gm * in.lda + gk] : 0.0;
+                uint32_t hi, lo;
+                tf32_split(v, &hi, &lo);
+                const uint32_t off = tc_off(r, k);
+                *(uint32_t*)(a_hi + off) = hi;
+                *(uint32_t*)(a_lo + off) = lo;
+            }
+            // B: k0 .. k0 + 31 x columns n0 .. n0 + 63, stored K-major (row = column n)
+            for (int idx = threadIdx.x; idx < kTcN * kTcK; idx += kTcThreads) {
+                const int k = idx / kTcN, n = idx % kTcN;
+                const int gk = k0 + k, gn = tl.n0 + n;
+                const double v = (gk < in.K && gn < o.N) ? in.B[(int64_t)gk * in.ldb + gn] : 0.0;
+                uint32_t hi, lo;
+                tf32_split(v, &hi, &lo);
+                const uint32_t off = tc_off(n, k);
+                *(uint32_t*)(b_hi + off) = hi;
+                *(uint32_t*)(b_lo + off) = lo;
+            }
+            // generic-proxy writes become visible to the tensor cores' (async) proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sa_hi = smem_addr(a_hi), sa_lo = smem_addr(a_lo);
+                const uint32_t sb_hi = smem_addr(b_hi), sb_lo = smem_addr(b_lo);
+                for (int kk = 0; kk < kTcK / 8; ++kk) {
+                    const uint32_t step = (uint32_t)kk * 256u;   // two core matrices along k per MMA
+                    const uint32_t first = (n_commits == 0 && kk == 0) ? 0u : 1u;
+                    tc_mma(tmem, tc_desc(sa_lo + step), tc_desc(sb_hi + step), first);
+                    tc_mma(tmem, tc_desc(sa_hi + step), tc_desc(sb_lo + step), 1u);
+                    tc_mma(tmem, tc_desc(sa_hi + step), tc_desc(sb_hi + step), 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 bar_a)
+                             : "memory");
+            }
+            ++n_commits;
+        }
+    }
+    if (n_commits > 0) {
+        if (!mbar_wait(bar_a, (n_commits - 1) & 1)) {
+            if (threadIdx.x == 0) atomicExch(&gave_up, 1);
+        }
+        __syncthreads();
+        if (gave_up) goto finish;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    {
+        // warp w holds rows m0 + 32 w + lane of the tile
+        const int row = tl.m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < kTcN; c0 += 16) {
+            uint32_t v[16];
+            if (n_commits > 0) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                    "%12, %13, %14, %15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0u;
+            }
+            if (row < o.M) {
+                double* cr = o.C + (int64_t)row * o.ldc;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = tl.n0 + c0 + j;
+                    if (col < o.N) cr[col] = o.beta == 0.0 ? (double)__uint_as_float(v[j])
+                                                           : o.beta * cr[col] + (double)__uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+finish:
+    if (gave_up) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        // MMAs of this CTA may still be in flight: give them a bounded wait before
+        // the tensor memory they write is released
+        if (n_commits > 0) mbar_wait(bar_a, (n_commits - 1) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+}
+
+}  // namespace
+
+bool gemm_tf32x3_eligible(const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins) {
+    for (const GemmOut& g : outs)
+        for (int c = g.beg; c < g.end; ++c)
+            if (ins[c].transA) return false;
+    return true;
+}
+
+void launch_gemm_tf32x3(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins, int kind) {
+    if (outs.empty()) return;
+    std::vector<TcTile> tiles;
+    double fl = 0.0, by = 0.0;
+    for (int o = 0; o < (int)outs.size(); ++o) {
+        const GemmOut& g = outs[o];
+        if (g.M <= 0 || g.N <= 0) continue;
+        for (int m0 = 0; m0 < g.M; m0 += kTcM)
+            for (int n0 = 0; n0 < g.N; n0 += kTcN) tiles.push_back({o, m0, n0});
+        for (int c = g.beg; c < g.end; ++c) {
+            BSM_REQUIRE(!ins[c].transA, BSMPS_ERR_INVALID_ARG, "split-precision GEMM: untransposed operands only");
+            fl += 2.0 * g.M * g.N * (double)ins[c].K;
+            by += 8.0 * ((double)g.M * ins[c].K + (double)ins[c].K * g.N);
+        }
+        by += 8.0 * g.M * (double)g.N * (g.beta == 0.0 ? 1.0 : 2.0);
+    }
+    if (tiles.empty()) return;
+    ctx->flops += fl;
+    Scratch s(ctx);
+    const GemmOut* d_outs = s.up(outs);
+    const GemmIn* d_ins = ins.empty() ? nullptr : s.up(ins);
+    const TcTile* d_tiles = s.up(tiles);
+    const int smem = kTcOperandBytes + 1024;   // room to align the operand tiles to 1024 bytes
+    static bool attr_set = false;
+    if (!attr_set) {
+        BSM_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set = true;
+    }
+    ProfScope ps(ctx, kind, fl, by);
+    k_gemm_tf32x3<<<(unsigned)tiles.size(), kTcThreads, smem, ctx->stream>>>(d_outs, d_ins, d_tiles,
+                                                                             ctx->err_word());
+    check_launch(ctx);
+    ps.done();
+}
+
+}  // namespace bsm

@@ -1,0 +1,247 @@
+// Zip-up application of the Hamiltonian MPO (Sec. 2.4) fused with the
+// left-to-right QR sweep of Sec. 2.3: u_i = (H_gamma + shift I) S_i x for a set
+// of site scalings S_i, each returned in left-orthogonal form, without forming
+// the exact cores (whose bonds are MPO width x rank).
+//
+// For y = (H + s) S x, the exact bond-t basis of a sector m is the list of
+// channel segments (a, n = m - Delta_a) of x's sector dims.  The carry
+// C_t[m] (rho_y(m) x rho_exact(m)) maps y's orthogonalised bond basis into it.
+// Site t computes, for every block (m, s') of y's core t,
+//     T[(m, s')][:, seg_b] = sum_{(a, s): W_t(a, b, s', s) != 0}  w f_s C_t[m][:, seg_a] X_t(n_a, s)
+// as one grouped GEMM over all blocks, segments and scalings (the contraction
+// stage, whose 2mnk flops are the apply's algorithmic work), then factorises,
+// per sector m' of bond t+1, the stack of the blocks (m, s') -> m' (rows in
+// layout order): no more rows than columns gives Q = I and C_{t+1}[m'] = the
+// stack; otherwise Householder QR (diag R >= 0), Q into y's core t and
+// R = C_{t+1}[m'].  The last site's blocks are y's last core.
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.h"
+#include "ops.h"
+
+namespace bsm {
+
+std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
+                                          const std::vector<std::vector<double>>& f0,
+                                          const std::vector<std::vector<double>>& f1) {
+    const Layout& X = x->lay;
+    BSM_REQUIRE(W.K == X.K && W.species == X.species, BSMPS_ERR_INVALID_ARG, "MPO and MPS act on different sites");
+    BSM_REQUIRE(f0.size() == f1.size() && !f0.empty(), BSMPS_ERR_INVALID_ARG, "scalings mismatch");
+    BSM_REQUIRE(X.columns() == 1, BSMPS_ERR_INVALID_ARG, "zip-up application of a single-column MPS");
+    const int K = X.K;
+    const int nb = (int)f0.size();
+    const auto valid = valid_sectors(X.species, X.target);
+
+    // exact bond bases: per bond b the exact sectors, and for (x sector li,
+    // channel a) the exact sector index and the segment offset in it
+    std::vector<Bond> ex(K + 1);
+    std::vector<std::vector<int>> esec(K + 1), eoff(K + 1);
+    for (int b = 0; b <= K; ++b) {
+        const int w = W.bond_dim(b), nx = (int)X.bonds[b].q.size();
+        esec[b].assign((size_t)nx * w, -1);
+        eoff[b].assign((size_t)nx * w, -1);
+        for (const Charge& m : valid[b]) {
+            const int mi = (int)ex[b].q.size();
+            int tot = 0;
+            for (int a = 0; a < w; ++a) {
+                const int li = X.bonds[b].find(m - W.charges[b][a]);
+                if (li < 0) continue;
+                esec[b][(size_t)li * w + a] = mi;
+                eoff[b][(size_t)li * w + a] = tot;
+                tot += X.bonds[b].dim[li];
+            }
+            if (tot > 0) {
+                ex[b].q.push_back(m);
+                ex[b].dim.push_back(tot);
+            }
+        }
+    }
+    std::vector<int> xlook;   // (li * 2 + sigma) -> block index of x's core t
+
+    Layout Y;
+    Y.K = K;
+    Y.species = X.species;
+    Y.target = X.target;
+    Y.bonds.assign(K + 1, Bond{});
+    Y.bonds[0] = ex[0];
+    std::vector<MpsPtr> ys(nb);
+    for (int i = 0; i < nb; ++i) {
+        ys[i].reset(new Mps);
+        ys[i]->ctx = ctx;
+        ys[i]->core.assign(K, nullptr);
+    }
+    // carry per branch and per sector of Y's bond t: device pointer, leading dimension
+    std::vector<std::vector<const double*>> carry(nb, std::vector<const double*>(Y.bonds[0].q.size(), nullptr));
+    std::vector<int> carry_ld(Y.bonds[0].q.size(), 1);
+    double* one = (double*)ctx->upload(std::vector<double>{1.0});
+    std::vector<void*> held = {one};    // device buffers the carry points into (freed one site later)
+    for (int i = 0; i < nb; ++i) carry[i][0] = one;    // C_0 = [1]: bond 0 has one sector of dim 1
+    BSM_REQUIRE(Y.bonds[0].q.size() == 1 && Y.bonds[0].dim[0] == 1, BSMPS_ERR_INVALID_ARG,
+                "bond 0 must have a single sector of dimension 1");
+
+    for (int t = 0; t < K; ++t) {
+        const int sp = X.species[t];
+        const int wl = W.bond_dim(t), wr = W.bond_dim(t + 1);
+        const Bond& yb = Y.bonds[t];
+        const int ny = (int)yb.q.size();
+        const int ne = (int)ex[t + 1].q.size();
+        xlook.assign(X.bonds[t].q.size() * 2, -1);
+        for (int bi = 0; bi < (int)X.blocks[t].size(); ++bi)
+            xlook[X.blocks[t][bi].li * 2 + X.blocks[t][bi].sigma] = bi;
+        // stacks of the exact sectors of bond t+1: blocks (mi, s') in layout order
+        struct TB {
+            int mi, so, em, r0;
+        };
+        std::vector<TB> tbs;
+        std::vector<int> rows(ne, 0);
+        for (int mi = 0; mi < ny; ++mi)
+            for (int so = 0; so < 2; ++so) {
+                const int em = ex[t + 1].find(yb.q[mi] + site_delta(sp, so));
+                if (em < 0) continue;
+                tbs.push_back({mi, so, em, rows[em]});
+                rows[em] += yb.dim[mi];
+            }
+        std::vector<int64_t> stack_off(ne, 0);
+        int64_t tsize = 0;
+        for (int em = 0; em < ne; ++em) {
+            stack_off[em] = tsize;
+            tsize += (int64_t)rows[em] * ex[t + 1].dim[em];
+        }
+        // T buffers (one per branch); at the last site they are y's last core
+        std::vector<double*> T(nb, nullptr);
+        for (int i = 0; i < nb; ++i) T[i] = tsize > 0 ? (double*)ctx->alloc((size_t)tsize * sizeof(double)) : nullptr;
+        // the contraction: one grouped GEMM for all branches
+        std::vector<GemmOut> outs;
+        std::vector<GemmIn> ins;
+        for (const TB& tb : tbs) {
+            const Charge m = yb.q[tb.mi], m2 = ex[t + 1].q[tb.em];
+            const int ldc = ex[t + 1].dim[tb.em];
+            const int em_t = ex[t].find(m);
+            // segments b of the exact sector m2: channel b with x sector n_b = m2 - Delta_b
+            for (int b = 0; b < wr; ++b) {
+                const int rb = X.bonds[t + 1].find(m2 - W.charges[t + 1][b]);
+                if (rb < 0) continue;
+                const int coff = eoff[t + 1][(size_t)rb * wr + b];
+                const int ncols = X.bonds[t + 1].dim[rb];
+                for (int i = 0; i < nb; ++i) {
+                    GemmOut o{T[i] + stack_off[tb.em] + (int64_t)tb.r0 * ldc + coff, yb.dim[tb.mi], ncols, ldc,
+                              (int)ins.size(), (int)ins.size(), 0.0};
+                    for (int ei = 0; ei < (int)W.entries[t].size(); ++ei) {
+                        const MpoEntry& e = W.entries[t][ei];
+                        if (e.so != tb.so || e.b != b) continue;
+                        const int la = X.bonds[t].find(m - W.charges[t][e.a]);
+                        if (la < 0) continue;
+                        const int xb = xlook[la * 2 + e.si];
+                        if (xb < 0) continue;
+                        const Block& bk = X.blocks[t][xb];
+                        if (bk.ri != rb) continue;
+                        double w = e.w;
+                        if (t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1])) w += shift;
+                        const std::vector<double>& f = e.si ? f1[i] : f0[i];
+                        const double fs = f.empty() ? 1.0 : f[t];
+                        const int aoff = eoff[t][(size_t)la * wl + e.a];
+                        BSM_REQUIRE(em_t >= 0 && aoff >= 0, BSMPS_ERR_INVALID_ARG, "zip-up: inconsistent bases");
+                        ins.push_back({carry[i][tb.mi] + aoff, x->core[t] + bk.off, bk.rows, carry_ld[tb.mi],
+                                       bk.cols, 0, w * fs});
+                    }
+                    o.end = (int)ins.size();
+                    outs.push_back(o);
+                }
+            }
+        }
+        launch_gemm(ctx, outs, ins, KK_APPLY);
+        // buffers of the previous site's carry are no longer read
+        for (void* p : held)
+            if (p != one) ctx->free(p);
+        held.assign(1, one);
+        if (t == K - 1) {
+            Y.bonds[K] = ex[K];
+            for (int i = 0; i < nb; ++i) ys[i]->core[t] = T[i];
+            break;
+        }
+        // new bond t+1: k = min(stacked rows, exact columns) per exact sector
+        Bond nbnd;
+        std::vector<int> newidx(ne, -1);
+        for (int em = 0; em < ne; ++em) {
+            if (rows[em] == 0) continue;
+            newidx[em] = (int)nbnd.q.size();
+            nbnd.q.push_back(ex[t + 1].q[em]);
+            nbnd.dim.push_back(std::min(rows[em], ex[t + 1].dim[em]));
+        }
+        Y.bonds[t + 1] = nbnd;
+        // the blocks of core t, (mi, s') -> (yb.dim[mi] x k(m')), in layout order (= tbs order)
+        int64_t csize = 0;
+        std::vector<int64_t> boff(tbs.size(), 0);
+        for (size_t q = 0; q < tbs.size(); ++q) {
+            boff[q] = csize;
+            csize += (int64_t)yb.dim[tbs[q].mi] * nbnd.dim[newidx[tbs[q].em]];
+        }
+        std::vector<double*> core(nb, nullptr);
+        std::vector<double*> zp;
+        std::vector<int64_t> zn;
+        for (int i = 0; i < nb; ++i) {
+            core[i] = csize > 0 ? (double*)ctx->alloc((size_t)csize * sizeof(double)) : nullptr;
+            if (core[i]) {
+                zp.push_back(core[i]);
+                zn.push_back(csize);
+            }
+        }
+        launch_zero(ctx, zp, zn);
+        std::vector<CopyTask> gather, scatter;
+        std::vector<QrTask> qr;
+        std::vector<std::vector<const double*>> ncarry(nb, std::vector<const double*>(nbnd.q.size(), nullptr));
+        std::vector<int> ncarry_ld(nbnd.q.size(), 1);
+        std::vector<void*> nheld = {one};
+        for (int em = 0; em < ne; ++em) {
+            const int ni = newidx[em];
+            if (ni < 0) continue;
+            const int M = rows[em], N = ex[t + 1].dim[em], k = nbnd.dim[ni];
+            ncarry_ld[ni] = N;
+            for (int i = 0; i < nb; ++i) {
+                if (M <= N) {
+                    // Q = I: the identity rows of each block, the stack itself is the carry
+                    ncarry[i][ni] = T[i] + stack_off[em];
+                    for (size_t q = 0; q < tbs.size(); ++q)
+                        if (tbs[q].em == em)
+                            scatter.push_back({one, core[i] + boff[q] + tbs[q].r0, yb.dim[tbs[q].mi], 1, 0, k + 1, 0,
+                                               0, 0, 1.0});
+                } else {
+                    double* A = (double*)ctx->alloc((size_t)M * N * sizeof(double));
+                    double* Q = (double*)ctx->alloc((size_t)M * k * sizeof(double));
+                    double* R = (double*)ctx->alloc((size_t)k * N * sizeof(double));
+                    double* tau = (double*)ctx->alloc((size_t)k * sizeof(double));
+                    gather.push_back({T[i] + stack_off[em], A, M, N, N, M, 0, 1, 0, 1.0});
+                    qr.push_back({A, Q, R, tau, M, N});
+                    for (size_t q = 0; q < tbs.size(); ++q)
+                        if (tbs[q].em == em)
+                            scatter.push_back({Q + tbs[q].r0, core[i] + boff[q], yb.dim[tbs[q].mi], k, M, k, 1, 0, 0,
+                                               1.0});
+                    ncarry[i][ni] = R;
+                    nheld.push_back(R);
+                    held.push_back(A);    // freed after the next site's launches (stream order)
+                    held.push_back(Q);
+                    held.push_back(tau);
+                }
+            }
+        }
+        launch_copy(ctx, gather);
+        launch_qr(ctx, qr);
+        launch_copy(ctx, scatter);
+        for (int i = 0; i < nb; ++i) {
+            ys[i]->core[t] = core[i];
+            nheld.push_back(T[i]);
+        }
+        for (void* p : nheld) held.push_back(p);
+        carry.swap(ncarry);
+        carry_ld.swap(ncarry_ld);
+    }
+    for (void* p : held)
+        if (p != one) ctx->free(p);
+    ctx->free(one);
+    Y.rebuild_blocks();
+    for (int i = 0; i < nb; ++i) ys[i]->lay = Y;
+    return ys;
+}
+
+}  // namespace bsm

@@ -34,7 +34,8 @@ class SolverParams(C.Structure):
 
 
 class SolverState(C.Structure):
-    _fields_ = [("eta_res", C.c_double), ("n", C.c_int), ("last_tries", C.c_int)]
+    _fields_ = [("eta_res", C.c_double), ("n", C.c_int), ("last_tries", C.c_int),
+                ("last_sum_norms", C.c_double), ("fp64_locked", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -42,7 +43,8 @@ class StepInfo(C.Structure):
                 ("res_norm", C.c_double), ("eta_tries", C.c_int), ("bound", C.c_double),
                 ("releig_bound", C.c_double), ("lambda_star", C.c_double), ("omega", C.c_double),
                 ("eta_in", C.c_double), ("delta_A", C.c_double), ("converged", C.c_int),
-                ("max_rank", C.c_int), ("flops", C.c_double), ("cap_discarded", C.c_double)]
+                ("max_rank", C.c_int), ("flops", C.c_double), ("cap_discarded", C.c_double),
+                ("precision", C.c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -122,6 +124,7 @@ _SIGS = {
     "bsmps_mpo_channel_charges": (_i, [_vp, _i, _pi]),
     "bsmps_mpo_destroy": (_i, [_vp]),
     "bsmps_apply_H": (_i, [_vp, _vp, _vp, _d, _d, _i, C.POINTER(_vp), _pd]),
+    "bsmps_apply_zipup": (_i, [_vp, _vp, _vp, _d, C.POINTER(_vp), _pd]),
     "bsmps_truncate": (_i, [_vp, _vp, _d, _i, C.POINTER(_vp), _pd, _pd]),
     "bsmps_add": (_i, [_vp, _vp, _vp, _d, _d, C.POINTER(_vp)]),
     "bsmps_scale_sites": (_i, [_vp, _vp, _pd, _pd, C.POINTER(_vp)]),
@@ -142,6 +145,8 @@ _SIGS = {
     "bsmps_mlp_destroy": (_i, [_vp]),
     "bsmps_eigensolve_step": (_i, [_vp, _vp, C.POINTER(Precond), C.POINTER(SolverParams),
                                    C.POINTER(SolverState), C.POINTER(_vp), C.POINTER(StepInfo)]),
+    "bsmps_gemm_tf32x3": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _i, _vp, _i]),
+    "bsmps_ctx_set_precision": (_i, [_vp, _i]),
     "bsmps_gemm_ozaki": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _i, _vp, _i, _i]),
     "bsmps_ctx_set_gemm_emulation": (_i, [_vp, _i]),
     "bsmps_mps_joint_random_size": (_i, [_i, _i, _i, _i, _i, _i, _pi64]),
@@ -209,11 +214,15 @@ class Context:
     def launch_count(self):
         return int(lib().bsmps_ctx_launch_count(self.h))
 
+    def set_precision(self, precision):
+        """Arithmetic of the zip-up contraction stage (PREC_FP64 or PREC_TF32X3)."""
+        _check(self, lib().bsmps_ctx_set_precision(self.h, int(precision)))
+
     def alloc_count(self):
         """Device-memory requests served by the context's allocator so far."""
         return int(lib().bsmps_ctx_alloc_count(self.h))
 
-    KERNELS = ("copy", "gemm", "qr", "svd", "sumsq")
+    KERNELS = ("copy", "gemm", "qr", "svd", "sumsq", "apply")
 
     def set_gemm_emulation(self, min_log2_flops=0):
         """Block products of at least 2^min_log2_flops flops on the tensor cores
@@ -439,6 +448,14 @@ def apply_H(ctx, mpo, x, shift=0.0, tol=0.0, r_max=0):
     return MPS(ctx, y), fl.value
 
 
+def apply_zipup(ctx, mpo, x, shift=0.0):
+    """(H_gamma + shift) x in left-orthogonal form by the zip-up application (bsmps_apply_zipup)."""
+    y = _vp()
+    fl = C.c_double()
+    _check(ctx, lib().bsmps_apply_zipup(ctx.h, mpo.h, x.h, shift, C.byref(y), C.byref(fl)))
+    return MPS(ctx, y), fl.value
+
+
 def truncate(ctx, x, eps, r_max=0):
     y = _vp()
     dt = C.c_double()
@@ -501,7 +518,7 @@ def solver_params(c, delta, eps_num=None, t_eig=0.5, tau=1e-8, r_max=0, u_rel=1e
 
 
 def solver_state():
-    return SolverState(math.inf, 0, 0)
+    return SolverState(math.inf, 0, 0, 0.0, 0)
 
 
 def eigensolve_step(ctx, mpo, p, params, state, x):
@@ -525,6 +542,19 @@ def eigensolve_outer(ctx, mpo, p, params, x, tau, alpha=1.0, max_outer=20, max_i
                                              max_inner, C.byref(h), recs, C.byref(n), C.byref(ok)))
     x.h = None          # destroyed by the library
     return MPS(ctx, h), [recs[i].as_dict() for i in range(n.value)], bool(ok.value)
+
+
+def gemm_tf32x3(ctx, A, B, C):
+    """C = A B (row-major float64 device tensors) on the tensor cores in split
+    precision (3xTF32, FP32 accumulation); stream-ordered on ctx's stream."""
+    M, K = A.shape
+    N = B.shape[1]
+    _check(ctx, lib().bsmps_gemm_tf32x3(ctx.h, M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                        C.data_ptr(), C.stride(0)))
+    return C
+
+
+PREC_FP64, PREC_TF32X3 = 0, 1
 
 
 def gemm_ozaki(ctx, A, B, C, slices=8):

@@ -62,3 +62,32 @@ def precond_for(wl, gamma, c0=0.1, alpha0=0.7):
 
 def oracle_mpo(wl, gamma):
     return OM.build_mpo(wl.h, wl.eri, wl.spin, wl.n_particles, gamma)
+
+
+def amplitude(x, occ):
+    """<occ|x>: the product of the blocks along the occupation string's sector path
+    (Eq. (mps)); 0 when the path leaves the stored sectors."""
+    v = np.ones((1, 1))
+    q = (0, 0)
+    for t, s in enumerate(occ):
+        key = (q, int(s))
+        if key not in x.cores[t]:
+            return 0.0
+        v = v @ x.cores[t][key]
+        q = OB.add_charge(q, OB.delta(x.species[t], int(s)))
+    return float(v[0, 0])
+
+
+def random_occupations(species, target, n, seed):
+    """n random occupation strings of the particle sector (target per species)."""
+    rng = np.random.default_rng(seed)
+    species = np.asarray(species)
+    out = []
+    for _ in range(n):
+        occ = np.zeros(len(species), dtype=np.int64)
+        for s in (0, 1):
+            sites = np.flatnonzero(species == s)
+            if target[s]:
+                occ[rng.choice(sites, size=target[s], replace=False)] = 1
+        out.append(occ)
+    return out
