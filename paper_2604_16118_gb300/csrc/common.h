@@ -125,8 +125,10 @@ struct ProfRec {
     cudaEvent_t e0, e1;
 };
 
-// KK_APPLY: the contraction stage of the zip-up MPO application (grouped GEMM)
-enum KernelKind { KK_COPY = 0, KK_GEMM = 1, KK_QR = 2, KK_SVD = 3, KK_SUMSQ = 4, KK_APPLY = 5, KK_COUNT = 6 };
+// KK_APPLY: the contraction stage of the zip-up MPO application (grouped GEMM);
+// KK_APPLY_QR: the zip-up's own factorisation launches (zeroing, gathers, QR)
+enum KernelKind { KK_COPY = 0, KK_GEMM = 1, KK_QR = 2, KK_SVD = 3, KK_SUMSQ = 4, KK_APPLY = 5, KK_APPLY_QR = 6,
+                  KK_COUNT = 7 };
 
 struct Context {
     int device = 0;

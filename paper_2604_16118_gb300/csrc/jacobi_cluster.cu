@@ -1,7 +1,7 @@
 // One-sided Jacobi of a k x k matrix (k up to kClusterJacobiMax) on one
 // thread-block cluster: the columns of G and of the rotation accumulator V are
 // spread over the shared memories of the cluster's CTAs (CTA c holds columns
-// c kc .. c kc + kc - 1, kc = ceil(k / C)), every warp of the cluster takes the
+// c kc .. c kc + kc - 1, kc = ceil(k / C), C = 16 or 8), every warp of the cluster takes the
 // column pairs of a round (the cyclic round-robin ordering of dev::jacobi) and
 // reads / writes the partner columns through distributed shared memory, and a
 // round ends at the cluster's hardware barrier instead of a grid-wide wait.
@@ -27,16 +27,16 @@ namespace cg = cooperative_groups;
 namespace bsm {
 namespace {
 
-constexpr int kClusterCtas = 8;
 constexpr int kClusterThreads = 512;
 constexpr int kClusterWarps = kClusterThreads / 32;
 constexpr size_t kClusterSmemMax = 225 * 1024;
 
-size_t cluster_smem(int k) {
-    const size_t kc = (size_t)(k + kClusterCtas - 1) / kClusterCtas;
+size_t cluster_smem(int k, int ctas) {
+    const size_t kc = (size_t)(k + ctas - 1) / ctas;
     return 2 * kc * (size_t)k * sizeof(double);
 }
 
+template <int kClusterCtas>
 __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTask* __restrict__ tasks) {
     extern __shared__ double jc_smem[];
     __shared__ double s_part[kClusterCtas];     // CTA 0's slots: partial ||G||^2 of every CTA
@@ -149,45 +149,54 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTas
     cluster.sync();
 }
 
-}  // namespace
-
-// Tasks with k <= kClusterJacobiMax, one cluster each; false (nothing launched)
-// when a cluster of this size and shared memory cannot be scheduled.
-bool launch_jacobi_cluster(Context* ctx, const std::vector<JacTask>& tasks) {
-    if (tasks.empty()) return true;
-    int kmax = 0;
-    for (const JacTask& t : tasks) kmax = std::max(kmax, t.k);
-    if (kmax > kClusterJacobiMax) return false;
-    const size_t smem = cluster_smem(kmax);
+// One launch of the C-CTA kernel; false (nothing launched) when such clusters
+// cannot be scheduled.
+template <int C>
+bool launch_cluster_size(Context* ctx, const std::vector<JacTask>& tasks, int kmax) {
+    const size_t smem = cluster_smem(kmax, C);
     if (smem > kClusterSmemMax) return false;
-    static size_t attr_smem = 0;
-    if (smem > attr_smem) {
-        BSM_CUDA(cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static bool attr = false;
+    if (!attr) {
+        BSM_CUDA(cudaFuncSetAttribute(k_jacobi_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kClusterSmemMax));
-        attr_smem = kClusterSmemMax;
+        if (C > 8) BSM_CUDA(cudaFuncSetAttribute(k_jacobi_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        attr = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(tasks.size() * kClusterCtas));
+    cfg.gridDim = dim3((unsigned)(tasks.size() * C));
     cfg.blockDim = dim3(kClusterThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = ctx->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kClusterCtas;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
+    cudaLaunchAttribute attr_l[1];
+    attr_l[0].id = cudaLaunchAttributeClusterDimension;
+    attr_l[0].val.clusterDim.x = C;
+    attr_l[0].val.clusterDim.y = 1;
+    attr_l[0].val.clusterDim.z = 1;
+    cfg.attrs = attr_l;
     cfg.numAttrs = 1;
     int n_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&n_clusters, k_jacobi_cluster, &cfg) != cudaSuccess || n_clusters < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n_clusters, k_jacobi_cluster<C>, &cfg) != cudaSuccess || n_clusters < 1) {
         (void)cudaGetLastError();
         return false;
     }
     Scratch s(ctx);
     const JacTask* d = s.up(tasks);
-    BSM_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_cluster, d));
+    BSM_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_cluster<C>, d));
     check_launch(ctx);
     return true;
+}
+
+}  // namespace
+
+// Tasks with k <= kClusterJacobiMax, one cluster each: 16 CTAs per cluster when
+// such clusters can be scheduled (more FP64 units per matrix), else 8; false
+// (nothing launched) when neither can.
+bool launch_jacobi_cluster(Context* ctx, const std::vector<JacTask>& tasks) {
+    if (tasks.empty()) return true;
+    int kmax = 0;
+    for (const JacTask& t : tasks) kmax = std::max(kmax, t.k);
+    if (kmax > kClusterJacobiMax) return false;
+    return launch_cluster_size<16>(ctx, tasks, kmax) || launch_cluster_size<8>(ctx, tasks, kmax);
 }
 
 }  // namespace bsm

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_zero(const ZeroChunk* __restrict__
     for (int64_t e = threadIdx.x; e < c.n; e += kThreads) c.p[e] = 0.0;
 }
 
-void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n) {
+void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n, int kind) {
     std::vector<ZeroChunk> chunks;
     for (size_t i = 0; i < ptr.size(); ++i)
         for (int64_t b = 0; b < n[i]; b += kCopyChunk) chunks.push_back({ptr[i] + b, std::min(n[i] - b, kCopyChunk)});
@@ -255,7 +255,7 @@ void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vecto
     configure_carveout();
     Scratch s(ctx);
     const ZeroChunk* d = s.up(chunks);
-    ProfScope ps(ctx, KK_COPY, 0.0, 8.0 * [&] {
+    ProfScope ps(ctx, kind, 0.0, 8.0 * [&] {
         double t = 0.0;
         for (int64_t v : n) t += (double)v;
         return t;
@@ -265,7 +265,7 @@ void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vecto
     ps.done();
 }
 
-void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
+void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks, int kind) {
     if (tasks.empty()) return;
     configure_carveout();
     std::vector<CopyChunk> chunks;
@@ -279,7 +279,7 @@ void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks) {
     Scratch s(ctx);
     CopyTask* dt = s.up(tasks);
     CopyChunk* dc = s.up(chunks);
-    ProfScope ps(ctx, KK_COPY, 0.0, by);
+    ProfScope ps(ctx, kind, 0.0, by);
     k_copy<<<(unsigned)chunks.size(), kThreads, 0, ctx->stream>>>(dt, dc);
     check_launch(ctx);
     ps.done();
@@ -364,13 +364,20 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
 
 constexpr size_t kSmemBudget = 220 * 1024;
 
-void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in) {
+void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in, int kind) {
     if (tasks_in.empty()) return;
     configure_carveout();
     double fl = 0.0, by = 0.0;
-    std::vector<QrTask> small, large;
+    std::vector<QrTask> small, large, clustered;
     size_t smem_max = 0;
     for (QrTask t : tasks_in) {
+        if (qr_cluster_eligible(t.M, t.N)) {
+            const double m = t.M, n = t.N, k = std::min(m, n);
+            fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k + 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;
+            by += 8.0 * (m * n + m * k + k * n);
+            clustered.push_back(t);
+            continue;
+        }
         const double m = t.M, n = t.N, k = std::min(m, n);
         fl += 2.0 * m * n * k - (m + n) * k * k + 2.0 / 3.0 * k * k * k;   // factorisation
         fl += 2.0 * m * k * k - 2.0 / 3.0 * k * k * k;                     // forming Q
@@ -388,7 +395,16 @@ void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in) {
     }
     ctx->flops += fl;
     Scratch s(ctx);
-    ProfScope ps(ctx, KK_QR, fl, by);
+    ProfScope ps(ctx, kind, fl, by);
+    if (!clustered.empty() && !launch_qr_cluster(ctx, clustered)) {
+        for (QrTask t : clustered) {   // no cluster could be scheduled: one CTA per matrix
+            const size_t need = sizeof(double) * ((size_t)t.M * t.N + (size_t)t.M * std::min(t.M, t.N) +
+                                                  (size_t)std::min(t.M, t.N));
+            t.smem = need <= kSmemBudget ? 1 : 0;
+            if (t.smem) smem_max = std::max(smem_max, need);
+            (t.smem ? small : large).push_back(t);
+        }
+    }
     if (!small.empty()) {
         QrTask* d = s.up(small);
         BSM_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));

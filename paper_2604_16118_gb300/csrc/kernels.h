@@ -109,9 +109,10 @@ struct OzGemm {
 };
 void launch_gemm_ozaki_group(Context* ctx, const std::vector<OzGemm>& gs, int S);
 
-void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks);
+void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks, int kind = KK_COPY);
 // Sets n[i] doubles at ptr[i] to zero, all regions in one launch.
-void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n);
+void launch_zero(Context* ctx, const std::vector<double*>& ptr, const std::vector<int64_t>& n,
+                 int kind = KK_COPY);
 // Counts a launch and raises the launch error, if any.
 void check_launch(Context* ctx);
 // The same grouped GEMM on the tensor cores in split precision (3xTF32, FP32
@@ -123,7 +124,13 @@ void launch_gemm_tf32x3(Context* ctx, const std::vector<GemmOut>& outs, const st
 // precision is BSMPS_PREC_TF32X3)
 void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins,
                  int kind = KK_GEMM);
-void launch_qr(Context* ctx, const std::vector<QrTask>& tasks);
+void launch_qr(Context* ctx, const std::vector<QrTask>& tasks, int kind = KK_QR);
+// Householder QR of one matrix on a thread-block cluster (csrc/qr_cluster.cu),
+// same output as a QrTask of launch_qr; used by launch_qr for matrices with
+// min(M, N) >= kClusterQrMin whose columns fit the cluster's shared memory.
+constexpr int kClusterQrMin = 48;
+bool qr_cluster_eligible(int M, int N);
+bool launch_qr_cluster(Context* ctx, const std::vector<QrTask>& tasks);
 void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks);
 // out[i] = sum of squares of x[0..n) for a list of (x, n) segments
 void launch_sumsq(Context* ctx, const std::vector<const double*>& xs, const std::vector<int64_t>& ns,

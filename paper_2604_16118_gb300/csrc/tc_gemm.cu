@@ -5,6 +5,13 @@
 // below 2^-21 relative, is dropped).  The relative error of an entry is a few
 // units of 2^-21 times sum_k |a_ik| |b_kj| plus the FP32 accumulation error.
 //
+// Every row i of a tile is scaled by 2^-e_i and every column j by 2^-f_j before
+// the split, with e_i (f_j) the exponent of the largest |alpha a_ik| (|b_kj|)
+// over all contributions of the output: the scaling is exact, keeps every
+// operand in TF32's range whatever the magnitudes of the FP64 data (MPS blocks
+// can carry factors far outside the FP32 range), and is undone in FP64 when the
+// tile is stored (C_ij = acc_ij 2^(e_i + f_j)).
+//
 // One CTA computes one 128 x 64 output tile of one grouped-GEMM output: 4 warps
 // stage 32-wide k chunks of every contribution in shared memory (FP64 loads,
 // split, canonical K-major layout without swizzle), one thread issues the
@@ -69,6 +76,13 @@ __device__ __forceinline__ void tf32_split(double v, uint32_t* hi, uint32_t* lo)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Exponent e with 2^-e x in [1, 2) for the largest magnitude x given by its bit
+// pattern (0 for x = 0: such rows and columns hold zeros only).
+__device__ __forceinline__ int pow2_exponent(unsigned long long bits) {
+    if (bits == 0ull) return 0;
+    return (int)((bits >> 52) & 0x7ff) - 1023;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -107,6 +121,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int gave_up;
+    __shared__ unsigned long long row_max[kTcM], col_max[kTcN];
+    __shared__ int row_sc[kTcM], col_sc[kTcN];
     unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
     unsigned char* a_hi = base;
     unsigned char* a_lo = a_hi + kTcM * kTcK * 4;
@@ -122,6 +138,34 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    // row and column scales: largest magnitudes (as ordered bit patterns of
+    // non-negative doubles) over every contribution, then powers of two
+    for (int r = threadIdx.x; r < kTcM; r += kTcThreads) row_max[r] = 0ull;
+    for (int c = threadIdx.x; c < kTcN; c += kTcThreads) col_max[c] = 0ull;
+    __syncthreads();
+    for (int c = o.beg; c < o.end; ++c) {
+        const GemmIn in = ins[c];
+        const double aa = fabs(in.alpha);
+        for (int r = warp; r < kTcM; r += kTcThreads / 32) {
+            const int gm = tl.m0 + r;
+            if (gm >= o.M) break;
+            double mx = 0.0;
+            for (int k = lane; k < in.K; k += 32) mx = fmax(mx, fabs(in.A[(int64_t)gm * in.lda + k]));
+            for (int d = 16; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+            if (lane == 0 && mx * aa > 0.0) atomicMax(&row_max[r], (unsigned long long)__double_as_longlong(mx * aa));
+        }
+        for (int n = threadIdx.x; n < kTcN; n += kTcThreads) {
+            const int gn = tl.n0 + n;
+            if (gn >= o.N) continue;
+            double mx = 0.0;
+            for (int k = 0; k < in.K; ++k) mx = fmax(mx, fabs(in.B[(int64_t)k * in.ldb + gn]));
+            if (mx > 0.0) atomicMax(&col_max[n], (unsigned long long)__double_as_longlong(mx));
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < kTcM; r += kTcThreads) row_sc[r] = pow2_exponent(row_max[r]);
+    for (int c = threadIdx.x; c < kTcN; c += kTcThreads) col_sc[c] = pow2_exponent(col_max[c]);
+    __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                      "r"(kTcN));
@@ -148,7 +192,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
             for (int idx = threadIdx.x; idx < kTcM * kTcK; idx += kTcThreads) {
                 const int r = idx / kTcK, k = idx % kTcK;
                 const int gm = tl.m0 + r, gk = k0 + k;
-                const double v = (gm < o.M && gk < in.K) ? in.alpha * in.A[(int64_t)gm * in.lda + gk] : 0.0;
+                const double v = (gm < o.M && gk < in.K)
+                                     ? ldexp(in.alpha * in.A[(int64_t)gm * in.lda + gk], -row_sc[r]) : 0.0;
                 uint32_t hi, lo;
                 tf32_split(v, &hi, &lo);
                 const uint32_t off = tc_off(r, k);
@@ -159,7 +204,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
             for (int idx = threadIdx.x; idx < kTcN * kTcK; idx += kTcThreads) {
                 const int k = idx / kTcN, n = idx % kTcN;
                 const int gk = k0 + k, gn = tl.n0 + n;
-                const double v = (gk < in.K && gn < o.N) ? in.B[(int64_t)gk * in.ldb + gn] : 0.0;
+                const double v = (gk < in.K && gn < o.N) ? ldexp(in.B[(int64_t)gk * in.ldb + gn], -col_sc[n]) : 0.0;
                 uint32_t hi, lo;
                 tf32_split(v, &hi, &lo);
                 const uint32_t off = tc_off(n, k);
@@ -218,8 +263,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = tl.n0 + c0 + j;
-                    if (col < o.N) cr[col] = o.beta == 0.0 ? (double)__uint_as_float(v[j])
-                                                           : o.beta * cr[col] + (double)__uint_as_float(v[j]);
+                    const double acc = ldexp((double)__uint_as_float(v[j]), row_sc[warp * 32 + lane] + col_sc[c0 + j]);
+                    if (col < o.N) cr[col] = o.beta == 0.0 ? acc : o.beta * cr[col] + acc;
                 }
             }
         }

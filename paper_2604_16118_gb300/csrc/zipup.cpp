@@ -187,7 +187,7 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
                 zn.push_back(csize);
             }
         }
-        launch_zero(ctx, zp, zn);
+        launch_zero(ctx, zp, zn, KK_APPLY_QR);
         std::vector<CopyTask> gather, scatter;
         std::vector<QrTask> qr;
         std::vector<std::vector<const double*>> ncarry(nb, std::vector<const double*>(nbnd.q.size(), nullptr));
@@ -225,9 +225,9 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
                 }
             }
         }
-        launch_copy(ctx, gather);
-        launch_qr(ctx, qr);
-        launch_copy(ctx, scatter);
+        launch_copy(ctx, gather, KK_APPLY_QR);
+        launch_qr(ctx, qr, KK_APPLY_QR);
+        launch_copy(ctx, scatter, KK_APPLY_QR);
         for (int i = 0; i < nb; ++i) {
             ys[i]->core[t] = core[i];
             nheld.push_back(T[i]);

@@ -15,9 +15,10 @@ Training data come from the plain solver: for every problem of a set, each
 the decrease of the energy per GFLOP; the label is the best grid point.  At
 run time the prediction is snapped to the grid, so every parameter set the
 controller uses is a valid plain-preconditioner parameter set.  The plain
-parameters (c_0 = 0.1, the paper's value, margin 1) are the fallback: they are
-used when the prediction is not finite, and the controller switches back to
-them when a learned step fails to lower the Rayleigh quotient.
+parameters (c_0 = 0.1, the paper's value, margin 1) are the fallback and the
+judge: they are used when the prediction is not finite, and a learned step whose
+result misses the per-step guarantee of Thm. conv is redone with them (the run
+then stays with them).
 """
 
 import math
@@ -164,16 +165,54 @@ def choose(net, wl):
 
 
 def solve(ctx, net, wl, n_steps, r_max=64):
-    """Alg. 2 steps with the learned parameters; the plain parameters take over
-    (from the current iterate's energy scale, restarting from e_1) when a
-    learned step raises the Rayleigh quotient or the prediction is unusable.
-    Returns (energies, flops, used parameters)."""
-    params = choose(net, wl)
+    """Alg. 2 steps with the learned parameters, each judged against the plain
+    guarantee of Thm. conv: the energy after a learned step must satisfy
+    E(x') <= E_* + t_eig (E(x) - E_*) with E_* the step's lower Ritz value (all
+    energies lambda - gamma, since the shifts of the two parameter sets differ).
+    A step that misses it is redone from x with the plain parameters, which are
+    kept from then on (as they are when the prediction is unusable).  Returns
+    (energies at the start of every step, flops per step, parameters per step)."""
+    learned = choose(net, wl)
+    plain_s = setup(ctx, wl, PLAIN[0], PLAIN[1], r_max)
     try:
-        E, F, _ = run(ctx, wl, params[0], params[1], n_steps, r_max)
+        learned_s = setup(ctx, wl, learned[0], learned[1], r_max) if learned != PLAIN else plain_s
     except (ValueError, nat.BsmpsError):
-        E, F = [], []
-    if len(E) < 2 or any(b > a + 1e-12 * abs(a) for a, b in zip(E, E[1:])) or not all(map(math.isfinite, E)):
-        params = PLAIN
-        E, F, _ = run(ctx, wl, PLAIN[0], PLAIN[1], n_steps, r_max)
-    return E, F, params
+        learned, learned_s = PLAIN, plain_s
+    use_plain = learned == PLAIN
+    st = nat.solver_state()
+    x = nat.mps_create(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn)
+    E, F, used = [], [], []
+    pending = None        # (x before the learned step, its energy, E_*, state copy)
+    t_eig = SOLVER["t_eig"]
+    for _ in range(n_steps):
+        S = plain_s if use_plain else learned_s
+        x_prev = x.export(), x.bonds()
+        st_prev = nat.SolverState(st.eta_res, st.n, st.last_tries, st.last_sum_norms, st.fp64_locked)
+        x, info = nat.eigensolve_step(ctx, S["W"], S["p"], S["sp"], st, x)
+        e = info["lambda"] - S["gamma"]
+        if pending is not None:
+            e_prev, e_star = pending
+            if e > e_star + t_eig * (e_prev - e_star) + 1e-12 * abs(e_prev):
+                # the learned step missed the plain guarantee: redo it with the plain parameters
+                use_plain = True
+                hx, bonds = pending_x
+                st = pending_st
+                x = nat.mps_import(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, bonds, hx)
+                used[-1] = PLAIN
+                x, info = nat.eigensolve_step(ctx, plain_s["W"], plain_s["p"], plain_s["sp"], st, x)
+                F[-1] = info["flops"]
+                e_redo = info["lambda"] - plain_s["gamma"]
+                E[-1] = e_redo
+                x, info = nat.eigensolve_step(ctx, plain_s["W"], plain_s["p"], plain_s["sp"], st, x)
+                e = info["lambda"] - plain_s["gamma"]
+                S = plain_s
+        pending = None
+        E.append(e)
+        F.append(info["flops"])
+        used.append(PLAIN if S is plain_s else learned)
+        if info["converged"]:
+            break
+        if S is learned_s and "lambda_star" in info:
+            pending = (e, info["lambda_star"] - S["gamma"])
+            pending_x, pending_st = x_prev, st_prev
+    return E, F, used
