@@ -916,6 +916,173 @@ def main_tta(args):
     return 0
 
 
+def main_tta_k12(args):
+    """Time to |E - E_ref| <= 1e-8 on the spinless random chain K = 12, N = 6 of
+    the config-1 generator (seed 0) from its random start of rank 32 (seed 0),
+    without a rank cap (the cap of 32 leaves an error near 3e-4): Alg. 2 steps
+    with the constants and the exact E_ref = lambda_1 - gamma stored by
+    tests/golden/make_config1_trajectory.py; the contraction precision from
+    --precision."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_16118_gb300 import build
+    build.build()
+    from paper_2604_16118_gb300 import native as nat
+    from synth import random_block_values, spinless_random_chain
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_config1_trajectory.json")) as f:
+        g = json.load(f)
+    w, cst = g["workload"], g["constants"]
+    wl = spinless_random_chain(K=w["K"], N=w["N"], seed=w["seed"])
+    e_ref = cst["lambda1"] - cst["gamma"]
+    stream = torch.cuda.Stream(device=dev)
+    ctx = nat.Context(local, stream.cuda_stream)
+    W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, 0, wl.n_up, cst["gamma"])
+    p = nat.make_precond(np.array(cst["theta"]), cst["t_min"], cst["t_max"], cst["c0"], cst["alpha0"])
+    sp = nat.solver_params(cst["c"], cst["delta"], eps_num=cst["eps_num"], t_eig=cst["t_eig"], tau=1e-12, r_max=0)
+    vals = random_block_values(w["n_values"], w["seed"])
+    ctx.set_precision(nat.PREC_TF32X3 if args.precision == "tf32x3" else nat.PREC_FP64)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x = nat.mps_create(ctx, wl.n_orb, 0, wl.n_up, 0, w["r_max"], vals)
+    st = nat.solver_state()
+    recs, reached = [], None
+    for n in range(args.max_steps):
+        x, info = nat.eigensolve_step(ctx, W, p, sp, st, x)
+        el = time.perf_counter() - t0
+        err = info["lambda"] - cst["gamma"] - e_ref
+        recs.append({"n": n, "t": el, "error": err, "rho": info["rho"], "max_rank": info["max_rank"],
+                     "precision": info["precision"]})
+        if abs(err) <= 1e-8 and reached is None:
+            reached = el
+            break
+        if info["converged"] or el > args.max_seconds:
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    out = {"metric": "time to |E - E_ref| <= 1e-8 Eh (Alg. 2, exact E_ref)", "value": reached, "unit": "s",
+           "n_gpus": 1, "steps": len(recs), "warmup": 0, "ms_per_step": 1e3 * wall / max(len(recs), 1),
+           "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (tf32x3 contraction)",
+           "data": "synthetic",
+           "config": {"workload": "spinless_random_chain K=12 N=6 seed 0 (config-1 generator), random start of "
+                                  "rank 32, no rank cap, constants and E_ref by exact diagonalisation",
+                      "precision": args.precision, "l2": "not flushed (one solve)"},
+           "clocks": clocks, "wall_s": wall, "final_error": recs[-1]["error"] if recs else None,
+           "split_steps": sum(1 for r in recs if r["precision"] != 0), "trajectory": recs,
+           "e2e": {"value": reached, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main_batched(args):
+    """The batched form: zip-up applications of 128 independent molecule-like
+    Hamiltonians (the generator of configs 3 and 4; L cycling through 3..6,
+    N = L, ranks cycling through 64, 128, 256, 512, capped by the exact ranks;
+    seeds 1000 + i) in one batched call, against one call per instance.  Each is
+    timed with events on the library's stream after a warm-up (which also fixes
+    the contraction autotuner's choices), L2 flushed before every repetition."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_16118_gb300 import build, problem
+    build.build()
+    from paper_2604_16118_gb300 import native as nat
+    from synth import molecule_like, random_block_values
+    stream = torch.cuda.Stream(device=dev)
+    ctx = nat.Context(local, stream.cuda_stream)
+    n_inst = 128
+    Ls, ranks = (3, 4, 5, 6), (64, 128, 256, 512)
+    Ws, xs, shifts, shapes = [], [], [], []
+    for i in range(n_inst):
+        L, r = Ls[i % 4], ranks[(i // 4) % 4]
+        wl = molecule_like(L=L, n_up=(L + 1) // 2, n_dn=L // 2, seed=1000 + i)
+        gamma = problem.cholesky_shift(wl.h, wl.eri, wl.n_up, wl.n_dn, 1, margin=1.0)
+        nval = nat.mps_random_size(L, 1, wl.n_up, wl.n_dn, r)
+        xs.append(nat.mps_create(ctx, L, 1, wl.n_up, wl.n_dn, r, random_block_values(nval, 1000 + i)))
+        Ws.append(nat.mpo_from_integrals(ctx, wl.h, wl.eri, 1, wl.n_particles, gamma))
+        shifts.append(-1.0)
+        shapes.append((L, r, max(xs[-1].ranks())))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        ms = []
+        for it in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            del out
+            if it >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    fl = nat.apply_zipup_batch(ctx, Ws, xs, shifts)[1]
+    l0 = ctx.launch_count()
+    ms_batch = timed(lambda: nat.apply_zipup_batch(ctx, Ws, xs, shifts))
+    lb = (ctx.launch_count() - l0) // (args.warmup + args.steps)
+    l0 = ctx.launch_count()
+    ms_single = timed(lambda: [nat.apply_zipup(ctx, W, x, s) for W, x, s in zip(Ws, xs, shifts)])
+    ls = (ctx.launch_count() - l0) // (args.warmup + args.steps)
+    out = {"metric": "MPO.MPS apply, 128 independent Hamiltonians, TFLOP/s", "value": fl / (ms_batch * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "128 molecule-like Hamiltonians (L cycling 3..6, N = L, r cycling 64..512 capped "
+                                  "by the exact ranks), zip-up application of a random iterate each",
+                      "l2": "flushed before every repetition"},
+           "batched": {"ms": ms_batch, "launches": lb, "tflops": fl / (ms_batch * 1e-3) / 1e12},
+           "one_by_one": {"ms": ms_single, "launches": ls, "tflops": fl / (ms_single * 1e-3) / 1e12},
+           "speedup": ms_single / ms_batch, "flops": fl,
+           "max_ranks": sorted(set(s[2] for s in shapes)),
+           "e2e": {"value": fl / (ms_batch * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main_profile(args):
+    """Small fixed runs for profilers (no timing of their own):
+    profile_step: one Alg. 2 step of the default workload (Hubbard L = 32 from the
+    seed-1 rank-256 iterate); profile_apply: the zip-up application of that
+    iterate, twice; profile_truncation: one truncation of a random spinless
+    K = 20, N = 10 iterate at exact ranks (sectors up to 252 wide).
+    --precision selects the contraction arithmetic."""
+    from paper_2604_16118_gb300 import build
+    build.build()
+    from paper_2604_16118_gb300 import native as nat
+    ctx = nat.Context(0)
+    ctx.set_precision(nat.PREC_TF32X3 if args.precision == "tf32x3" else nat.PREC_FP64)
+    t0 = time.perf_counter()
+    if args.workload == "profile_truncation":
+        from synth import random_block_values
+        n = nat.mps_random_size(20, 0, 10, 0, 1024)
+        x = nat.mps_create(ctx, 20, 0, 10, 0, 1024, random_block_values(n, 7))
+        z, _, _ = nat.truncate(ctx, x, 1e-3)
+        what = {"max_rank": max(z.ranks())}
+    else:
+        S = setup(ctx, nat, seed=1)
+        if args.workload == "profile_apply":
+            for _ in range(2):
+                y, fl = nat.apply_zipup(ctx, S["W"], S["x"], shift=-70.0)
+            what = {"flops": fl, "max_rank": max(y.ranks())}
+        else:
+            _, info = nat.eigensolve_step(ctx, S["W"], S["p"], S["sp"], nat.solver_state(), S["x"])
+            what = {"lambda": info["lambda"], "rho": info["rho"], "flops": info["flops"]}
+    ctx.sync()
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "wall_s": time.perf_counter() - t0,
+                      **what}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -928,8 +1095,8 @@ def main():
     ap.add_argument("--max-steps", type=int, default=400, help="hubbard_tta: step limit")
     ap.add_argument("--max-seconds", type=float, default=1800.0, help="hubbard_tta: time limit")
     ap.add_argument("--workload", default="hubbard",
-                    choices=["hubbard", "hubbard_e1", "hubbard_tta", "coulomb14_alg4_D4", "coulomb14_alg3",
-                             "ozaki_gemm"],
+                    choices=["hubbard", "hubbard_e1", "hubbard_tta", "tta_k12", "batched", "coulomb14_alg4_D4",
+                             "coulomb14_alg3", "ozaki_gemm", "profile_step", "profile_apply", "profile_truncation"],
                     help="hubbard: Alg. 2 steps at full rank (the JSON contract); hubbard_e1: the trajectory "
                          "from e_1; hubbard_tta: time to convergence from e_1; coulomb14_alg4_D4: Alg. 4 (D = 4); "
                          "coulomb14_alg3: time to solution of the paper's K = 14 run; "
@@ -943,6 +1110,12 @@ def main():
         return main_ozaki(args)
     if args.workload == "hubbard_tta":
         return main_tta(args)
+    if args.workload == "tta_k12":
+        return main_tta_k12(args)
+    if args.workload == "batched":
+        return main_batched(args)
+    if args.workload.startswith("profile_"):
+        return main_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "hubbard_e1":

@@ -336,6 +336,19 @@ BSMPS_API bsmps_status bsmps_apply_H(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, do
 BSMPS_API bsmps_status bsmps_apply_zipup(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double shift, bsmps_mps* y,
                                          double* flops);
 
+/* The zip-up application of bsmps_apply_zipup for n independent problems
+ * y[i] = (H_i + shift[i] I) x[i] (W[i] the operator of x[i]; the problems may
+ * differ in operator, sites, particle numbers and ranks), advanced together:
+ * site t of every problem that has one shares one grouped-GEMM launch for the
+ * contraction and one launch each for the zeroing, gathers, QRs and scatters of
+ * the factorisation.  Results equal those of n separate bsmps_apply_zipup
+ * calls to rounding (the contraction's kernel split is autotuned per launch
+ * size class, so sums may be ordered differently).  W, x, shift: n entries, host
+ * arrays; y: n new handles.  flops (may be NULL): algorithmic FP64 flops of the
+ * batch.  Errors: INVALID_ARG, OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_apply_zipup_batch(bsmps_ctx ctx, int n, const bsmps_mpo* W, const bsmps_mps* x,
+                                               const double* shift, bsmps_mps* y, double* flops);
+
 /* trunc_eps (Sec. 2.2, Eq. (ttsvdquasiopt)): QR sweep left to right (diag R
  * >= 0), then right to left SVD of [X_b(n,0) | X_b(n,1)] per left sector;
  * at every bond the pooled singular values are discarded from the smallest

@@ -677,6 +677,24 @@ bsmps_status bsmps_apply_zipup(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x, double s
     });
 }
 
+bsmps_status bsmps_apply_zipup_batch(bsmps_ctx ctx, int n, const bsmps_mpo* W, const bsmps_mps* x,
+                                     const double* shift, bsmps_mps* y, double* flops) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(n >= 0 && (n == 0 || (W && x && shift && y)), BSMPS_ERR_INVALID_ARG, "null argument");
+        std::vector<bsm::ZipProblem> probs;
+        for (int i = 0; i < n; ++i) {
+            BSM_REQUIRE(W[i] && x[i], BSMPS_ERR_INVALID_ARG, "null handle in the batch");
+            probs.push_back({&W[i]->W, M(x[i]), shift[i], {{}}, {{}}});
+        }
+        const double f0 = c->flops;
+        std::vector<std::vector<bsm::MpsPtr>> r = bsm::op_apply_zipup_batch(c, probs);
+        c->sync();
+        if (flops) *flops = c->flops - f0;
+        for (int i = 0; i < n; ++i) y[i] = wrap(std::move(r[i][0]));
+    });
+}
+
 bsmps_status bsmps_truncate(bsmps_ctx ctx, bsmps_mps x, double eps, int r_max, bsmps_mps* y, double* disc_tol,
                             double* disc_cap) {
     return guarded(ctx, [&] {

@@ -286,12 +286,12 @@ void launch_copy(Context* ctx, const std::vector<CopyTask>& tasks, int kind) {
 }
 
 
-void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins, int kind) {
-    if (outs.empty()) return;
-    if (kind == KK_APPLY && ctx->apply_precision == BSMPS_PREC_TF32X3 && gemm_tf32x3_eligible(outs, ins)) {
-        launch_gemm_tf32x3(ctx, outs, ins, kind);
-        return;
-    }
+namespace {
+
+// The FP64 grouped GEMM with outputs of max(M, N) <= small_max on the
+// one-thread-per-entry kernel and the rest on 32 x 32 tiles (small_max <= 32).
+void launch_gemm_fp64(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins, int kind,
+                      int small_max) {
     configure_carveout();
     std::vector<GemmTile> tiles;
     std::vector<int> small, emulated;
@@ -307,7 +307,7 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
             emulated.push_back(o);
             continue;
         }
-        if (g.M <= kTile && g.N <= kTile) {
+        if (std::max(g.M, g.N) <= small_max) {
             if (g.M > 0 && g.N > 0) small.push_back(o);
         } else {
             for (int m0 = 0; m0 < g.M; m0 += kTile)
@@ -360,6 +360,78 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
         check_launch(ctx);
     }
     ps.done();
+}
+
+// Size class of a contraction launch for the autotuner: the fractions of
+// outputs with max(M, N) <= 8, <= 16, <= 32 (in quarters) and log2 of the flops.
+int64_t gemm_size_class(const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins) {
+    int64_t c8 = 0, c16 = 0, c32 = 0;
+    double fl = 0.0;
+    for (const GemmOut& g : outs) {
+        const int mx = std::max(g.M, g.N);
+        c8 += mx <= 8;
+        c16 += mx <= 16;
+        c32 += mx <= 32;
+        for (int c = g.beg; c < g.end; ++c) fl += 2.0 * g.M * g.N * (double)ins[c].K;
+    }
+    const int64_t n = std::max<int64_t>((int64_t)outs.size(), 1);
+    const int64_t q8 = 4 * c8 / n, q16 = 4 * c16 / n, q32 = 4 * c32 / n;
+    const int64_t lf = fl > 1.0 ? (int64_t)std::log2(fl) : 0;
+    return ((q8 * 5 + q16) * 5 + q32) * 64 + std::min<int64_t>(lf, 63);
+}
+
+}  // namespace
+
+// The zip-up contraction (kind KK_APPLY) in FP64 is autotuned: the split
+// between the one-thread-per-entry kernel and the 32 x 32 tiled kernel
+// (small_max in {0, 8, 16, 32}) is chosen per context and size class by timing
+// every candidate on the first launch of that class (the contraction overwrites
+// its outputs, so the repeats change nothing) and kept for later launches.
+void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vector<GemmIn>& ins, int kind) {
+    if (outs.empty()) return;
+    if (kind == KK_APPLY && ctx->apply_precision == BSMPS_PREC_TF32X3 && gemm_tf32x3_eligible(outs, ins)) {
+        launch_gemm_tf32x3(ctx, outs, ins, kind);
+        return;
+    }
+    if (kind != KK_APPLY || !ctx->autotune) {
+        launch_gemm_fp64(ctx, outs, ins, kind, kTile);
+        return;
+    }
+    for (const GemmOut& g : outs)
+        if (g.beta != 0.0) {   // accumulating outputs cannot be repeated
+            launch_gemm_fp64(ctx, outs, ins, kind, kTile);
+            return;
+        }
+    const int64_t key = gemm_size_class(outs, ins);
+    auto it = ctx->gemm_tuned.find(key);
+    if (it != ctx->gemm_tuned.end()) {
+        launch_gemm_fp64(ctx, outs, ins, kind, it->second);
+        return;
+    }
+    const int cand[4] = {0, 8, 16, 32};
+    float best_ms = 0.0f;
+    int best = kTile;
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;   // tuning launches are not part of the profile
+    cudaEvent_t e0 = ctx->take_event(), e1 = ctx->take_event();
+    for (int c : cand) {
+        BSM_CUDA(cudaEventRecord(e0, ctx->stream));
+        launch_gemm_fp64(ctx, outs, ins, kind, c);
+        BSM_CUDA(cudaEventRecord(e1, ctx->stream));
+        BSM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        BSM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (c == cand[0] || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    ctx->event_pool.push_back(e0);
+    ctx->event_pool.push_back(e1);
+    ctx->profiling = prof;
+    ctx->gemm_tuned[key] = best;
+    // the launch that counts (and is profiled)
+    launch_gemm_fp64(ctx, outs, ins, kind, best);
 }
 
 constexpr size_t kSmemBudget = 220 * 1024;

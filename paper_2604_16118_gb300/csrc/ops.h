@@ -50,6 +50,16 @@ std::vector<MpsPtr> op_apply_exact_scaled(Context* ctx, const Mpo& W, const Mps*
 std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
                                           const std::vector<std::vector<double>>& f0,
                                           const std::vector<std::vector<double>>& f1);
+// Several independent zip-up applications (different operators, iterates and
+// sizes) advanced together: site t of every problem shares the launches of that
+// site.  Result j holds the branches of problem j.
+struct ZipProblem {
+    const Mpo* W;
+    const Mps* x;
+    double shift;
+    std::vector<std::vector<double>> f0, f1;   // per branch (empty inner vector: no scaling)
+};
+std::vector<std::vector<MpsPtr>> op_apply_zipup_batch(Context* ctx, const std::vector<ZipProblem>& probs);
 
 // trunc_eps of left-orthogonal MPS: the right SVD sweep alone (the left QR
 // sweep of a truncation leaves such an MPS as it is, up to the bond gauge).

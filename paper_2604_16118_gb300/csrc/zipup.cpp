@@ -14,6 +14,10 @@
 // layout order): no more rows than columns gives Q = I and C_{t+1}[m'] = the
 // stack; otherwise Householder QR (diag R >= 0), Q into y's core t and
 // R = C_{t+1}[m'].  The last site's blocks are y's last core.
+//
+// Several independent problems (different operators, iterates and sizes) run
+// together: site t of every problem that has one shares the grouped-GEMM
+// launch and the zeroing, gather, QR and scatter launches of that site.
 #include <algorithm>
 #include <cmath>
 
@@ -21,80 +25,91 @@
 #include "ops.h"
 
 namespace bsm {
+namespace {
 
-std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
-                                          const std::vector<std::vector<double>>& f0,
-                                          const std::vector<std::vector<double>>& f1) {
-    const Layout& X = x->lay;
-    BSM_REQUIRE(W.K == X.K && W.species == X.species, BSMPS_ERR_INVALID_ARG, "MPO and MPS act on different sites");
-    BSM_REQUIRE(f0.size() == f1.size() && !f0.empty(), BSMPS_ERR_INVALID_ARG, "scalings mismatch");
-    BSM_REQUIRE(X.columns() == 1, BSMPS_ERR_INVALID_ARG, "zip-up application of a single-column MPS");
-    const int K = X.K;
-    const int nb = (int)f0.size();
-    const auto valid = valid_sectors(X.species, X.target);
+// One problem of a zip-up batch: its bases, layout, carries and buffers.
+struct ZipJob {
+    Context* ctx = nullptr;
+    const Mpo* W = nullptr;
+    const Mps* x = nullptr;
+    double shift = 0.0;
+    const std::vector<std::vector<double>>* f0 = nullptr;
+    const std::vector<std::vector<double>>* f1 = nullptr;
+    const double* one = nullptr;
+    int K = 0, nb = 0;
+    std::vector<Bond> ex;                  // exact bond bases
+    std::vector<std::vector<int>> eoff;    // (x sector li, channel a) -> segment offset in its exact sector
+    Layout Y;
+    std::vector<MpsPtr> ys;
+    std::vector<std::vector<const double*>> carry;   // per branch, per sector of Y's bond t
+    std::vector<int> carry_ld;
+    std::vector<void*> held;               // buffers the carry reads (freed after the next contraction)
+    // site state between the contraction and the factorisation
+    struct TB {
+        int mi, so, em, r0;
+    };
+    std::vector<TB> tbs;
+    std::vector<int> rows;
+    std::vector<int64_t> stack_off;
+    std::vector<double*> T;
 
-    // exact bond bases: per bond b the exact sectors, and for (x sector li,
-    // channel a) the exact sector index and the segment offset in it
-    std::vector<Bond> ex(K + 1);
-    std::vector<std::vector<int>> esec(K + 1), eoff(K + 1);
-    for (int b = 0; b <= K; ++b) {
-        const int w = W.bond_dim(b), nx = (int)X.bonds[b].q.size();
-        esec[b].assign((size_t)nx * w, -1);
-        eoff[b].assign((size_t)nx * w, -1);
-        for (const Charge& m : valid[b]) {
-            const int mi = (int)ex[b].q.size();
-            int tot = 0;
-            for (int a = 0; a < w; ++a) {
-                const int li = X.bonds[b].find(m - W.charges[b][a]);
-                if (li < 0) continue;
-                esec[b][(size_t)li * w + a] = mi;
-                eoff[b][(size_t)li * w + a] = tot;
-                tot += X.bonds[b].dim[li];
-            }
-            if (tot > 0) {
-                ex[b].q.push_back(m);
-                ex[b].dim.push_back(tot);
+    void init() {
+        const Layout& X = x->lay;
+        BSM_REQUIRE(W->K == X.K && W->species == X.species, BSMPS_ERR_INVALID_ARG,
+                    "MPO and MPS act on different sites");
+        BSM_REQUIRE(f0->size() == f1->size() && !f0->empty(), BSMPS_ERR_INVALID_ARG, "scalings mismatch");
+        BSM_REQUIRE(X.columns() == 1, BSMPS_ERR_INVALID_ARG, "zip-up application of a single-column MPS");
+        K = X.K;
+        nb = (int)f0->size();
+        const auto valid = valid_sectors(X.species, X.target);
+        ex.assign(K + 1, Bond{});
+        eoff.assign(K + 1, {});
+        for (int b = 0; b <= K; ++b) {
+            const int w = W->bond_dim(b), nx = (int)X.bonds[b].q.size();
+            eoff[b].assign((size_t)nx * w, -1);
+            for (const Charge& m : valid[b]) {
+                int tot = 0;
+                for (int a = 0; a < w; ++a) {
+                    const int li = X.bonds[b].find(m - W->charges[b][a]);
+                    if (li < 0) continue;
+                    eoff[b][(size_t)li * w + a] = tot;
+                    tot += X.bonds[b].dim[li];
+                }
+                if (tot > 0) {
+                    ex[b].q.push_back(m);
+                    ex[b].dim.push_back(tot);
+                }
             }
         }
+        Y.K = K;
+        Y.species = X.species;
+        Y.target = X.target;
+        Y.bonds.assign(K + 1, Bond{});
+        Y.bonds[0] = ex[0];
+        BSM_REQUIRE(Y.bonds[0].q.size() == 1 && Y.bonds[0].dim[0] == 1, BSMPS_ERR_INVALID_ARG,
+                    "bond 0 must have a single sector of dimension 1");
+        ys.resize(nb);
+        for (int i = 0; i < nb; ++i) {
+            ys[i].reset(new Mps);
+            ys[i]->ctx = ctx;
+            ys[i]->core.assign(K, nullptr);
+        }
+        carry.assign(nb, std::vector<const double*>(1, one));   // C_0 = [1]
+        carry_ld.assign(1, 1);
     }
-    std::vector<int> xlook;   // (li * 2 + sigma) -> block index of x's core t
 
-    Layout Y;
-    Y.K = K;
-    Y.species = X.species;
-    Y.target = X.target;
-    Y.bonds.assign(K + 1, Bond{});
-    Y.bonds[0] = ex[0];
-    std::vector<MpsPtr> ys(nb);
-    for (int i = 0; i < nb; ++i) {
-        ys[i].reset(new Mps);
-        ys[i]->ctx = ctx;
-        ys[i]->core.assign(K, nullptr);
-    }
-    // carry per branch and per sector of Y's bond t: device pointer, leading dimension
-    std::vector<std::vector<const double*>> carry(nb, std::vector<const double*>(Y.bonds[0].q.size(), nullptr));
-    std::vector<int> carry_ld(Y.bonds[0].q.size(), 1);
-    double* one = (double*)ctx->upload(std::vector<double>{1.0});
-    std::vector<void*> held = {one};    // device buffers the carry points into (freed one site later)
-    for (int i = 0; i < nb; ++i) carry[i][0] = one;    // C_0 = [1]: bond 0 has one sector of dim 1
-    BSM_REQUIRE(Y.bonds[0].q.size() == 1 && Y.bonds[0].dim[0] == 1, BSMPS_ERR_INVALID_ARG,
-                "bond 0 must have a single sector of dimension 1");
-
-    for (int t = 0; t < K; ++t) {
+    // The contraction of site t: allocates the T buffers and appends the outputs.
+    void contraction(int t, std::vector<GemmOut>& outs, std::vector<GemmIn>& ins) {
+        const Layout& X = x->lay;
         const int sp = X.species[t];
-        const int wl = W.bond_dim(t), wr = W.bond_dim(t + 1);
+        const int wl = W->bond_dim(t), wr = W->bond_dim(t + 1);
         const Bond& yb = Y.bonds[t];
-        const int ny = (int)yb.q.size();
-        const int ne = (int)ex[t + 1].q.size();
-        xlook.assign(X.bonds[t].q.size() * 2, -1);
+        const int ny = (int)yb.q.size(), ne = (int)ex[t + 1].q.size();
+        std::vector<int> xlook(X.bonds[t].q.size() * 2, -1);   // (li * 2 + sigma) -> block of x's core t
         for (int bi = 0; bi < (int)X.blocks[t].size(); ++bi)
             xlook[X.blocks[t][bi].li * 2 + X.blocks[t][bi].sigma] = bi;
-        // stacks of the exact sectors of bond t+1: blocks (mi, s') in layout order
-        struct TB {
-            int mi, so, em, r0;
-        };
-        std::vector<TB> tbs;
-        std::vector<int> rows(ne, 0);
+        tbs.clear();
+        rows.assign(ne, 0);
         for (int mi = 0; mi < ny; ++mi)
             for (int so = 0; so < 2; ++so) {
                 const int em = ex[t + 1].find(yb.q[mi] + site_delta(sp, so));
@@ -102,46 +117,41 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
                 tbs.push_back({mi, so, em, rows[em]});
                 rows[em] += yb.dim[mi];
             }
-        std::vector<int64_t> stack_off(ne, 0);
+        stack_off.assign(ne, 0);
         int64_t tsize = 0;
         for (int em = 0; em < ne; ++em) {
             stack_off[em] = tsize;
             tsize += (int64_t)rows[em] * ex[t + 1].dim[em];
         }
-        // T buffers (one per branch); at the last site they are y's last core
-        std::vector<double*> T(nb, nullptr);
+        T.assign(nb, nullptr);
         for (int i = 0; i < nb; ++i) T[i] = tsize > 0 ? (double*)ctx->alloc((size_t)tsize * sizeof(double)) : nullptr;
-        // the contraction: one grouped GEMM for all branches
-        std::vector<GemmOut> outs;
-        std::vector<GemmIn> ins;
         for (const TB& tb : tbs) {
             const Charge m = yb.q[tb.mi], m2 = ex[t + 1].q[tb.em];
             const int ldc = ex[t + 1].dim[tb.em];
-            const int em_t = ex[t].find(m);
             // segments b of the exact sector m2: channel b with x sector n_b = m2 - Delta_b
             for (int b = 0; b < wr; ++b) {
-                const int rb = X.bonds[t + 1].find(m2 - W.charges[t + 1][b]);
+                const int rb = X.bonds[t + 1].find(m2 - W->charges[t + 1][b]);
                 if (rb < 0) continue;
                 const int coff = eoff[t + 1][(size_t)rb * wr + b];
                 const int ncols = X.bonds[t + 1].dim[rb];
                 for (int i = 0; i < nb; ++i) {
                     GemmOut o{T[i] + stack_off[tb.em] + (int64_t)tb.r0 * ldc + coff, yb.dim[tb.mi], ncols, ldc,
                               (int)ins.size(), (int)ins.size(), 0.0};
-                    for (int ei = 0; ei < (int)W.entries[t].size(); ++ei) {
-                        const MpoEntry& e = W.entries[t][ei];
+                    for (int ei = 0; ei < (int)W->entries[t].size(); ++ei) {
+                        const MpoEntry& e = W->entries[t][ei];
                         if (e.so != tb.so || e.b != b) continue;
-                        const int la = X.bonds[t].find(m - W.charges[t][e.a]);
+                        const int la = X.bonds[t].find(m - W->charges[t][e.a]);
                         if (la < 0) continue;
                         const int xb = xlook[la * 2 + e.si];
                         if (xb < 0) continue;
                         const Block& bk = X.blocks[t][xb];
                         if (bk.ri != rb) continue;
                         double w = e.w;
-                        if (t == 0 && (ei == W.shift_entry[0] || ei == W.shift_entry[1])) w += shift;
-                        const std::vector<double>& f = e.si ? f1[i] : f0[i];
+                        if (t == 0 && (ei == W->shift_entry[0] || ei == W->shift_entry[1])) w += shift;
+                        const std::vector<double>& f = e.si ? (*f1)[i] : (*f0)[i];
                         const double fs = f.empty() ? 1.0 : f[t];
                         const int aoff = eoff[t][(size_t)la * wl + e.a];
-                        BSM_REQUIRE(em_t >= 0 && aoff >= 0, BSMPS_ERR_INVALID_ARG, "zip-up: inconsistent bases");
+                        BSM_REQUIRE(aoff >= 0, BSMPS_ERR_INVALID_ARG, "zip-up: inconsistent bases");
                         ins.push_back({carry[i][tb.mi] + aoff, x->core[t] + bk.off, bk.rows, carry_ld[tb.mi],
                                        bk.cols, 0, w * fs});
                     }
@@ -150,16 +160,25 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
                 }
             }
         }
-        launch_gemm(ctx, outs, ins, KK_APPLY);
-        // buffers of the previous site's carry are no longer read
-        for (void* p : held)
-            if (p != one) ctx->free(p);
-        held.assign(1, one);
+    }
+
+    // After the contraction launch: the previous carry's buffers are free.
+    void release_held() {
+        for (void* p : held) ctx->free(p);
+        held.clear();
+    }
+
+    // The factorisation of site t (appended to the site's shared launches), or
+    // at the last site the T buffers become the last core.
+    void factor(int t, std::vector<double*>& zp, std::vector<int64_t>& zn, std::vector<CopyTask>& gather,
+                std::vector<QrTask>& qr, std::vector<CopyTask>& scatter) {
         if (t == K - 1) {
             Y.bonds[K] = ex[K];
             for (int i = 0; i < nb; ++i) ys[i]->core[t] = T[i];
-            break;
+            return;
         }
+        const Bond& yb = Y.bonds[t];
+        const int ne = (int)ex[t + 1].q.size();
         // new bond t+1: k = min(stacked rows, exact columns) per exact sector
         Bond nbnd;
         std::vector<int> newidx(ne, -1);
@@ -169,7 +188,6 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
             nbnd.q.push_back(ex[t + 1].q[em]);
             nbnd.dim.push_back(std::min(rows[em], ex[t + 1].dim[em]));
         }
-        Y.bonds[t + 1] = nbnd;
         // the blocks of core t, (mi, s') -> (yb.dim[mi] x k(m')), in layout order (= tbs order)
         int64_t csize = 0;
         std::vector<int64_t> boff(tbs.size(), 0);
@@ -178,8 +196,6 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
             csize += (int64_t)yb.dim[tbs[q].mi] * nbnd.dim[newidx[tbs[q].em]];
         }
         std::vector<double*> core(nb, nullptr);
-        std::vector<double*> zp;
-        std::vector<int64_t> zn;
         for (int i = 0; i < nb; ++i) {
             core[i] = csize > 0 ? (double*)ctx->alloc((size_t)csize * sizeof(double)) : nullptr;
             if (core[i]) {
@@ -187,12 +203,8 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
                 zn.push_back(csize);
             }
         }
-        launch_zero(ctx, zp, zn, KK_APPLY_QR);
-        std::vector<CopyTask> gather, scatter;
-        std::vector<QrTask> qr;
         std::vector<std::vector<const double*>> ncarry(nb, std::vector<const double*>(nbnd.q.size(), nullptr));
         std::vector<int> ncarry_ld(nbnd.q.size(), 1);
-        std::vector<void*> nheld = {one};
         for (int em = 0; em < ne; ++em) {
             const int ni = newidx[em];
             if (ni < 0) continue;
@@ -218,30 +230,87 @@ std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps*
                             scatter.push_back({Q + tbs[q].r0, core[i] + boff[q], yb.dim[tbs[q].mi], k, M, k, 1, 0, 0,
                                                1.0});
                     ncarry[i][ni] = R;
-                    nheld.push_back(R);
-                    held.push_back(A);    // freed after the next site's launches (stream order)
+                    // A, Q, tau and R are released one site later (stream order keeps
+                    // them alive for the launches of this site)
+                    held.push_back(A);
                     held.push_back(Q);
                     held.push_back(tau);
+                    held.push_back(R);
                 }
             }
         }
-        launch_copy(ctx, gather, KK_APPLY_QR);
-        launch_qr(ctx, qr, KK_APPLY_QR);
-        launch_copy(ctx, scatter, KK_APPLY_QR);
         for (int i = 0; i < nb; ++i) {
             ys[i]->core[t] = core[i];
-            nheld.push_back(T[i]);
+            if (T[i]) held.push_back(T[i]);
         }
-        for (void* p : nheld) held.push_back(p);
+        Y.bonds[t + 1] = nbnd;
         carry.swap(ncarry);
         carry_ld.swap(ncarry_ld);
     }
-    for (void* p : held)
-        if (p != one) ctx->free(p);
+
+    std::vector<MpsPtr> finish() {
+        release_held();
+        Y.rebuild_blocks();
+        for (int i = 0; i < nb; ++i) ys[i]->lay = Y;
+        return std::move(ys);
+    }
+};
+
+}  // namespace
+
+std::vector<std::vector<MpsPtr>> op_apply_zipup_batch(Context* ctx, const std::vector<ZipProblem>& probs) {
+    std::vector<std::vector<MpsPtr>> out(probs.size());
+    if (probs.empty()) return out;
+    double* one = (double*)ctx->upload(std::vector<double>{1.0});
+    std::vector<ZipJob> jobs(probs.size());
+    int kmax = 0;
+    try {
+        for (size_t j = 0; j < probs.size(); ++j) {
+            ZipJob& J = jobs[j];
+            J.ctx = ctx;
+            J.W = probs[j].W;
+            J.x = probs[j].x;
+            J.shift = probs[j].shift;
+            J.f0 = &probs[j].f0;
+            J.f1 = &probs[j].f1;
+            J.one = one;
+            J.init();
+            kmax = std::max(kmax, J.K);
+        }
+        for (int t = 0; t < kmax; ++t) {
+            std::vector<GemmOut> outs;
+            std::vector<GemmIn> ins;
+            for (ZipJob& J : jobs)
+                if (t < J.K) J.contraction(t, outs, ins);
+            launch_gemm(ctx, outs, ins, KK_APPLY);
+            for (ZipJob& J : jobs)
+                if (t < J.K) J.release_held();
+            std::vector<double*> zp;
+            std::vector<int64_t> zn;
+            std::vector<CopyTask> gather, scatter;
+            std::vector<QrTask> qr;
+            for (ZipJob& J : jobs)
+                if (t < J.K) J.factor(t, zp, zn, gather, qr, scatter);
+            launch_zero(ctx, zp, zn, KK_APPLY_QR);
+            launch_copy(ctx, gather, KK_APPLY_QR);
+            launch_qr(ctx, qr, KK_APPLY_QR);
+            launch_copy(ctx, scatter, KK_APPLY_QR);
+        }
+    } catch (...) {
+        for (ZipJob& J : jobs) J.release_held();
+        ctx->free(one);
+        throw;
+    }
+    for (size_t j = 0; j < jobs.size(); ++j) out[j] = jobs[j].finish();
     ctx->free(one);
-    Y.rebuild_blocks();
-    for (int i = 0; i < nb; ++i) ys[i]->lay = Y;
-    return ys;
+    return out;
+}
+
+std::vector<MpsPtr> op_apply_zipup_scaled(Context* ctx, const Mpo& W, const Mps* x, double shift,
+                                          const std::vector<std::vector<double>>& f0,
+                                          const std::vector<std::vector<double>>& f1) {
+    std::vector<ZipProblem> p{{&W, x, shift, f0, f1}};
+    return std::move(op_apply_zipup_batch(ctx, p)[0]);
 }
 
 }  // namespace bsm

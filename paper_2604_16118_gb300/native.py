@@ -125,6 +125,7 @@ _SIGS = {
     "bsmps_mpo_destroy": (_i, [_vp]),
     "bsmps_apply_H": (_i, [_vp, _vp, _vp, _d, _d, _i, C.POINTER(_vp), _pd]),
     "bsmps_apply_zipup": (_i, [_vp, _vp, _vp, _d, C.POINTER(_vp), _pd]),
+    "bsmps_apply_zipup_batch": (_i, [_vp, _i, C.POINTER(_vp), C.POINTER(_vp), _pd, C.POINTER(_vp), _pd]),
     "bsmps_truncate": (_i, [_vp, _vp, _d, _i, C.POINTER(_vp), _pd, _pd]),
     "bsmps_add": (_i, [_vp, _vp, _vp, _d, _d, C.POINTER(_vp)]),
     "bsmps_scale_sites": (_i, [_vp, _vp, _pd, _pd, C.POINTER(_vp)]),
@@ -454,6 +455,18 @@ def apply_zipup(ctx, mpo, x, shift=0.0):
     fl = C.c_double()
     _check(ctx, lib().bsmps_apply_zipup(ctx.h, mpo.h, x.h, shift, C.byref(y), C.byref(fl)))
     return MPS(ctx, y), fl.value
+
+
+def apply_zipup_batch(ctx, mpos, xs, shifts):
+    """Zip-up applications of independent problems advanced together (bsmps_apply_zipup_batch)."""
+    n = len(xs)
+    Wa = (_vp * n)(*[w.h for w in mpos])
+    Xa = (_vp * n)(*[x.h for x in xs])
+    sh = np.ascontiguousarray(shifts, dtype=np.float64)
+    Ya = (_vp * n)()
+    fl = C.c_double()
+    _check(ctx, lib().bsmps_apply_zipup_batch(ctx.h, n, Wa, Xa, _dptr(sh), Ya, C.byref(fl)))
+    return [MPS(ctx, _vp(Ya[i])) for i in range(n)], fl.value
 
 
 def truncate(ctx, x, eps, r_max=0):
