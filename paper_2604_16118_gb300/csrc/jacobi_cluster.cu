@@ -1,20 +1,31 @@
-// One-sided Jacobi of a k x k matrix (k up to kClusterJacobiMax) on one
-// thread-block cluster: the columns of G and of the rotation accumulator V are
-// spread over the shared memories of the cluster's CTAs (CTA c holds columns
-// c kc .. c kc + kc - 1, kc = ceil(k / C), C = 16 or 8), every warp of the cluster takes the
-// column pairs of a round (the cyclic round-robin ordering of dev::jacobi) and
-// reads / writes the partner columns through distributed shared memory, and a
-// round ends at the cluster's hardware barrier instead of a grid-wide wait.
+// One-sided Jacobi of a k x k matrix G (k up to kClusterJacobiMax) on one
+// thread-block cluster of C CTAs (C = 16, else 8), in a block-cyclic ordering.
+//
+// The k columns form 2C blocks of b = ceil(k / 2C) columns.  A sweep is a
+// round-robin tournament of the blocks by the circle method (position 0 keeps
+// block 0, positions 1 .. 2C-1 rotate by one per step; 2C - 1 steps).  In a step
+// CTA c holds the blocks at positions c and 2C-1-c in its shared memory and
+// rotates every column pair between them in local rounds (round r pairs column
+// j of the first block with column (j + r) mod B of the second, one warp per
+// pair, __syncthreads between rounds); in the first step of a sweep it also
+// rotates the pairs inside both blocks (the round-robin ordering of
+// dev::jacobi).  One cluster barrier ends a step; then every CTA pulls the two
+// blocks of its next positions from the other CTAs' shared memory into its
+// second buffer.  So a sweep still meets every pair of columns once, with 2C
+// cluster barriers instead of one per round of k / 2 pairs, and the rotations
+// read and write the CTA's own shared memory.  The accumulated rotations V
+// (k x k) stay in global memory (L2-resident, read with __ldcg because another
+// CTA of the cluster wrote them in an earlier step).
+//
 // A pair rotates while g^2 > (k eps)^2 a b and min(a, b) > (k eps)^2 ||G||_F^2
 // (the stopping rule of dev::jacobi without its square root), by the rotation
 // of dev::jacobi_rotation_fast (angle in FP32, c and s in FP64 with
 // c^2 + s^2 = 1 to FP64 rounding); a sweep without a rotation ends the
 // iteration (at most dev::kMaxSweeps sweeps).  On this GPU an SM retires one
 // FP64 warp instruction per 16 cycles, so one CTA's Jacobi is bound by its SM's
-// FP64 rate: the cluster brings the FP64 units of kClusterCtas SMs to one
-// matrix.  Every CTA reaches the same decisions (the rotation flags and
-// ||G||_F^2 are combined in a fixed order), so all of them pass the same
-// barriers.
+// FP64 rate: the cluster brings the FP64 units of C SMs to one matrix.  Every
+// CTA takes the same decisions (the rotation flags and ||G||_F^2 are combined
+// in a fixed order), so all of them pass the same barriers.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -31,36 +42,84 @@ constexpr int kClusterThreads = 512;
 constexpr int kClusterWarps = kClusterThreads / 32;
 constexpr size_t kClusterSmemMax = 225 * 1024;
 
+// shared memory of one CTA: two buffers of two block slots of b columns of G
 size_t cluster_smem(int k, int ctas) {
-    const size_t kc = (size_t)(k + ctas - 1) / ctas;
-    return 2 * kc * (size_t)k * sizeof(double);
+    const size_t b = (size_t)(k + 2 * ctas - 1) / (2 * ctas);
+    return 4 * b * (size_t)k * sizeof(double);
 }
 
-template <int kClusterCtas>
+// Block at tournament position p in step s (n2m1 = 2C - 1; position 0 fixed).
+__device__ __forceinline__ int block_at(int p, int s, int n2m1) {
+    return p == 0 ? 0 : (p - 1 + s) % n2m1 + 1;
+}
+// Position of block beta in step s (the inverse of block_at).
+__device__ __forceinline__ int pos_of(int beta, int s, int n2m1) {
+    return beta == 0 ? 0 : ((beta - 1 - s) % n2m1 + n2m1) % n2m1 + 1;
+}
+
+// One warp: rotate columns Gp, Gq (shared memory) and columns gp, gq of V.
+__device__ __forceinline__ void rotate_pair(double* Gp, double* Gq, double* __restrict__ V, int gp, int gq, int k,
+                                            double tol2, double tiny2, int lane, int* s_rot) {
+    double a = 0.0, b = 0.0, g = 0.0;
+    for (int i = lane; i < k; i += 32) {
+        const double xp = Gp[i], xq = Gq[i];
+        a += xp * xp;
+        b += xq * xq;
+        g += xp * xq;
+    }
+    a = dev::warp_sum(a);
+    b = dev::warp_sum(b);
+    g = dev::warp_sum(g);
+    if (g * g > tol2 * (a * b) && fmin(a, b) > tiny2) {
+        double c, sn;
+        dev::jacobi_rotation_fast(a, b, g, &c, &sn);
+        double* Vp = V + (int64_t)gp * k;
+        double* Vq = V + (int64_t)gq * k;
+        for (int i = lane; i < k; i += 32) {
+            const double xp = Gp[i], xq = Gq[i];
+            Gp[i] = c * xp - sn * xq;
+            Gq[i] = sn * xp + c * xq;
+            const double vp = __ldcg(Vp + i), vq = __ldcg(Vq + i);
+            Vp[i] = c * vp - sn * vq;
+            Vq[i] = sn * vp + c * vq;
+        }
+        if (lane == 0) *s_rot = 1;
+    }
+}
+
+template <int C>
 __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTask* __restrict__ tasks) {
     extern __shared__ double jc_smem[];
-    __shared__ double s_part[kClusterCtas];     // CTA 0's slots: partial ||G||^2 of every CTA
-    __shared__ int s_flag[2][kClusterCtas];     // CTA 0's slots: rotation flags, by sweep parity
-    __shared__ int s_rot;                       // this CTA rotated in the current sweep
+    __shared__ double s_part[C];     // CTA 0's slots: partial ||G||^2 of every CTA
+    __shared__ int s_flag[2][C];     // CTA 0's slots: rotation flags, by sweep parity
+    __shared__ int s_rot;            // this CTA rotated in the current sweep
+    __shared__ double red[33];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const JacTask tk = tasks[blockIdx.x / kClusterCtas];
+    const JacTask tk = tasks[blockIdx.x / C];
     const int k = tk.k;
-    const int kc = (k + kClusterCtas - 1) / kClusterCtas;
+    constexpr int nblk = 2 * C, n2m1 = 2 * C - 1;
+    const int b = (k + nblk - 1) / nblk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double* Gl = jc_smem;                      // local columns: Gl[(p - rank kc) k + i]
-    double* Vl = jc_smem + (size_t)kc * k;
-    const int c_beg = rank * kc, c_end = min(k, c_beg + kc);
-    // load the CTA's columns of G, V = I, partial ||G||_F^2
+    // slot sl of buffer buf: b columns of k rows
+    auto slot = [&](int buf, int sl) { return jc_smem + (size_t)(buf * 2 + sl) * b * k; };
+    auto bcols = [&](int beta) { return max(0, min(b, k - beta * b)); };
+    // step 0: CTA c holds blocks c (slot 0) and 2C-1-c (slot 1); load them, set
+    // their columns of V to the identity, partial ||G||_F^2
     double f = 0.0;
-    for (int64_t e = threadIdx.x; e < (int64_t)(c_end - c_beg) * k; e += kClusterThreads) {
-        const int j = (int)(e / k), i = (int)(e % k);
-        const double v = tk.G[(int64_t)(c_beg + j) * k + i];
-        Gl[e] = v;
-        Vl[e] = (i == c_beg + j) ? 1.0 : 0.0;
-        f += v * v;
+    for (int sl = 0; sl < 2; ++sl) {
+        const int beta = sl == 0 ? rank : nblk - 1 - rank;
+        const int nc = bcols(beta);
+        double* dst = slot(0, sl);
+        const int64_t off = (int64_t)beta * b * k;
+        for (int64_t e = threadIdx.x; e < (int64_t)nc * k; e += kClusterThreads) {
+            const double v = tk.G[off + e];
+            dst[e] = v;
+            f += v * v;
+            const int j = (int)(e / k), i = (int)(e % k);
+            tk.V[off + e] = i == beta * b + j ? 1.0 : 0.0;
+        }
     }
-    __shared__ double red[33];
     f = dev::block_sum(f, red);
     double* part0 = cluster.map_shared_rank(s_part, 0);
     if (threadIdx.x == 0) {
@@ -69,81 +128,91 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTas
     }
     cluster.sync();
     double fro = 0.0;
-    for (int c = 0; c < kClusterCtas; ++c) fro += part0[c];
+    for (int c = 0; c < C; ++c) fro += part0[c];
     const double tol = (double)k * DBL_EPSILON;
     const double tol2 = tol * tol, tiny2 = tol2 * fro;
-    const int n2 = k + (k & 1);
     int* flag0 = cluster.map_shared_rank(&s_flag[0][0], 0);
-    auto colG = [&](int p) -> double* {
-        return cluster.map_shared_rank(Gl + (size_t)(p % kc) * k, p / kc);
-    };
-    auto colV = [&](int p) -> double* {
-        return cluster.map_shared_rank(Vl + (size_t)(p % kc) * k, p / kc);
-    };
-    const int gw = rank * kClusterWarps + warp, nw = kClusterCtas * kClusterWarps;
+    int gstep = 0;   // steps taken: buffer gstep & 1 holds the current blocks
     for (int sweep = 0; sweep < dev::kMaxSweeps && k > 1; ++sweep) {
-        for (int round = 0; round < n2 - 1; ++round) {
-            for (int pi = gw; pi < n2 / 2; pi += nw) {
-                int p = dev::rr_player(pi, round, n2), q = dev::rr_player(n2 - 1 - pi, round, n2);
-                if (p >= k || q >= k) continue;
-                if (p > q) {
-                    const int tmp = p;
-                    p = q;
-                    q = tmp;
-                }
-                double* Gp = colG(p);
-                double* Gq = colG(q);
-                double a = 0.0, b = 0.0, g = 0.0;
-                for (int i = lane; i < k; i += 32) {
-                    const double xp = Gp[i], xq = Gq[i];
-                    a += xp * xp;
-                    b += xq * xq;
-                    g += xp * xq;
-                }
-                a = dev::warp_sum(a);
-                b = dev::warp_sum(b);
-                g = dev::warp_sum(g);
-                if (g * g > tol2 * (a * b) && fmin(a, b) > tiny2) {
-                    double c, sn;
-                    dev::jacobi_rotation_fast(a, b, g, &c, &sn);
-                    double* Vp = colV(p);
-                    double* Vq = colV(q);
-                    for (int i = lane; i < k; i += 32) {
-                        const double xp = Gp[i], xq = Gq[i];
-                        Gp[i] = c * xp - sn * xq;
-                        Gq[i] = sn * xp + c * xq;
-                        const double vp = Vp[i], vq = Vq[i];
-                        Vp[i] = c * vp - sn * vq;
-                        Vq[i] = sn * vp + c * vq;
+        for (int s = 0; s < n2m1; ++s, ++gstep) {
+            const int cur = gstep & 1;
+            const int bL = block_at(rank, s, n2m1), bR = block_at(nblk - 1 - rank, s, n2m1);
+            const int nL = bcols(bL), nR = bcols(bR);
+            double* L = slot(cur, 0);
+            double* R = slot(cur, 1);
+            if (s == 0) {
+                // pairs inside each block: round-robin over nb2 players per block
+                const int nb = max(nL, nR), nb2 = nb + (nb & 1), half = nb2 / 2;
+                for (int round = 0; round < nb2 - 1; ++round) {
+                    for (int u = warp; u < nb2; u += kClusterWarps) {
+                        const int pi = u % half, side = u / half;
+                        int p = dev::rr_player(pi, round, nb2), q = dev::rr_player(nb2 - 1 - pi, round, nb2);
+                        if (p > q) {
+                            const int t = p;
+                            p = q;
+                            q = t;
+                        }
+                        if (q >= (side == 0 ? nL : nR)) continue;
+                        double* X = side == 0 ? L : R;
+                        const int c0 = (side == 0 ? bL : bR) * b;
+                        rotate_pair(X + (size_t)p * k, X + (size_t)q * k, tk.V, c0 + p, c0 + q, k, tol2, tiny2, lane,
+                                    &s_rot);
                     }
-                    if (lane == 0) s_rot = 1;
+                    __syncthreads();
                 }
             }
+            // pairs between the two blocks
+            const int B = max(nL, nR);
+            for (int r = 0; r < B; ++r) {
+                for (int j = warp; j < B; j += kClusterWarps) {
+                    const int q = (j + r) % B;
+                    if (j >= nL || q >= nR) continue;
+                    rotate_pair(L + (size_t)j * k, R + (size_t)q * k, tk.V, bL * b + j, bR * b + q, k, tol2, tiny2,
+                                lane, &s_rot);
+                }
+                __syncthreads();
+            }
             cluster.sync();
+            // pull the blocks of the next step's positions into the other buffer
+            const int s1 = s + 1 == n2m1 ? 0 : s + 1;
+            for (int sl = 0; sl < 2; ++sl) {
+                const int beta = block_at(sl == 0 ? rank : nblk - 1 - rank, s1, n2m1);
+                const int hp = pos_of(beta, s, n2m1);   // its position in this step
+                const int holder = hp < C ? hp : nblk - 1 - hp;
+                const double* src = cluster.map_shared_rank(slot(cur, hp < C ? 0 : 1), holder);
+                double* dst = slot(cur ^ 1, sl);
+                const int64_t n = (int64_t)bcols(beta) * k;
+                for (int64_t e = threadIdx.x; e < n; e += kClusterThreads) dst[e] = src[e];
+            }
+            __syncthreads();
         }
         // combine the CTAs' rotation flags in CTA 0's slots (parity-indexed, so the
         // slots of one sweep are never reset while another CTA still reads them)
         const int par = sweep & 1;
         if (threadIdx.x == 0) {
-            flag0[par * kClusterCtas + rank] = s_rot;
+            flag0[par * C + rank] = s_rot;
             s_rot = 0;
         }
         cluster.sync();
         int rot = 0;
-        for (int c = 0; c < kClusterCtas; ++c) rot |= flag0[par * kClusterCtas + c];
+        for (int c = 0; c < C; ++c) rot |= flag0[par * C + c];
         if (!rot) break;
     }
-    // column norms of the rotated G, then G and V back to global memory
-    for (int j = c_beg + warp; j < c_end; j += kClusterWarps) {
-        const double* Gj = Gl + (size_t)(j - c_beg) * k;
-        double a = 0.0;
-        for (int i = lane; i < k; i += 32) a += Gj[i] * Gj[i];
-        a = dev::warp_sum(a);
-        if (lane == 0) tk.Sraw[j] = sqrt(a);
-    }
-    for (int64_t e = threadIdx.x; e < (int64_t)(c_end - c_beg) * k; e += kClusterThreads) {
-        tk.G[(int64_t)c_beg * k + e] = Gl[e];
-        tk.V[(int64_t)c_beg * k + e] = Vl[e];
+    // the current blocks (step gstep mod 2C-1 of the tournament) back to global
+    // memory, with the column norms
+    const int cur = gstep & 1, s_now = gstep % n2m1;
+    for (int sl = 0; sl < 2; ++sl) {
+        const int beta = block_at(sl == 0 ? rank : nblk - 1 - rank, s_now, n2m1);
+        const int nc = bcols(beta);
+        const double* X = slot(cur, sl);
+        for (int j = warp; j < nc; j += kClusterWarps) {
+            double a = 0.0;
+            for (int i = lane; i < k; i += 32) a += X[(size_t)j * k + i] * X[(size_t)j * k + i];
+            a = dev::warp_sum(a);
+            if (lane == 0) tk.Sraw[beta * b + j] = sqrt(a);
+        }
+        const int64_t off = (int64_t)beta * b * k;
+        for (int64_t e = threadIdx.x; e < (int64_t)nc * k; e += kClusterThreads) tk.G[off + e] = X[e];
     }
     // no CTA leaves while another may still read its shared memory
     cluster.sync();

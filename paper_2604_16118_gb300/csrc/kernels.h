@@ -81,10 +81,12 @@ struct JacTask {
 // error word, raised at the next sync).  Returns false when no grid can be
 // resident (the caller then runs one CTA per matrix).
 bool launch_jacobi_grid(Context* ctx, const std::vector<JacTask>& tasks);
-// Jacobi of matrices with k <= kClusterJacobiMax, one thread-block cluster of 8
-// CTAs per matrix with G and V in the CTAs' distributed shared memory and a
-// cluster barrier per round (csrc/jacobi_cluster.cu).  Returns false, with
-// nothing launched, when such a cluster cannot be scheduled.
+// Jacobi of matrices with k <= kClusterJacobiMax, one thread-block cluster of 16
+// (else 8) CTAs per matrix in a block-cyclic ordering: every CTA rotates the
+// pairs of the two column blocks it holds in its own shared memory, and the
+// blocks move between the CTAs' shared memories at a cluster barrier per
+// tournament step (csrc/jacobi_cluster.cu).  Returns false, with nothing
+// launched, when such a cluster cannot be scheduled.
 constexpr int kClusterJacobiMax = 336;
 // Jacobi problems from this size on go to the cluster kernel: below it one SM's
 // FP64 units suffice for the latency of a round.
