@@ -61,6 +61,7 @@ typedef struct bsmps_ctx_s* bsmps_ctx;
 typedef struct bsmps_mps_s* bsmps_mps;
 typedef struct bsmps_mpo_s* bsmps_mpo;
 typedef struct bsmps_mlp_s* bsmps_mlp;
+typedef struct bsmps_plan_s* bsmps_plan;
 
 typedef enum {
     BSMPS_OK = 0,
@@ -279,6 +280,11 @@ BSMPS_API bsmps_status bsmps_mps_sectors(bsmps_mps x, int* triples);
 BSMPS_API bsmps_status bsmps_mps_size(bsmps_mps x, int64_t* n_values);
 /* Copy the blocks to host memory in flat layout (synchronises). */
 BSMPS_API bsmps_status bsmps_mps_export(bsmps_mps x, double* values);
+/* Overwrite the blocks of x in place from host memory in flat layout (n_values
+ * = bsmps_mps_size; synchronises).  The device buffers of x keep their
+ * addresses, so a recorded plan that reads x sees the new values at its next
+ * launch.  Errors: INVALID_ARG, CUDA. */
+BSMPS_API bsmps_status bsmps_mps_write(bsmps_mps x, const double* values, int64_t n_values);
 BSMPS_API bsmps_status bsmps_mps_destroy(bsmps_mps x);
 
 /* ---- MPO ----------------------------------------------------------------- */
@@ -348,6 +354,37 @@ BSMPS_API bsmps_status bsmps_apply_zipup(bsmps_ctx ctx, bsmps_mpo W, bsmps_mps x
  * batch.  Errors: INVALID_ARG, OOM, CUDA. */
 BSMPS_API bsmps_status bsmps_apply_zipup_batch(bsmps_ctx ctx, int n, const bsmps_mpo* W, const bsmps_mps* x,
                                                const double* shift, bsmps_mps* y, double* flops);
+
+/* The batched zip-up application of bsmps_apply_zipup_batch recorded once as a
+ * CUDA graph, for repeated application of the same operators to iterates of
+ * fixed structure (the inner loop of a batch of independent solves at fixed
+ * ranks).  Recording runs the batch once on the context's stream (which sizes
+ * the graph's memory and fixes the contraction autotuner's choices), then
+ * captures the same launch sequence into a graph whose buffers live in one
+ * device arena and whose task lists live in pinned host memory owned by the
+ * plan.  bsmps_plan_launch replays every launch of the batch with one graph
+ * launch on the context's stream: it reads the blocks x[i] hold at that point
+ * in stream order (update them in place with bsmps_mps_write) and overwrites
+ * the plan's outputs.  ctx: a context created with a non-default stream.  W, x:
+ * n handles each, which must outlive the plan; shift: n values, read now.
+ * y: n new handles to the outputs, whose blocks belong to the plan (valid from
+ * the first bsmps_plan_launch until bsmps_plan_destroy; bsmps_mps_destroy on
+ * them releases the handle only).  flops (may be NULL): algorithmic FP64 flops
+ * of one launch.  The recording runs the zip-up's FP64 or split-precision
+ * contraction as the context's precision selects at this call.
+ * Errors: INVALID_ARG (null arguments, default stream), OOM, CUDA. */
+BSMPS_API bsmps_status bsmps_plan_apply_zipup_batch(bsmps_ctx ctx, int n, const bsmps_mpo* W, const bsmps_mps* x,
+                                                    const double* shift, bsmps_plan* plan, bsmps_mps* y,
+                                                    double* flops);
+/* One replay of the recorded batch on the context's stream (asynchronous;
+ * bsmps_ctx_sync or any synchronising call waits for it).  Errors: INVALID_ARG,
+ * CUDA. */
+BSMPS_API bsmps_status bsmps_plan_launch(bsmps_plan plan);
+/* Kernel launches one bsmps_plan_launch replays (also added to the context's
+ * bsmps_ctx_launch_count at every launch). */
+BSMPS_API int64_t bsmps_plan_launch_count(bsmps_plan plan);
+/* Waits for the context's stream, then releases the graph and its memory. */
+BSMPS_API bsmps_status bsmps_plan_destroy(bsmps_plan plan);
 
 /* trunc_eps (Sec. 2.2, Eq. (ttsvdquasiopt)): QR sweep left to right (diag R
  * >= 0), then right to left SVD of [X_b(n,0) | X_b(n,1)] per left sector;
@@ -470,6 +507,15 @@ BSMPS_API bsmps_status bsmps_ctx_set_precision(bsmps_ctx ctx, int precision);
  * (the iteration stays within its error control, but the trajectory is not the
  * FP64 one).  Errors: INVALID_ARG (negative or above 60). */
 BSMPS_API bsmps_status bsmps_ctx_set_gemm_emulation(bsmps_ctx ctx, int min_log2_flops);
+
+/* Truncation SVDs whose triangular factor is k x k with min_k <= k <= 336 start
+ * the FP64 one-sided Jacobi from an FP32 one: the FP32 rotations P (orthogonal
+ * to about 1e-6), re-orthogonalised in FP64 by Householder QR (Qp), give
+ * G Qp, whose FP64 Jacobi converges in a few sweeps; V = Qp V1.  Every
+ * quantity the truncation reads (singular values, vectors) is still the
+ * result of the FP64 Jacobi, to FP64 rounding.  min_k = 0 turns it off; the
+ * default is 96.  Errors: INVALID_ARG (negative). */
+BSMPS_API bsmps_status bsmps_ctx_set_jacobi_precond(bsmps_ctx ctx, int min_k);
 
 BSMPS_API bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda,
                                         const double* B, int ldb, double* C, int ldc, int slices);

@@ -17,6 +17,22 @@ struct bsmps_mpo_s {
     bsm::Context* ctx;
     bsm::Mpo W;
 };
+// A recorded batch of zip-up applications: the graph, its memory and the
+// outputs its launches write.
+struct bsmps_plan_s {
+    bsm::Context* ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bsm::PlanArena arena;
+    int64_t launches = 0;
+    double flops = 0.0;
+    ~bsmps_plan_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (arena.dev) cudaFree(arena.dev);
+        if (arena.host) cudaFreeHost(arena.host);
+    }
+};
 
 namespace bsm {
 
@@ -29,6 +45,15 @@ Context* context_of(bsmps_ctx c) {
 void* Context::alloc(size_t bytes) {
     if (bytes == 0) return nullptr;
     ++alloc_calls;
+    const size_t granule = (bytes + 255) & ~size_t(255);
+    alloc_bytes += granule;
+    if (rec) {
+        BSM_REQUIRE(rec->dev_used + granule <= rec->dev_cap, BSMPS_ERR_OOM,
+                    "recorded graph: device arena exhausted (the recording took another path than the sizing run)");
+        void* p = rec->dev + rec->dev_used;
+        rec->dev_used += granule;
+        return p;
+    }
 #ifdef BSM_NO_ALLOC_CACHE   // host-side checking builds: every block goes back to the pool
     {
         void* q = nullptr;
@@ -58,6 +83,7 @@ void* Context::alloc(size_t bytes) {
 
 void Context::free(void* p) {
     if (!p) return;
+    if (rec && rec->owns(p)) return;   // arena blocks live as long as the graph
 #ifdef BSM_NO_ALLOC_CACHE
     cudaFreeAsync(p, stream);
     return;
@@ -90,6 +116,19 @@ void Context::release_cache() {
 
 void* Context::upload_raw(const void* src, size_t bytes) {
     void* d = alloc(bytes);
+    const size_t granule = (bytes + 255) & ~size_t(255);
+    upload_bytes += granule;
+    if (rec) {
+        // recording: the staged copy must outlive the capture (the graph's copy
+        // node reads it at every launch)
+        BSM_REQUIRE(rec->host_used + granule <= rec->host_cap, BSMPS_ERR_OOM,
+                    "recorded graph: host staging arena exhausted");
+        unsigned char* h = rec->host + rec->host_used;
+        rec->host_used += granule;
+        std::memcpy(h, src, bytes);
+        BSM_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, stream));
+        return d;
+    }
     const size_t half = kRingBytes / 2;
     if (bytes > half) {
         BSM_CUDA(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, stream));
@@ -288,6 +327,14 @@ bsmps_status bsmps_ctx_kernel_stats(bsmps_ctx ctx, int kind, int reset, int64_t*
             }
             c->prof.clear();
         }
+    });
+}
+
+bsmps_status bsmps_ctx_set_jacobi_precond(bsmps_ctx ctx, int min_k) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(min_k >= 0, BSMPS_ERR_INVALID_ARG, "min_k must be >= 0");
+        c->jacobi_precond_min = min_k;
     });
 }
 
@@ -692,6 +739,101 @@ bsmps_status bsmps_apply_zipup_batch(bsmps_ctx ctx, int n, const bsmps_mpo* W, c
         c->sync();
         if (flops) *flops = c->flops - f0;
         for (int i = 0; i < n; ++i) y[i] = wrap(std::move(r[i][0]));
+    });
+}
+
+bsmps_status bsmps_mps_write(bsmps_mps x, const double* values, int64_t n_values) {
+    return guarded(nullptr, [&] {
+        BSM_REQUIRE(x && x->m, BSMPS_ERR_INVALID_ARG, "null MPS handle");
+        bsm::Mps* m = x->m.get();
+        BSM_REQUIRE(n_values == m->lay.total() && (values || n_values == 0), BSMPS_ERR_INVALID_ARG,
+                    "values must match the sector dims");
+        BSM_CUDA(cudaSetDevice(m->ctx->device));
+        bsm::mps_upload(m, values);
+    });
+}
+
+bsmps_status bsmps_plan_apply_zipup_batch(bsmps_ctx ctx, int n, const bsmps_mpo* W, const bsmps_mps* x,
+                                          const double* shift, bsmps_plan* plan, bsmps_mps* y, double* flops) {
+    return guarded(ctx, [&] {
+        bsm::Context* c = C(ctx);
+        BSM_REQUIRE(n > 0 && W && x && shift && y && plan, BSMPS_ERR_INVALID_ARG, "null argument");
+        BSM_REQUIRE(c->stream != nullptr, BSMPS_ERR_INVALID_ARG,
+                    "recording a plan needs a context on a non-default stream");
+        BSM_REQUIRE(c->rec == nullptr, BSMPS_ERR_INVALID_ARG, "the context is already recording");
+        std::vector<bsm::ZipProblem> probs;
+        for (int i = 0; i < n; ++i) {
+            BSM_REQUIRE(W[i] && x[i], BSMPS_ERR_INVALID_ARG, "null handle in the batch");
+            probs.push_back({&W[i]->W, M(x[i]), shift[i], {{}}, {{}}});
+        }
+        // sizing run: the same batch, uncaptured; it also tunes every contraction
+        // size class, so the recording makes no timing runs
+        const size_t a0 = c->alloc_bytes, u0 = c->upload_bytes;
+        {
+            std::vector<std::vector<bsm::MpsPtr>> r = bsm::op_apply_zipup_batch(c, probs);
+        }
+        c->sync();
+        c->err_word();   // created outside the capture
+        std::unique_ptr<bsmps_plan_s> P(new bsmps_plan_s);
+        P->ctx = c;
+        P->arena.dev_cap = c->alloc_bytes - a0 + (size_t(1) << 20);
+        P->arena.host_cap = c->upload_bytes - u0 + (size_t(1) << 16);
+        BSM_CUDA(cudaMalloc((void**)&P->arena.dev, P->arena.dev_cap));
+        BSM_CUDA(cudaMallocHost((void**)&P->arena.host, P->arena.host_cap));
+        const bool prof = c->profiling;
+        const int64_t l0 = c->launches;
+        const double f0 = c->flops;
+        std::vector<std::vector<bsm::MpsPtr>> r;
+        c->profiling = false;
+        c->rec = &P->arena;
+        BSM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        try {
+            r = bsm::op_apply_zipup_batch(c, probs);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(c->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            c->rec = nullptr;
+            c->profiling = prof;
+            throw;
+        }
+        const cudaError_t ec = cudaStreamEndCapture(c->stream, &P->graph);
+        c->rec = nullptr;
+        c->profiling = prof;
+        BSM_CUDA(ec);
+        BSM_CUDA(cudaGraphInstantiate(&P->exec, P->graph, 0));
+        P->launches = c->launches - l0;
+        P->flops = c->flops - f0;
+        c->launches = l0;   // nothing ran yet: launches count at bsmps_plan_launch
+        c->flops = f0;
+        if (flops) *flops = P->flops;
+        for (int i = 0; i < n; ++i) {
+            r[i][0]->owns_cores = false;
+            y[i] = wrap(std::move(r[i][0]));
+        }
+        *plan = P.release();
+    });
+}
+
+bsmps_status bsmps_plan_launch(bsmps_plan plan) {
+    if (!plan) return BSMPS_ERR_INVALID_ARG;
+    return guarded(nullptr, [&] {
+        bsm::Context* c = plan->ctx;
+        BSM_CUDA(cudaSetDevice(c->device));
+        BSM_CUDA(cudaGraphLaunch(plan->exec, c->stream));
+        c->launches += plan->launches;
+        c->flops += plan->flops;
+    });
+}
+
+int64_t bsmps_plan_launch_count(bsmps_plan plan) { return plan ? plan->launches : -1; }
+
+bsmps_status bsmps_plan_destroy(bsmps_plan plan) {
+    if (!plan) return BSMPS_ERR_INVALID_ARG;
+    return guarded(nullptr, [&] {
+        BSM_CUDA(cudaSetDevice(plan->ctx->device));
+        BSM_CUDA(cudaStreamSynchronize(plan->ctx->stream));
+        delete plan;
     });
 }
 

@@ -115,7 +115,20 @@ struct Mps {
     Context* ctx = nullptr;
     Layout lay;
     std::vector<double*> core;   // device pointers (nullptr when the core is empty)
+    bool owns_cores = true;      // false: the cores belong to a recorded graph's arena
     ~Mps();
+};
+
+// Memory of a recorded CUDA graph (bsmps_plan): while a context records, its
+// device requests are carved from dev (never recycled, so every buffer keeps
+// the address the graph's launches were captured with) and its task lists are
+// staged in host (pinned, read by the graph's copy nodes at every launch).
+struct PlanArena {
+    char* dev = nullptr;
+    size_t dev_cap = 0, dev_used = 0;
+    unsigned char* host = nullptr;
+    size_t host_cap = 0, host_used = 0;
+    bool owns(const void* p) const { return p >= dev && p < dev + dev_cap; }
 };
 
 // Per-launch record of the optional profiler (events resolved on query).
@@ -136,11 +149,15 @@ struct Context {
     std::string last_error;
     int64_t launches = 0;
     int64_t alloc_calls = 0;         // requests served by alloc()
+    size_t alloc_bytes = 0;          // bytes requested from alloc() (256-byte granules), running total
+    size_t upload_bytes = 0;         // bytes staged by upload_raw() (256-byte granules), running total
+    PlanArena* rec = nullptr;        // set while a graph is being recorded
     double flops = 0.0;              // algorithmic FP64 flops issued (running total)
     bool profiling = false;
     int gemm_emulation_log2 = 0;     // block products >= 2^this flops on the tensor cores (0: never)
     int apply_precision = BSMPS_PREC_FP64;   // arithmetic of the zip-up contraction stage
     bool autotune = true;                    // autotune the FP64 zip-up contraction (launch_gemm)
+    int jacobi_precond_min = 96;             // cluster Jacobi from this k on starts from an FP32 Jacobi (0: never)
     std::map<int64_t, int> gemm_tuned;       // size class -> chosen split between the two GEMM kernels
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;

@@ -218,18 +218,197 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTas
     cluster.sync();
 }
 
-// One launch of the C-CTA kernel; false (nothing launched) when such clusters
-// cannot be scheduled.
+// One-sided Jacobi in FP32 of the k x k FP64 matrix G, as a preconditioner:
+// the same block-cyclic tournament as k_jacobi_cluster, with G (scaled by a
+// power of two to ||G||_F ~ 1, rounded to FP32) and the accumulated rotations
+// V both in the CTAs' shared memory (a block moves with its columns of V).
+// FP32 arithmetic runs at 64 times the FP64 rate of this GPU.  A pair rotates
+// while |g| > tol sqrt(a) sqrt(b), tol = 4 sqrt(k) eps_32 (above the rounding
+// noise of the FP32 inner products), and min(a, b) > 1e-36 (of ||G||_F^2 ~ 1):
+// floating point resolves the small columns of a graded G relative to their
+// own norms, so they are rotated too, which leaves the FP64 Jacobi only the
+// last quadratic sweeps at every scale.  The rotation is that of
+// dev::jacobi_rotation_fast in FP32, with d = b - a and 2g scaled by their
+// larger magnitude so that no square underflows.  Output: tk.V = the FP32 V as
+// FP64 (orthogonal to about 1e-6); tk.G is read only; tk.Sraw unused.
+constexpr int kMaxSweepsF32 = 20;
+
+__device__ __forceinline__ void rotate_pair_f32(float* Gp, float* Gq, float* Vp, float* Vq, int k, float tol,
+                                                int lane, int* s_rot) {
+    float a = 0.0f, b = 0.0f, g = 0.0f;
+    for (int i = lane; i < k; i += 32) {
+        const float xp = Gp[i], xq = Gq[i];
+        a = fmaf(xp, xp, a);
+        b = fmaf(xq, xq, b);
+        g = fmaf(xp, xq, g);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+    }
+    if (fabsf(g) > tol * sqrtf(a) * sqrtf(b) && fminf(a, b) > 1e-36f) {
+        // t = tan of the angle, the smaller root of t^2 + 2 zeta t - 1 = 0 with
+        // zeta = (b - a) / 2g; c = 1 / sqrt(1 + t^2), s = c t
+        const float d = b - a, g2 = g + g;
+        const float m = fmaxf(fabsf(d), fabsf(g2));   // > 0 (g != 0)
+        const float dn = d / m, gn = g2 / m;
+        const float r = sqrtf(fmaf(dn, dn, gn * gn));
+        const float sz = (d == 0.0f || ((d > 0.0f) == (g2 > 0.0f))) ? 1.0f : -1.0f;
+        const float t = sz * __fdividef(fabsf(gn), fabsf(dn) + r);
+        const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
+        for (int i = lane; i < k; i += 32) {
+            const float xp = Gp[i], xq = Gq[i];
+            Gp[i] = c * xp - sn * xq;
+            Gq[i] = sn * xp + c * xq;
+            const float vp = Vp[i], vq = Vq[i];
+            Vp[i] = c * vp - sn * vq;
+            Vq[i] = sn * vp + c * vq;
+        }
+        if (lane == 0) *s_rot = 1;
+    }
+}
+
 template <int C>
-bool launch_cluster_size(Context* ctx, const std::vector<JacTask>& tasks, int kmax) {
-    const size_t smem = cluster_smem(kmax, C);
+__global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster_f32(const JacTask* __restrict__ tasks) {
+    extern __shared__ float jf_smem[];
+    __shared__ double s_part[C];
+    __shared__ int s_flag[2][C];
+    __shared__ int s_rot;
+    __shared__ double red[33];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const JacTask tk = tasks[blockIdx.x / C];
+    const int k = tk.k;
+    constexpr int nblk = 2 * C, n2m1 = 2 * C - 1;
+    const int b = (k + nblk - 1) / nblk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // slot sl of buffer buf: b columns of G, then b columns of V (k rows each)
+    auto slot = [&](int buf, int sl) { return jf_smem + (size_t)(buf * 2 + sl) * 2 * b * k; };
+    auto bcols = [&](int beta) { return max(0, min(b, k - beta * b)); };
+    double f = 0.0;
+    for (int sl = 0; sl < 2; ++sl) {
+        const int beta = sl == 0 ? rank : nblk - 1 - rank;
+        const int64_t off = (int64_t)beta * b * k;
+        for (int64_t e = threadIdx.x; e < (int64_t)bcols(beta) * k; e += kClusterThreads) {
+            const double v = tk.G[off + e];
+            f += v * v;
+        }
+    }
+    f = dev::block_sum(f, red);
+    double* part0 = cluster.map_shared_rank(s_part, 0);
+    if (threadIdx.x == 0) {
+        part0[rank] = f;
+        s_rot = 0;
+    }
+    cluster.sync();
+    double fro = 0.0;
+    for (int c = 0; c < C; ++c) fro += part0[c];
+    int ex = 0;
+    if (fro > 0.0) frexp(sqrt(fro), &ex);
+    const double sc = ldexp(1.0, -ex);   // exact power of two: ||sc G||_F in [1/2, 1)
+    for (int sl = 0; sl < 2; ++sl) {
+        const int beta = sl == 0 ? rank : nblk - 1 - rank;
+        const int nc = bcols(beta);
+        const int64_t off = (int64_t)beta * b * k;
+        float* dst = slot(0, sl);
+        for (int64_t e = threadIdx.x; e < (int64_t)nc * k; e += kClusterThreads) {
+            dst[e] = (float)(tk.G[off + e] * sc);
+            const int j = (int)(e / k), i = (int)(e % k);
+            dst[(int64_t)b * k + e] = i == beta * b + j ? 1.0f : 0.0f;
+        }
+    }
+    __syncthreads();
+    const float tol = 4.0f * sqrtf((float)k) * FLT_EPSILON;
+    int* flag0 = cluster.map_shared_rank(&s_flag[0][0], 0);
+    int gstep = 0;
+    for (int sweep = 0; sweep < kMaxSweepsF32 && k > 1; ++sweep) {
+        for (int s = 0; s < n2m1; ++s, ++gstep) {
+            const int cur = gstep & 1;
+            const int bL = block_at(rank, s, n2m1), bR = block_at(nblk - 1 - rank, s, n2m1);
+            const int nL = bcols(bL), nR = bcols(bR);
+            float* L = slot(cur, 0);
+            float* R = slot(cur, 1);
+            float* LV = L + (size_t)b * k;
+            float* RV = R + (size_t)b * k;
+            if (s == 0) {
+                const int nb = max(nL, nR), nb2 = nb + (nb & 1), half = nb2 / 2;
+                for (int round = 0; round < nb2 - 1; ++round) {
+                    for (int u = warp; u < nb2; u += kClusterWarps) {
+                        const int pi = u % half, side = u / half;
+                        int p = dev::rr_player(pi, round, nb2), q = dev::rr_player(nb2 - 1 - pi, round, nb2);
+                        if (p > q) {
+                            const int t = p;
+                            p = q;
+                            q = t;
+                        }
+                        if (q >= (side == 0 ? nL : nR)) continue;
+                        float* X = side == 0 ? L : R;
+                        float* XV = side == 0 ? LV : RV;
+                        rotate_pair_f32(X + (size_t)p * k, X + (size_t)q * k, XV + (size_t)p * k, XV + (size_t)q * k,
+                                        k, tol, lane, &s_rot);
+                    }
+                    __syncthreads();
+                }
+            }
+            const int B = max(nL, nR);
+            for (int r = 0; r < B; ++r) {
+                for (int j = warp; j < B; j += kClusterWarps) {
+                    const int q = (j + r) % B;
+                    if (j >= nL || q >= nR) continue;
+                    rotate_pair_f32(L + (size_t)j * k, R + (size_t)q * k, LV + (size_t)j * k, RV + (size_t)q * k, k,
+                                    tol, lane, &s_rot);
+                }
+                __syncthreads();
+            }
+            cluster.sync();
+            const int s1 = s + 1 == n2m1 ? 0 : s + 1;
+            for (int sl = 0; sl < 2; ++sl) {
+                const int beta = block_at(sl == 0 ? rank : nblk - 1 - rank, s1, n2m1);
+                const int hp = pos_of(beta, s, n2m1);
+                const int holder = hp < C ? hp : nblk - 1 - hp;
+                const float* src = cluster.map_shared_rank(slot(cur, hp < C ? 0 : 1), holder);
+                float* dst = slot(cur ^ 1, sl);
+                const int64_t n = (int64_t)bcols(beta) * k;
+                for (int64_t e = threadIdx.x; e < n; e += kClusterThreads) {
+                    dst[e] = src[e];
+                    dst[(int64_t)b * k + e] = src[(int64_t)b * k + e];
+                }
+            }
+            __syncthreads();
+        }
+        const int par = sweep & 1;
+        if (threadIdx.x == 0) {
+            flag0[par * C + rank] = s_rot;
+            s_rot = 0;
+        }
+        cluster.sync();
+        int rot = 0;
+        for (int c = 0; c < C; ++c) rot |= flag0[par * C + c];
+        if (!rot) break;
+    }
+    const int cur = gstep & 1, s_now = gstep % n2m1;
+    for (int sl = 0; sl < 2; ++sl) {
+        const int beta = block_at(sl == 0 ? rank : nblk - 1 - rank, s_now, n2m1);
+        const float* XV = slot(cur, sl) + (size_t)b * k;
+        const int64_t off = (int64_t)beta * b * k;
+        for (int64_t e = threadIdx.x; e < (int64_t)bcols(beta) * k; e += kClusterThreads) tk.V[off + e] = XV[e];
+    }
+    cluster.sync();
+}
+
+// One launch of a C-CTA kernel (the FP64 Jacobi, or the FP32 one when f32);
+// false (nothing launched) when such clusters cannot be scheduled.
+template <int C>
+bool launch_cluster_size(Context* ctx, const std::vector<JacTask>& tasks, int kmax, bool f32 = false) {
+    const size_t smem = cluster_smem(kmax, C);   // FP32: G and V in the same bytes as the FP64 G
     if (smem > kClusterSmemMax) return false;
-    static bool attr = false;
-    if (!attr) {
-        BSM_CUDA(cudaFuncSetAttribute(k_jacobi_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kClusterSmemMax));
-        if (C > 8) BSM_CUDA(cudaFuncSetAttribute(k_jacobi_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        attr = true;
+    void (*kern)(const JacTask*) = f32 ? k_jacobi_cluster_f32<C> : k_jacobi_cluster<C>;
+    static bool attr[2] = {false, false};
+    if (!attr[f32]) {
+        BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax));
+        if (C > 8) BSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        attr[f32] = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(tasks.size() * C));
@@ -244,13 +423,13 @@ bool launch_cluster_size(Context* ctx, const std::vector<JacTask>& tasks, int km
     cfg.attrs = attr_l;
     cfg.numAttrs = 1;
     int n_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&n_clusters, k_jacobi_cluster<C>, &cfg) != cudaSuccess || n_clusters < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n_clusters, kern, &cfg) != cudaSuccess || n_clusters < 1) {
         (void)cudaGetLastError();
         return false;
     }
     Scratch s(ctx);
     const JacTask* d = s.up(tasks);
-    BSM_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_cluster<C>, d));
+    BSM_CUDA(cudaLaunchKernelEx(&cfg, kern, d));
     check_launch(ctx);
     return true;
 }
@@ -266,6 +445,15 @@ bool launch_jacobi_cluster(Context* ctx, const std::vector<JacTask>& tasks) {
     for (const JacTask& t : tasks) kmax = std::max(kmax, t.k);
     if (kmax > kClusterJacobiMax) return false;
     return launch_cluster_size<16>(ctx, tasks, kmax) || launch_cluster_size<8>(ctx, tasks, kmax);
+}
+
+// The FP32 preconditioning Jacobi (k_jacobi_cluster_f32) of the same tasks.
+bool launch_jacobi_cluster_f32(Context* ctx, const std::vector<JacTask>& tasks) {
+    if (tasks.empty()) return true;
+    int kmax = 0;
+    for (const JacTask& t : tasks) kmax = std::max(kmax, t.k);
+    if (kmax > kClusterJacobiMax) return false;
+    return launch_cluster_size<16>(ctx, tasks, kmax, true) || launch_cluster_size<8>(ctx, tasks, kmax, true);
 }
 
 }  // namespace bsm

@@ -404,8 +404,10 @@ void launch_gemm(Context* ctx, const std::vector<GemmOut>& outs, const std::vect
         }
     const int64_t key = gemm_size_class(outs, ins);
     auto it = ctx->gemm_tuned.find(key);
-    if (it != ctx->gemm_tuned.end()) {
-        launch_gemm_fp64(ctx, outs, ins, kind, it->second);
+    if (it != ctx->gemm_tuned.end() || ctx->rec) {
+        // a graph being recorded takes the tuned split (its sizing run tuned every
+        // class) and never times candidates
+        launch_gemm_fp64(ctx, outs, ins, kind, it != ctx->gemm_tuned.end() ? it->second : kTile);
         return;
     }
     const int cand[4] = {0, 8, 16, 32};
@@ -519,13 +521,15 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
     // beyond, across the grid (one CTA per matrix when the cooperative launch
     // cannot be resident)
     std::vector<JacTask> small, mid, large;
+    std::vector<size_t> mid_i;
     double fl = 0.0, by = 0.0;
     for (size_t i = 0; i < tasks.size(); ++i) {
         const int k = std::min(tasks[i].M, tasks[i].N);
         JacTask jt{R[i], V[i], Sraw[i], k, 0};
-        if (k >= kClusterJacobiMin && k <= kClusterJacobiMax)
+        if (k >= kClusterJacobiMin && k <= kClusterJacobiMax) {
             mid.push_back(jt);
-        else if (k <= kSmemJacobiMax)
+            mid_i.push_back(i);
+        } else if (k <= kSmemJacobiMax)
             small.push_back(jt);
         else
             large.push_back(jt);
@@ -533,6 +537,62 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
         by += 8.0 * 3.0 * k * (double)k;
     }
     ctx->flops += fl;
+    // 2a. FP32 preconditioning of the cluster tasks with k >= jacobi_precond_min:
+    // P = the rotations of an FP32 one-sided Jacobi of G (orthogonal to ~1e-6),
+    // Qp = the Q factor of P (FP64 Householder, orthogonal to FP64 rounding,
+    // diag R >= 0 keeps it next to P), G <- G Qp.  The FP64 Jacobi below then
+    // starts from nearly orthogonal columns and converges in a few sweeps
+    // (quadratically), and V <- Qp V afterwards: G Qp V = U S exactly as before,
+    // with every step that decides the result in FP64.
+    struct Pre {
+        size_t m;          // index in mid
+        double *Qp, *V1;
+    };
+    std::vector<Pre> pre;
+    if (ctx->jacobi_precond_min > 0 && !mid.empty()) {
+        const double fl0 = ctx->flops;   // the preconditioner's work is not algorithmic work of the SVD
+        std::vector<JacTask> pj;
+        std::vector<double*> P;
+        double pb = 0.0;
+        for (size_t m = 0; m < mid.size(); ++m) {
+            const int k = mid[m].k;
+            if (k < ctx->jacobi_precond_min) continue;
+            P.push_back(s.dbl((size_t)k * k));
+            pj.push_back({mid[m].G, P.back(), nullptr, k, 0});
+            pre.push_back({m, s.dbl((size_t)k * k), s.dbl((size_t)k * k)});
+            pb += 16.0 * k * (double)k;
+        }
+        bool ok = pj.empty();
+        if (!ok) {
+            ProfScope ps(ctx, KK_SVD, 0.0, pb);
+            ok = launch_jacobi_cluster_f32(ctx, pj);
+            ps.done();
+        }
+        if (ok && !pre.empty()) {
+            std::vector<QrTask> pq;
+            for (size_t j = 0; j < pre.size(); ++j) {
+                const int k = pj[j].k;
+                pq.push_back({P[j], pre[j].Qp, s.dbl((size_t)k * k), s.dbl((size_t)k), k, k});
+            }
+            launch_qr(ctx, pq, KK_SVD);
+            // G1 = G Qp (column-major): G1^T = Qp^T G^T, the buffers read row-major
+            std::vector<GemmOut> go;
+            std::vector<GemmIn> gi;
+            for (Pre& pr : pre) {
+                JacTask& jt = mid[pr.m];
+                double* G1 = s.dbl((size_t)jt.k * jt.k);
+                go.push_back({G1, jt.k, jt.k, jt.k, (int)gi.size(), (int)gi.size() + 1, 0.0});
+                gi.push_back({pr.Qp, jt.G, jt.k, jt.k, jt.k, 0, 1.0});
+                jt.G = G1;
+                R[mid_i[pr.m]] = G1;   // the rotated G that step 4 reads
+                jt.V = pr.V1;
+            }
+            launch_gemm(ctx, go, gi, KK_SVD);
+        } else {
+            pre.clear();
+        }
+        ctx->flops = fl0;
+    }
     {
         ProfScope ps(ctx, KK_SVD, fl, by);
         if (!mid.empty() && !launch_jacobi_cluster(ctx, mid)) {
@@ -556,6 +616,19 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
             check_launch(ctx);
         }
         ps.done();
+    }
+    if (!pre.empty()) {
+        // V = Qp V1 (column-major): V^T = V1^T Qp^T
+        const double fl0 = ctx->flops;
+        std::vector<GemmOut> go;
+        std::vector<GemmIn> gi;
+        for (const Pre& pr : pre) {
+            const int k = mid[pr.m].k;
+            go.push_back({V[mid_i[pr.m]], k, k, k, (int)gi.size(), (int)gi.size() + 1, 0.0});
+            gi.push_back({pr.V1, pr.Qp, k, k, k, 0, 1.0});
+        }
+        launch_gemm(ctx, go, gi, KK_SVD);
+        ctx->flops = fl0;
     }
     // 3. (Q V)^T = V^T Q^T: A = V column-major read as V^T row-major, B = Q column-major = Q^T row-major
     std::vector<GemmOut> outs;

@@ -92,6 +92,11 @@ constexpr int kClusterJacobiMax = 336;
 // FP64 units suffice for the latency of a round.
 constexpr int kClusterJacobiMin = 32;
 bool launch_jacobi_cluster(Context* ctx, const std::vector<JacTask>& tasks);
+// FP32 one-sided Jacobi of the same tasks as a preconditioner: reads G (FP64,
+// unchanged), writes to V the accumulated FP32 rotations as FP64 (orthogonal to
+// about 1e-6); Sraw unused.  Returns false, with nothing launched, when no
+// cluster can be scheduled.
+bool launch_jacobi_cluster_f32(Context* ctx, const std::vector<JacTask>& tasks);
 
 // C (M x N) = alpha op(A) B, op(A) = A (M x K) or A^T (A stored K x M), B
 // (K x N), all row-major FP64 on the device with leading dimensions, emulated by

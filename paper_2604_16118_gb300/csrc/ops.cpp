@@ -12,7 +12,7 @@
 namespace bsm {
 
 Mps::~Mps() {
-    if (ctx)
+    if (ctx && owns_cores)
         for (double* p : core)
             if (p) ctx->free(p);
 }

@@ -116,6 +116,13 @@ _SIGS = {
     "bsmps_mps_sectors": (_i, [_vp, _pi]),
     "bsmps_mps_size": (_i, [_vp, _pi64]),
     "bsmps_mps_export": (_i, [_vp, _pd]),
+    "bsmps_mps_write": (_i, [_vp, _pd, _i64]),
+    "bsmps_plan_apply_zipup_batch": (_i, [_vp, _i, C.POINTER(_vp), C.POINTER(_vp), _pd, C.POINTER(_vp),
+                                         C.POINTER(_vp), _pd]),
+    "bsmps_ctx_set_jacobi_precond": (_i, [_vp, _i]),
+    "bsmps_plan_launch": (_i, [_vp]),
+    "bsmps_plan_launch_count": (_i64, [_vp]),
+    "bsmps_plan_destroy": (_i, [_vp]),
     "bsmps_mps_destroy": (_i, [_vp]),
     "bsmps_mpo_from_integrals": (_i, [_vp, _i, _pd, _pd, _i, _i, _d, _d, C.POINTER(_vp)]),
     "bsmps_mpo_bond_dims": (_i, [_vp, _pi]),
@@ -219,6 +226,10 @@ class Context:
         """Arithmetic of the zip-up contraction stage (PREC_FP64 or PREC_TF32X3)."""
         _check(self, lib().bsmps_ctx_set_precision(self.h, int(precision)))
 
+    def set_jacobi_precond(self, min_k):
+        """Cluster Jacobi SVDs with k >= min_k start from an FP32 Jacobi (0: never)."""
+        _check(self, lib().bsmps_ctx_set_jacobi_precond(self.h, int(min_k)))
+
     def alloc_count(self):
         """Device-memory requests served by the context's allocator so far."""
         return int(lib().bsmps_ctx_alloc_count(self.h))
@@ -307,6 +318,11 @@ class MPS:
         v = np.zeros(max(self.size(), 1))
         _check(self.ctx, lib().bsmps_mps_export(self.h, _dptr(v)))
         return v[:self.size()]
+
+    def write(self, values):
+        """Overwrite the blocks in place (flat layout; bsmps_mps_write)."""
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        _check(self.ctx, lib().bsmps_mps_write(self.h, _dptr(v), len(v)))
 
 
 class MPO:
@@ -467,6 +483,41 @@ def apply_zipup_batch(ctx, mpos, xs, shifts):
     fl = C.c_double()
     _check(ctx, lib().bsmps_apply_zipup_batch(ctx.h, n, Wa, Xa, _dptr(sh), Ya, C.byref(fl)))
     return [MPS(ctx, _vp(Ya[i])) for i in range(n)], fl.value
+
+
+class ZipupPlan:
+    """A batch of zip-up applications recorded as one CUDA graph
+    (bsmps_plan_apply_zipup_batch): launch() replays it on the context's
+    stream; outputs are the MPS the replays overwrite."""
+
+    def __init__(self, ctx, mpos, xs, shifts):
+        n = len(xs)
+        Wa = (_vp * n)(*[w.h for w in mpos])
+        Xa = (_vp * n)(*[x.h for x in xs])
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        Ya = (_vp * n)()
+        fl = C.c_double()
+        h = _vp()
+        _check(ctx, lib().bsmps_plan_apply_zipup_batch(ctx.h, n, Wa, Xa, _dptr(sh), C.byref(h), Ya, C.byref(fl)))
+        self.ctx, self.h, self.flops = ctx, h, fl.value
+        self._inputs = (list(mpos), list(xs))   # the graph reads them
+        self.outputs = [MPS(ctx, _vp(Ya[i])) for i in range(n)]
+        for o in self.outputs:
+            o._plan = self   # the outputs' blocks live in the plan's memory
+
+    def launch(self):
+        _check(self.ctx, lib().bsmps_plan_launch(self.h))
+
+    def launch_count(self):
+        return int(lib().bsmps_plan_launch_count(self.h))
+
+    def __del__(self):
+        try:
+            if self.h:
+                lib().bsmps_plan_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
 
 
 def truncate(ctx, x, eps, r_max=0):

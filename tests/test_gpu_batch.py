@@ -64,3 +64,42 @@ def test_batch_of_one_and_empty_batch(nat, ctx):
     y1, _ = nat.apply_zipup(ctx, W, x, shift=0.25)
     assert ys[0].bonds() == y1.bonds()
     assert nat.apply_zipup_batch(ctx, [], [], [])[0] == []
+
+
+def test_recorded_plan_replays_the_batch(nat):
+    """bsmps_plan_apply_zipup_batch: the batch recorded as one CUDA graph; every
+    launch reproduces the oracle's zip-up of the values the inputs hold at that
+    point (rewritten in place between launches), and counts its kernels."""
+    import torch
+    stream = torch.cuda.Stream(device=torch.device("cuda", 0))
+    ctx = nat.Context(0, stream.cuda_stream)
+    Ws, xs, shifts = [], [], []
+    for i, (wl, r, gamma) in enumerate(BATCH):
+        vals = random_block_values(n_random(wl, r), 60 + i)
+        xs.append(nat.mps_create(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, r, vals))
+        Ws.append(nat.mpo_from_integrals(ctx, wl.h, wl.eri, wl.spin, wl.n_particles, gamma))
+        shifts.append(0.2 * (i + 1))
+    plan = nat.ZipupPlan(ctx, Ws, xs, shifts)
+    assert plan.flops > 0 and plan.launch_count() > 0
+    for rep, seed0 in enumerate((60, 80, 100)):
+        if rep:
+            for i, (wl, r, _) in enumerate(BATCH):
+                xs[i].write(random_block_values(n_random(wl, r), seed0 + i))
+        l0 = ctx.launch_count()
+        plan.launch()
+        ctx.sync()
+        assert ctx.launch_count() - l0 == plan.launch_count()
+        for i, (wl, r, gamma) in enumerate(BATCH):
+            vals = random_block_values(n_random(wl, r), seed0 + i)
+            oy = OB.apply_zipup(oracle_mpo(wl, gamma), oracle_random(wl, r, vals), shift=shifts[i])
+            assert plan.outputs[i].bonds() == oy.bonds
+            assert rel_distance(to_oracle(wl, plan.outputs[i]), oy) <= 1e-12
+    del plan
+
+
+def test_plan_needs_a_stream(nat, ctx):
+    wl, r, gamma = BATCH[0]
+    x = nat.mps_create(ctx, wl.n_orb, wl.spin, wl.n_up, wl.n_dn, r, random_block_values(n_random(wl, r), 1))
+    W = nat.mpo_from_integrals(ctx, wl.h, wl.eri, wl.spin, wl.n_particles, gamma)
+    with pytest.raises(nat.BsmpsError):
+        nat.ZipupPlan(ctx, [W], [x], [0.0])

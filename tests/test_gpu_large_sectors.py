@@ -49,12 +49,22 @@ def test_truncate_large_sectors_matches_oracle(nat, ctx, eps_rel):
     assert np.sqrt(max(OB.dot(d, d), 0.0)) <= eps_rel * nrm * (1 + 1e-6) + 1e-12 * nrm
 
 
-@pytest.mark.parametrize("eps_rel", [0.3, 1e-6])
-def test_truncate_with_wide_sector_svds(nat, ctx, eps_rel):
+@pytest.mark.parametrize("precond", [0, 32, 96])
+@pytest.mark.parametrize("eps_rel", [0.3, 1e-6, 1e-11])
+def test_truncate_with_wide_sector_svds(nat, ctx, eps_rel, precond):
     """A random spinless K = 20, N = 10 iterate at exact ranks (middle sectors of
-    252): the right sweep's SVDs reach k > 110, beyond shared memory, and run
-    as the grid-wide Jacobi."""
+    252): the right sweep's SVDs reach k > 110 and run on clusters, with the
+    FP64 Jacobi started plainly (precond = 0) or from the FP32 Jacobi for
+    k >= precond."""
     from oracle import fermion as OF
+    ctx.set_jacobi_precond(precond)
+    try:
+        _wide_sector_case(nat, ctx, eps_rel, OF)
+    finally:
+        ctx.set_jacobi_precond(96)
+
+
+def _wide_sector_case(nat, ctx, eps_rel, OF):
     K, N, r = 20, 10, 1024
     species = OF.site_species(K, 0)
     dims = OB.default_dims(species, (N, 0), r)
@@ -71,6 +81,9 @@ def test_truncate_with_wide_sector_svds(nat, ctx, eps_rel):
     gz = OB.dot(to_oracle_k(z, species, N), to_oracle_k(z, species, N))
     assert abs(gz - OB.dot(oz, oz)) <= 1e-12 * OB.dot(oz, oz)
     assert abs(dt - odt) <= 1e-9 * odt
+    # the truncated vector itself (unique when no cut splits a cluster)
+    d = OB.add(to_oracle_k(z, species, N), oz, 1.0, -1.0)
+    assert np.sqrt(max(OB.dot(d, d), 0.0)) <= 1e-10 * np.sqrt(OB.dot(oz, oz))
 
 
 def to_oracle_k(z, species, N):
