@@ -724,6 +724,7 @@ def main_full(args):
     stream = torch.cuda.Stream(device=dev)
     ctx = nat.Context(local, stream.cuda_stream)
     prec = nat.PREC_TF32X3 if args.precision == "tf32x3" else nat.PREC_FP64
+    ctx.set_jacobi_precond(args.jacobi_precond)
     S = setup(ctx, nat, seed=1)
     fl_branch = apply_flops_per_branch(nat, ctx, S)
     ctx.set_precision(prec)
@@ -816,7 +817,8 @@ def main_full(args):
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (tf32x3 contraction)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "step": "one Alg. 2 step from the full-rank iterate (same input every step)",
-                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "precision": args.precision, "jacobi_precond": args.jacobi_precond,
+                   "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "value": "zip-up MPO application (all preconditioner branches): contraction flops / device "
                             "time of the contraction and the zip-up's factorisation launches, from the timed steps "
@@ -1089,6 +1091,7 @@ def main_profile(args):
     from paper_2604_16118_gb300 import native as nat
     ctx = nat.Context(0)
     ctx.set_precision(nat.PREC_TF32X3 if args.precision == "tf32x3" else nat.PREC_FP64)
+    ctx.set_jacobi_precond(args.jacobi_precond)
     t0 = time.perf_counter()
     if args.workload == "profile_truncation":
         from synth import random_block_values
@@ -1106,7 +1109,8 @@ def main_profile(args):
             _, info = nat.eigensolve_step(ctx, S["W"], S["p"], S["sp"], nat.solver_state(), S["x"])
             what = {"lambda": info["lambda"], "rho": info["rho"], "flops": info["flops"]}
     ctx.sync()
-    print(json.dumps({"workload": args.workload, "precision": args.precision, "wall_s": time.perf_counter() - t0,
+    print(json.dumps({"workload": args.workload, "precision": args.precision, "jacobi_precond": args.jacobi_precond,
+                      "wall_s": time.perf_counter() - t0,
                       **what}))
     return 0
 
@@ -1120,6 +1124,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3"],
                     help="arithmetic of the zip-up contraction stage")
+    ap.add_argument("--jacobi-precond", type=int, default=48,
+                    help="truncation SVDs with k >= this start from an FP32 Jacobi (0: never)")
     ap.add_argument("--max-steps", type=int, default=400, help="hubbard_tta: step limit")
     ap.add_argument("--max-seconds", type=float, default=1800.0, help="hubbard_tta: time limit")
     ap.add_argument("--workload", default="hubbard",

@@ -514,7 +514,7 @@ BSMPS_API bsmps_status bsmps_ctx_set_gemm_emulation(bsmps_ctx ctx, int min_log2_
  * G Qp, whose FP64 Jacobi converges in a few sweeps; V = Qp V1.  Every
  * quantity the truncation reads (singular values, vectors) is still the
  * result of the FP64 Jacobi, to FP64 rounding.  min_k = 0 turns it off; the
- * default is 96.  Errors: INVALID_ARG (negative). */
+ * default is 48.  Errors: INVALID_ARG (negative). */
 BSMPS_API bsmps_status bsmps_ctx_set_jacobi_precond(bsmps_ctx ctx, int min_k);
 
 BSMPS_API bsmps_status bsmps_gemm_ozaki(bsmps_ctx ctx, int M, int N, int K, const double* A, int lda,

@@ -157,7 +157,7 @@ struct Context {
     int gemm_emulation_log2 = 0;     // block products >= 2^this flops on the tensor cores (0: never)
     int apply_precision = BSMPS_PREC_FP64;   // arithmetic of the zip-up contraction stage
     bool autotune = true;                    // autotune the FP64 zip-up contraction (launch_gemm)
-    int jacobi_precond_min = 96;             // cluster Jacobi from this k on starts from an FP32 Jacobi (0: never)
+    int jacobi_precond_min = 48;             // cluster Jacobi from this k on starts from an FP32 Jacobi (0: never)
     std::map<int64_t, int> gemm_tuned;       // size class -> chosen split between the two GEMM kernels
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;

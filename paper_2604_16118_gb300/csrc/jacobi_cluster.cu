@@ -42,10 +42,31 @@ constexpr int kClusterThreads = 512;
 constexpr int kClusterWarps = kClusterThreads / 32;
 constexpr size_t kClusterSmemMax = 225 * 1024;
 
-// shared memory of one CTA: two buffers of two block slots of b columns of G
-size_t cluster_smem(int k, int ctas) {
-    const size_t b = (size_t)(k + 2 * ctas - 1) / (2 * ctas);
-    return 4 * b * (size_t)k * sizeof(double);
+// Slot strides, in elements, rounded up to 16 bytes so that blocks move between
+// the CTAs' shared memories in 16-byte units: FP64 slot = b columns of G; FP32
+// slot = b columns of G, then b columns of V, each part 16-byte aligned.
+__host__ __device__ __forceinline__ size_t slot_f64(int b, int k) { return ((size_t)b * k + 1) & ~size_t(1); }
+__host__ __device__ __forceinline__ size_t part_f32(int b, int k) { return ((size_t)b * k + 3) & ~size_t(3); }
+
+// shared memory of one CTA: two buffers of two block slots
+size_t cluster_smem(int k, int ctas, bool f32) {
+    const int b = (k + 2 * ctas - 1) / (2 * ctas);
+    return f32 ? 4 * 2 * part_f32(b, k) * sizeof(float) : 4 * slot_f64(b, k) * sizeof(double);
+}
+
+// Copy n16 16-byte units from src (another CTA's shared memory) to dst, with
+// four loads in flight per thread; both 16-byte aligned.
+__device__ __forceinline__ void pull16(float4* __restrict__ dst, const float4* __restrict__ src, int n16) {
+    constexpr int T = kClusterThreads;
+    int e = threadIdx.x;
+    for (; e + 3 * T < n16; e += 4 * T) {
+        const float4 v0 = src[e], v1 = src[e + T], v2 = src[e + 2 * T], v3 = src[e + 3 * T];
+        dst[e] = v0;
+        dst[e + T] = v1;
+        dst[e + 2 * T] = v2;
+        dst[e + 3 * T] = v3;
+    }
+    for (; e < n16; e += T) dst[e] = src[e];
 }
 
 // Block at tournament position p in step s (n2m1 = 2C - 1; position 0 fixed).
@@ -102,7 +123,8 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTas
     const int b = (k + nblk - 1) / nblk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // slot sl of buffer buf: b columns of k rows
-    auto slot = [&](int buf, int sl) { return jc_smem + (size_t)(buf * 2 + sl) * b * k; };
+    const size_t sstride = slot_f64(b, k);
+    auto slot = [&](int buf, int sl) { return jc_smem + (size_t)(buf * 2 + sl) * sstride; };
     auto bcols = [&](int beta) { return max(0, min(b, k - beta * b)); };
     // step 0: CTA c holds blocks c (slot 0) and 2C-1-c (slot 1); load them, set
     // their columns of V to the identity, partial ||G||_F^2
@@ -180,9 +202,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTas
                 const int hp = pos_of(beta, s, n2m1);   // its position in this step
                 const int holder = hp < C ? hp : nblk - 1 - hp;
                 const double* src = cluster.map_shared_rank(slot(cur, hp < C ? 0 : 1), holder);
-                double* dst = slot(cur ^ 1, sl);
-                const int64_t n = (int64_t)bcols(beta) * k;
-                for (int64_t e = threadIdx.x; e < n; e += kClusterThreads) dst[e] = src[e];
+                pull16((float4*)slot(cur ^ 1, sl), (const float4*)src, (bcols(beta) * k + 1) / 2);
             }
             __syncthreads();
         }
@@ -229,7 +249,8 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTas
 // own norms, so they are rotated too, which leaves the FP64 Jacobi only the
 // last quadratic sweeps at every scale.  The rotation is that of
 // dev::jacobi_rotation_fast in FP32, with d = b - a and 2g scaled by their
-// larger magnitude so that no square underflows.  Output: tk.V = the FP32 V as
+// larger magnitude so that no square underflows.  A sweep that rotates at most
+// 1/32 of the pairs ends the iteration (at most kMaxSweepsF32).  Output: tk.V = the FP32 V as
 // FP64 (orthogonal to about 1e-6); tk.G is read only; tk.Sraw unused.
 constexpr int kMaxSweepsF32 = 20;
 
@@ -265,7 +286,7 @@ __device__ __forceinline__ void rotate_pair_f32(float* Gp, float* Gq, float* Vp,
             Vp[i] = c * vp - sn * vq;
             Vq[i] = sn * vp + c * vq;
         }
-        if (lane == 0) *s_rot = 1;
+        if (lane == 0) atomicAdd(s_rot, 1);
     }
 }
 
@@ -284,7 +305,8 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster_f32(const Ja
     const int b = (k + nblk - 1) / nblk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // slot sl of buffer buf: b columns of G, then b columns of V (k rows each)
-    auto slot = [&](int buf, int sl) { return jf_smem + (size_t)(buf * 2 + sl) * 2 * b * k; };
+    const size_t vpart = part_f32(b, k);   // offset of the V columns in a slot
+    auto slot = [&](int buf, int sl) { return jf_smem + (size_t)(buf * 2 + sl) * 2 * vpart; };
     auto bcols = [&](int beta) { return max(0, min(b, k - beta * b)); };
     double f = 0.0;
     for (int sl = 0; sl < 2; ++sl) {
@@ -315,7 +337,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster_f32(const Ja
         for (int64_t e = threadIdx.x; e < (int64_t)nc * k; e += kClusterThreads) {
             dst[e] = (float)(tk.G[off + e] * sc);
             const int j = (int)(e / k), i = (int)(e % k);
-            dst[(int64_t)b * k + e] = i == beta * b + j ? 1.0f : 0.0f;
+            dst[vpart + e] = i == beta * b + j ? 1.0f : 0.0f;
         }
     }
     __syncthreads();
@@ -329,8 +351,8 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster_f32(const Ja
             const int nL = bcols(bL), nR = bcols(bR);
             float* L = slot(cur, 0);
             float* R = slot(cur, 1);
-            float* LV = L + (size_t)b * k;
-            float* RV = R + (size_t)b * k;
+            float* LV = L + vpart;
+            float* RV = R + vpart;
             if (s == 0) {
                 const int nb = max(nL, nR), nb2 = nb + (nb & 1), half = nb2 / 2;
                 for (int round = 0; round < nb2 - 1; ++round) {
@@ -369,28 +391,28 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster_f32(const Ja
                 const int holder = hp < C ? hp : nblk - 1 - hp;
                 const float* src = cluster.map_shared_rank(slot(cur, hp < C ? 0 : 1), holder);
                 float* dst = slot(cur ^ 1, sl);
-                const int64_t n = (int64_t)bcols(beta) * k;
-                for (int64_t e = threadIdx.x; e < n; e += kClusterThreads) {
-                    dst[e] = src[e];
-                    dst[(int64_t)b * k + e] = src[(int64_t)b * k + e];
-                }
+                const int n16 = (bcols(beta) * k + 3) / 4;
+                pull16((float4*)dst, (const float4*)src, n16);
+                pull16((float4*)(dst + vpart), (const float4*)(src + vpart), n16);
             }
             __syncthreads();
         }
+        // rotation counts of the sweep; a sweep that rotated at most 1/32 of the
+        // pairs ends the FP32 iteration (the FP64 Jacobi takes the rest)
         const int par = sweep & 1;
         if (threadIdx.x == 0) {
             flag0[par * C + rank] = s_rot;
             s_rot = 0;
         }
         cluster.sync();
-        int rot = 0;
-        for (int c = 0; c < C; ++c) rot |= flag0[par * C + c];
-        if (!rot) break;
+        int64_t rot = 0;
+        for (int c = 0; c < C; ++c) rot += flag0[par * C + c];
+        if (32 * rot <= (int64_t)k * (k - 1) / 2) break;
     }
     const int cur = gstep & 1, s_now = gstep % n2m1;
     for (int sl = 0; sl < 2; ++sl) {
         const int beta = block_at(sl == 0 ? rank : nblk - 1 - rank, s_now, n2m1);
-        const float* XV = slot(cur, sl) + (size_t)b * k;
+        const float* XV = slot(cur, sl) + vpart;
         const int64_t off = (int64_t)beta * b * k;
         for (int64_t e = threadIdx.x; e < (int64_t)bcols(beta) * k; e += kClusterThreads) tk.V[off + e] = XV[e];
     }
@@ -401,7 +423,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster_f32(const Ja
 // false (nothing launched) when such clusters cannot be scheduled.
 template <int C>
 bool launch_cluster_size(Context* ctx, const std::vector<JacTask>& tasks, int kmax, bool f32 = false) {
-    const size_t smem = cluster_smem(kmax, C);   // FP32: G and V in the same bytes as the FP64 G
+    const size_t smem = cluster_smem(kmax, C, f32);
     if (smem > kClusterSmemMax) return false;
     void (*kern)(const JacTask*) = f32 ? k_jacobi_cluster_f32<C> : k_jacobi_cluster<C>;
     static bool attr[2] = {false, false};
