@@ -179,7 +179,8 @@ BSMPS_API int64_t bsmps_ctx_alloc_count(bsmps_ctx ctx);
  * bsmps_ctx_kernel_stats synchronises the stream and returns, for kernel kind
  * `kind` (0 copy, 1 grouped GEMM, 2 QR, 3 SVD, 4 sum of squares, 5 the
  * contraction stage of the zip-up MPO application, 6 the zip-up's own
- * factorisation launches: zeroing, gathers, QR), the number
+ * factorisation launches: zeroing, gathers, QR; 7 the tensor-core products
+ * of the learned controller's network, FP32 flops), the number
  * of recorded launches, their summed device time in ms and summed
  * algorithmic FP64 flops and bytes; `reset` != 0 clears the records after
  * reading.  Errors: INVALID_ARG (kind out of range), CUDA. */

@@ -6,7 +6,13 @@ Definition: layers l map widths[l] -> widths[l+1], y = W h + b with W stored
 row-major (out x in); ReLU on hidden layers, linear output; loss = mean over
 batch and outputs of (y - t)^2.  The weights and biases used in the products
 are the FP32 parameters rounded to bfloat16 (round to nearest, ties to even),
-as in the product; everything else is FP64 here.
+as in the product.  With tf32=True (the product's network: its products run
+on the tensor cores in TF32) the other operand of every product -- the layer
+input h in the forward pass and in the weight gradient, the back-propagated
+error dy in both gradients -- enters rounded to FP32 and then to TF32 (10
+mantissa bits, nearest, ties away from zero); the bf16 weights are exact in
+TF32.  Everything else is FP64 here.  tf32=False is the exact network, which
+the finite-difference pin checks.
 """
 
 import numpy as np
@@ -19,6 +25,19 @@ def bf16_round(x):
     bias = 0x7FFF + ((bits >> 16) & 1)
     r = ((bits + bias) & 0xFFFF0000).astype(np.uint32)
     return r.view(np.float32).astype(np.float64)
+
+
+def tf32_round(x):
+    """Round to FP32, then to the nearest TF32 value (10 mantissa bits, ties away
+    from zero: add half an ulp to the magnitude bits and truncate), as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    r = ((bits + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def _identity(x):
+    return np.asarray(x, dtype=np.float64)
 
 
 def unpack(params, widths):
@@ -34,25 +53,27 @@ def unpack(params, widths):
     return out
 
 
-def forward(params, widths, x):
+def forward(params, widths, x, tf32=False):
     """Activations h_0 = x, ..., h_L = y with bf16-rounded parameters."""
+    rnd = tf32_round if tf32 else _identity
     layers = unpack(bf16_round(params), widths)
     hs = [np.asarray(x, dtype=np.float64)]
     for l, (W, b) in enumerate(layers):
-        z = hs[-1] @ W.T + b
+        z = rnd(hs[-1]) @ W.T + b
         hs.append(np.maximum(z, 0.0) if l + 1 < len(layers) else z)
     return hs
 
 
-def loss(params, widths, x, t):
-    y = forward(params, widths, x)[-1]
+def loss(params, widths, x, t, tf32=False):
+    y = forward(params, widths, x, tf32)[-1]
     return float(np.mean((y - np.asarray(t, dtype=np.float64)) ** 2))
 
 
-def loss_grad(params, widths, x, t):
+def loss_grad(params, widths, x, t, tf32=False):
     """Loss and its gradient w.r.t. the (bf16-rounded) flat parameters by backpropagation."""
+    rnd = tf32_round if tf32 else _identity
     layers = unpack(bf16_round(params), widths)
-    hs = forward(params, widths, x)
+    hs = forward(params, widths, x, tf32)
     y = hs[-1]
     t = np.asarray(t, dtype=np.float64)
     n = y.size
@@ -60,11 +81,12 @@ def loss_grad(params, widths, x, t):
     grads = []
     for l in range(len(layers) - 1, -1, -1):
         W, _ = layers[l]
-        dW = dy.T @ hs[l]
-        db = dy.sum(axis=0)
+        dyr = rnd(dy)
+        dW = dyr.T @ rnd(hs[l])
+        db = dyr.sum(axis=0)
         grads.append((dW, db))
         if l > 0:
-            dy = (dy @ W) * (hs[l] > 0.0)
+            dy = (dyr @ W) * (hs[l] > 0.0)
     grads.reverse()
     flat = np.concatenate([np.concatenate([dW.reshape(-1), db]) for dW, db in grads])
     return float(np.mean((y - t) ** 2)), flat

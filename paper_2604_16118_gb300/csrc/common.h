@@ -141,7 +141,7 @@ struct ProfRec {
 // KK_APPLY: the contraction stage of the zip-up MPO application (grouped GEMM);
 // KK_APPLY_QR: the zip-up's own factorisation launches (zeroing, gathers, QR)
 enum KernelKind { KK_COPY = 0, KK_GEMM = 1, KK_QR = 2, KK_SVD = 3, KK_SUMSQ = 4, KK_APPLY = 5, KK_APPLY_QR = 6,
-                  KK_COUNT = 7 };
+                  KK_MLP = 7, KK_COUNT = 8 };
 
 struct Context {
     int device = 0;

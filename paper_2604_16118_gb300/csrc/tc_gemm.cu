@@ -26,6 +26,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace bsm {
 namespace {
@@ -35,46 +36,25 @@ constexpr int kTcN = 64;          // columns of a tile: the N of one tcgen05.mma
 constexpr int kTcK = 32;          // k values per staged chunk (4 MMAs of K = 8 for tf32)
 constexpr int kTcThreads = 128;   // warp w reads TMEM lanes 32 w .. 32 w + 31
 constexpr int kTcOperandBytes = (2 * kTcM + 2 * kTcN) * kTcK * 4;   // A_hi, A_lo, B_hi, B_lo
-constexpr unsigned long long kTcWaitNs = 1000000000ull;              // 1 s
 
 struct TcTile {
     int out, m0, n0;
 };
 
-// Byte offset of element (row r, k) of a K-major operand tile in the canonical
-// layout without swizzle: 8-row x 16-byte core matrices, the 8 core matrices
-// of a row group along k contiguous (leading byte offset 128), row groups 1024
-// bytes apart (stride byte offset).
-__device__ __forceinline__ uint32_t tc_off(int r, int k) {
-    return (uint32_t)((r >> 3) * 1024 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
+constexpr uint32_t kTcIdesc = tc::idesc_tf32(kTcM, kTcN);
+using tc::global_ns;
+using tc::mbar_wait;
+using tc::smem_addr;
+using tc::tf32_bits;
 
-// Shared-memory matrix descriptor: start address, leading / stride byte
-// offsets (in 16-byte units), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(128u >> 4) << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor of kind::tf32: D in FP32, A and B TF32 and K-major,
-// N = kTcN, M = kTcM.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kTcM >> 4) << 24);
-
-// Round to the nearest TF32 value (10 mantissa bits), ties away from zero.
-__device__ __forceinline__ uint32_t tf32_bits(float f) { return (__float_as_uint(f) + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ uint32_t tc_off(int r, int k) { return tc::off(r, k); }
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) { return tc::desc(saddr); }
 
 __device__ __forceinline__ void tf32_split(double v, uint32_t* hi, uint32_t* lo) {
     const uint32_t h = tf32_bits((float)v);
     *hi = h;
     *lo = tf32_bits((float)(v - (double)__uint_as_float(h)));
 }
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Exponent e with 2^-e x in [1, 2) for the largest magnitude x given by its bit
 // pattern (0 for x = 0: such rows and columns hold zeros only).
@@ -83,35 +63,8 @@ __device__ __forceinline__ int pow2_exponent(unsigned long long bits) {
     return (int)((bits >> 52) & 0x7ff) - 1023;
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the mbarrier phase with the given parity; false when the wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const unsigned long long t0 = global_ns();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (global_ns() - t0 > kTcWaitNs) return false;
-    }
-}
-
 __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-        "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate));
+    tc::mma_tf32(tmem, adesc, bdesc, kTcIdesc, accumulate);
 }
 
 __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __restrict__ outs,

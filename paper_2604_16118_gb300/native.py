@@ -234,7 +234,7 @@ class Context:
         """Device-memory requests served by the context's allocator so far."""
         return int(lib().bsmps_ctx_alloc_count(self.h))
 
-    KERNELS = ("copy", "gemm", "qr", "svd", "sumsq", "apply", "apply_qr")
+    KERNELS = ("copy", "gemm", "qr", "svd", "sumsq", "apply", "apply_qr", "mlp")
 
     def set_gemm_emulation(self, min_log2_flops=0):
         """Block products of at least 2^min_log2_flops flops on the tensor cores

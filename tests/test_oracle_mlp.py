@@ -43,3 +43,30 @@ def test_gradient_matches_finite_differences():
         e[j] = h
         fd = (f(p + e) - f(p - e)) / (2 * h)
         assert abs(fd - g[j]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_tf32_rounding_ties_away():
+    # 1 + 2^-11 is a tie between 1 and 1 + 2^-10: rounds away from zero
+    x = np.array([1.0 + 2.0 ** -11, -(1.0 + 2.0 ** -11), 1.0 + 2.0 ** -12, 1.0 + 3 * 2.0 ** -11, 0.0])
+    r = OM.tf32_round(x)
+    assert r[0] == 1.0 + 2.0 ** -10 and r[1] == -(1.0 + 2.0 ** -10) and r[2] == 1.0
+    assert r[3] == 1.0 + 2.0 ** -9 and r[4] == 0.0
+    # bf16 values are TF32 values; the error is within half a TF32 ulp
+    y = np.random.default_rng(0).standard_normal(1000).astype(np.float32)
+    assert np.array_equal(OM.tf32_round(OM.bf16_round(y)), OM.bf16_round(y))
+    assert np.all(np.abs(OM.tf32_round(y) - y) <= np.abs(y) * 2.0 ** -11)
+
+
+def test_tf32_network_is_the_exact_one_on_tf32_data():
+    """With inputs, errors and activations already TF32 values the rounded
+    network is the exact one: here every product operand is a small dyadic
+    number (exact in TF32), so both give the same loss and gradient."""
+    widths = [4, 3, 2]
+    x = np.array([[0.5, -1.0, 0.25, 2.0], [1.0, 0.0, -0.5, 0.75]])
+    p = np.zeros(4 * 3 + 3 + 3 * 2 + 2, dtype=np.float32)
+    p[:12] = np.array([1, 0, -1, 0.5, 0.25, 1, 0, 0, -0.5, 0, 1, 2], dtype=np.float32)
+    p[15:21] = np.array([1, -1, 0.5, 0, 0.25, 1], dtype=np.float32)
+    t = np.array([[0.25, -0.5], [1.0, 0.0]])
+    l0, g0 = OM.loss_grad(p, widths, x, t, tf32=False)
+    l1, g1 = OM.loss_grad(p, widths, x, t, tf32=True)
+    assert l0 == l1 and np.array_equal(g0, g1)
