@@ -265,6 +265,13 @@ bsmps_status bsmps_ctx_destroy(bsmps_ctx ctx) {
             cudaEventDestroy(r.e1);
         }
         for (auto e : ctx->c.event_pool) cudaEventDestroy(e);
+        if (ctx->c.side) {
+            cudaStreamSynchronize(ctx->c.side);
+            cudaStreamDestroy(ctx->c.side);
+            cudaEventDestroy(ctx->c.fork_ev);
+            cudaEventDestroy(ctx->c.join_ev);
+            ctx->c.side = nullptr;
+        }
         ctx->c.release_ring();
         ctx->c.release_cache();
         ctx->c.sync();

@@ -152,6 +152,26 @@ struct Context {
     size_t alloc_bytes = 0;          // bytes requested from alloc() (256-byte granules), running total
     size_t upload_bytes = 0;         // bytes staged by upload_raw() (256-byte granules), running total
     PlanArena* rec = nullptr;        // set while a graph is being recorded
+    // A second stream for independent launches of one sweep step: work forked
+    // onto it after an event on `stream`, joined back by an event before the
+    // step's results are read; every buffer it touches is allocated before the
+    // fork and released after the join (the allocator orders reuse by `stream`).
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaStream_t fork_side() {
+        if (!side) {
+            BSM_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+            BSM_CUDA(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+            BSM_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+        }
+        BSM_CUDA(cudaEventRecord(fork_ev, stream));
+        BSM_CUDA(cudaStreamWaitEvent(side, fork_ev, 0));
+        return side;
+    }
+    void join_side() {
+        BSM_CUDA(cudaEventRecord(join_ev, side));
+        BSM_CUDA(cudaStreamWaitEvent(stream, join_ev, 0));
+    }
     double flops = 0.0;              // algorithmic FP64 flops issued (running total)
     bool profiling = false;
     int gemm_emulation_log2 = 0;     // block products >= 2^this flops on the tensor cores (0: never)

@@ -186,7 +186,11 @@ struct SvdSiteTask {
     double* Vt;
 };
 bool svd_site_fits(int M, int N);
-void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const std::vector<SvdPart>& parts);
+// keep: holds the uploaded task lists (the caller releases it after any join);
+// on_side: the kernel runs on the context's second stream, forked after the
+// uploads (the caller joins before reading the results).
+void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const std::vector<SvdPart>& parts,
+                     Scratch& keep, bool on_side = false);
 
 // After the cut of bond t, one CTA per kept sector n: copy the kept V^T rows into
 // the new core-t blocks and multiply the core-(t-1) blocks ending in n by the

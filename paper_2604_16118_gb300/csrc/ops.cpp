@@ -564,6 +564,10 @@ void right_sweep_sitewise(Context* ctx, TruncJob& J) {
             else
                 gen_sec.push_back(ni);
         }
+        // the one-CTA sector SVDs overlap the cluster chain of the wide sectors
+        // on the context's second stream (joined before the singular values
+        // are read; their buffers live in s until the end of the bond)
+        const bool overlap = !site_sec.empty() && !gen_sec.empty() && !ctx->profiling && !ctx->rec;
         if (!site_sec.empty()) {
             std::vector<SvdSiteTask> st;
             std::vector<SvdPart> parts;
@@ -582,7 +586,7 @@ void right_sweep_sitewise(Context* ctx, TruncJob& J) {
                 task.p_end = (int)parts.size();
                 st.push_back(task);
             }
-            launch_svd_site(ctx, st, parts);
+            launch_svd_site(ctx, st, parts, s, overlap);
         }
         if (!gen_sec.empty()) {
             std::vector<CopyTask> gather;
@@ -610,6 +614,7 @@ void right_sweep_sitewise(Context* ctx, TruncJob& J) {
             launch_copy(ctx, gather);
             launch_svd(ctx, svd);
         }
+        if (overlap) ctx->join_side();
         std::vector<double> S_h((size_t)stot);
         if (stot > 0) {
             BSM_CUDA(cudaMemcpyAsync(S_h.data(), S_all, (size_t)stot * sizeof(double),

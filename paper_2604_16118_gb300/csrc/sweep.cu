@@ -973,7 +973,8 @@ void launch_left_site(Context* ctx, const std::vector<LeftTask>& tasks, const st
     pr.done();
 }
 
-void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const std::vector<SvdPart>& parts) {
+void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const std::vector<SvdPart>& parts,
+                     Scratch& keep, bool on_side) {
     if (tasks.empty()) return;
     size_t smem = 0;
     double fl = 0.0, by = 0.0;
@@ -988,14 +989,15 @@ void launch_svd_site(Context* ctx, const std::vector<SvdSiteTask>& tasks, const 
     ctx->flops += fl;
     Pack pk;
     const size_t ot = pk.add(tasks), op = pk.add(parts);
-    Scratch s(ctx);
-    unsigned char* d = upload_pack(s, pk);
+    unsigned char* d = upload_pack(keep, pk);
+    on_side = on_side && !ctx->profiling;   // profiled launches stay on the context stream
     Prof pr(ctx, KK_SVD, fl, by);
     allow_smem(k_svd_site);
     int kmax = 1;
     for (const SvdSiteTask& t : tasks) kmax = std::max(kmax, t.k);
-    k_svd_site<<<(unsigned)tasks.size(), block_for(kmax, kSvdWarps), smem, ctx->stream>>>((const SvdSiteTask*)(d + ot),
-                                                                       (const SvdPart*)(d + op));
+    const cudaStream_t st = on_side ? ctx->fork_side() : ctx->stream;
+    k_svd_site<<<(unsigned)tasks.size(), block_for(kmax, kSvdWarps), smem, st>>>((const SvdSiteTask*)(d + ot),
+                                                                                 (const SvdPart*)(d + op));
     count_launch(ctx);
     pr.done();
 }
