@@ -158,6 +158,7 @@ struct Context {
     // fork and released after the join (the allocator orders reuse by `stream`).
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool side_open = false;          // forked and not yet joined
     cudaStream_t fork_side() {
         if (!side) {
             BSM_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
@@ -166,11 +167,13 @@ struct Context {
         }
         BSM_CUDA(cudaEventRecord(fork_ev, stream));
         BSM_CUDA(cudaStreamWaitEvent(side, fork_ev, 0));
+        side_open = true;
         return side;
     }
     void join_side() {
         BSM_CUDA(cudaEventRecord(join_ev, side));
         BSM_CUDA(cudaStreamWaitEvent(stream, join_ev, 0));
+        side_open = false;
     }
     double flops = 0.0;              // algorithmic FP64 flops issued (running total)
     bool profiling = false;

@@ -470,26 +470,36 @@ void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in, int kind) {
     ctx->flops += fl;
     Scratch s(ctx);
     ProfScope ps(ctx, kind, fl, by);
-    if (!clustered.empty() && !launch_qr_cluster(ctx, clustered)) {
-        for (QrTask t : clustered) {   // no cluster could be scheduled: one CTA per matrix
-            const size_t need = sizeof(double) * ((size_t)t.M * t.N + (size_t)t.M * std::min(t.M, t.N) +
-                                                  (size_t)std::min(t.M, t.N));
-            t.smem = need <= kSmemBudget ? 1 : 0;
-            if (t.smem) smem_max = std::max(smem_max, need);
-            (t.smem ? small : large).push_back(t);
+    bool cluster_ran = false;
+    if (!clustered.empty()) {
+        cluster_ran = launch_qr_cluster(ctx, clustered);
+        if (!cluster_ran) {
+            for (QrTask t : clustered) {   // no cluster could be scheduled: one CTA per matrix
+                const size_t need = sizeof(double) * ((size_t)t.M * t.N + (size_t)t.M * std::min(t.M, t.N) +
+                                                      (size_t)std::min(t.M, t.N));
+                t.smem = need <= kSmemBudget ? 1 : 0;
+                if (t.smem) smem_max = std::max(smem_max, need);
+                (t.smem ? small : large).push_back(t);
+            }
         }
     }
-    if (!small.empty()) {
-        QrTask* d = s.up(small);
+    // the one-CTA QRs overlap the cluster QRs on the context's second stream:
+    // their task lists are uploaded first, the fork follows, the join precedes
+    // the release of s
+    QrTask* d_small = small.empty() ? nullptr : s.up(small);
+    QrTask* d_large = large.empty() ? nullptr : s.up(large);
+    const bool overlap = cluster_ran && (d_small || d_large) && !ctx->profiling && !ctx->rec && !ctx->side_open;
+    const cudaStream_t st = overlap ? ctx->fork_side() : ctx->stream;
+    if (d_small) {
         BSM_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-        k_qr<<<(unsigned)small.size(), kThreads, smem_max, ctx->stream>>>(d);
+        k_qr<<<(unsigned)small.size(), kThreads, smem_max, st>>>(d_small);
         check_launch(ctx);
     }
-    if (!large.empty()) {
-        QrTask* d = s.up(large);
-        k_qr<<<(unsigned)large.size(), kThreads, 0, ctx->stream>>>(d);
+    if (d_large) {
+        k_qr<<<(unsigned)large.size(), kThreads, 0, st>>>(d_large);
         check_launch(ctx);
     }
+    if (overlap) ctx->join_side();
     ps.done();
 }
 
