@@ -995,6 +995,85 @@ def main_tta_k12(args):
     return 0
 
 
+def main_tta_learned(args):
+    """Time to |E - E_ref| <= 1e-8 Eh on the spinless random chain K = 12, N = 6
+    (config-1 generator, seed 0; E_ref exact, stored by
+    tests/golden/make_config1_trajectory.py), from e_1 without a rank cap, in
+    four arms: FP64 or split-precision (tf32x3) contraction, each with the plain
+    preconditioner parameters (c_0 = 0.1, margin 1) or the learned controller's
+    choice with its per-step plain fallback.  The controller is trained first,
+    inside this run, on the plain solver's grid scores of 12 small problems
+    (molecule-like L = 3, 4 and spinless chains K = 6, 8) by the library's
+    tensor-core network kernels; its training time is reported separately.
+    value: the mixed + learned arm's time; the plain FP64 arm's time beside it."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2604_16118_gb300 import build
+    build.build()
+    from paper_2604_16118_gb300 import learned as LP
+    from paper_2604_16118_gb300 import native as nat
+    from synth import molecule_like, spinless_random_chain
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_config1_trajectory.json")) as f:
+        g = json.load(f)
+    w, cst = g["workload"], g["constants"]
+    e_ref = cst["lambda1"] - cst["gamma"]
+    wl = spinless_random_chain(K=w["K"], N=w["N"], seed=w["seed"])
+    stream = torch.cuda.Stream(device=dev)
+    ctx = nat.Context(local, stream.cuda_stream)
+    train_p = []
+    for s_ in range(6):
+        train_p.append(molecule_like(L=3 + s_ % 2, n_up=1 + s_ % 2, n_dn=1 + (s_ // 2) % 2, seed=100 + s_))
+        K = 6 + 2 * (s_ % 2)
+        train_p.append(spinless_random_chain(K=K, N=K // 2, seed=200 + s_))
+    t0 = time.perf_counter()
+    X, Y, _ = LP.make_dataset(ctx, train_p, n_steps=3)
+    net, losses = LP.train(ctx, X, Y, steps=300)
+    t_train = time.perf_counter() - t0
+    choice = LP.choose(net, wl)
+    sampler = ClockSampler(local)
+    sampler.start()
+    arms = {}
+    for prec in ("fp64", "tf32x3"):
+        for kind in ("plain", "learned"):
+            ctx.set_precision(nat.PREC_TF32X3 if prec == "tf32x3" else nat.PREC_FP64)
+            trace = []
+            reached = []
+
+            def stop(e):
+                if abs(e - e_ref) <= 1e-8:
+                    reached.append(True)
+                    return True
+                return False
+
+            ctx.sync()
+            E, F, used = LP.solve(ctx, net, wl, args.max_steps, r_max=0,
+                                  params=LP.PLAIN if kind == "plain" else None, stop=stop, trace=trace)
+            arms[f"{prec}+{kind}"] = {
+                "seconds": trace[-1][0] if (trace and reached) else None, "steps": len(E),
+                "final_error": E[-1] - e_ref if E else None, "gflop": sum(F) * 1e-9,
+                "params": [list(u) for u in sorted(set(used))]}
+    clocks = sampler.stop()
+    ctx.set_precision(nat.PREC_FP64)
+    ml, fp = arms["tf32x3+learned"]["seconds"], arms["fp64+plain"]["seconds"]
+    out = {"metric": "time to |E - E_ref| <= 1e-8 Eh, mixed + learned vs FP64 plain", "value": ml, "unit": "s",
+           "n_gpus": 1, "steps": arms["tf32x3+learned"]["steps"], "warmup": 0,
+           "ms_per_step": 1e3 * ml / arms["tf32x3+learned"]["steps"] if ml else None,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (tf32x3 contraction)", "data": "synthetic",
+           "config": {"workload": "spinless_random_chain K=12 N=6 seed 0 (config-1 generator) from e_1, no rank "
+                                  "cap, E_ref by exact diagonalisation; set-up of the controller's problems "
+                                  "(c = 0.7, delta = 20, t_eig = 0.5)",
+                      "l2": "not flushed (one solve per arm)"},
+           "clocks": clocks, "fp64_plain_seconds": fp, "speedup_vs_fp64_plain": (fp / ml) if (fp and ml) else None,
+           "arms": arms, "controller": {"choice": list(choice), "train_seconds": t_train,
+                                        "loss_first_last": [losses[0], losses[-1]], "samples": int(len(X))},
+           "e2e": {"value": ml, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
 def main_batched(args):
     """The batched form: zip-up applications of 128 independent molecule-like
     Hamiltonians (the generator of configs 3 and 4; L cycling through 3..6,
@@ -1208,7 +1287,8 @@ def main():
     ap.add_argument("--max-steps", type=int, default=400, help="hubbard_tta: step limit")
     ap.add_argument("--max-seconds", type=float, default=1800.0, help="hubbard_tta: time limit")
     ap.add_argument("--workload", default="hubbard",
-                    choices=["hubbard", "hubbard_e1", "hubbard_tta", "tta_k12", "batched", "coulomb14_alg4_D4",
+                    choices=["hubbard", "hubbard_e1", "hubbard_tta", "tta_k12", "tta_learned", "batched",
+                             "coulomb14_alg4_D4",
                              "coulomb14_alg3", "ozaki_gemm", "mlp", "profile_step", "profile_apply",
                              "profile_truncation"],
                     help="hubbard: Alg. 2 steps at full rank (the JSON contract); hubbard_e1: the trajectory "
@@ -1226,6 +1306,8 @@ def main():
         return main_tta(args)
     if args.workload == "tta_k12":
         return main_tta_k12(args)
+    if args.workload == "tta_learned":
+        return main_tta_learned(args)
     if args.workload == "batched":
         return main_batched(args)
     if args.workload == "mlp":

@@ -1,6 +1,7 @@
 // Grouped FP64-in / FP64-out GEMM on the 5th-generation tensor cores in split
 // precision (3xTF32): every operand value v (scaled by its contribution's alpha)
-// is split into v_hi = tf32(v) and v_lo = tf32(v - v_hi), and a tile accumulates
+// is split into v_hi (its leading 11 significant bits) and v_lo = tf32(v - v_hi),
+// by integer operations on the FP64 bit pattern, and a tile accumulates
 // A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 in tensor memory (the A_lo B_lo term,
 // below 2^-21 relative, is dropped).  The relative error of an entry is a few
 // units of 2^-21 times sum_k |a_ik| |b_kj| plus the FP32 accumulation error.
@@ -50,10 +51,48 @@ using tc::tf32_bits;
 __device__ __forceinline__ uint32_t tc_off(int r, int k) { return tc::off(r, k); }
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) { return tc::desc(saddr); }
 
-__device__ __forceinline__ void tf32_split(double v, uint32_t* hi, uint32_t* lo) {
-    const uint32_t h = tf32_bits((float)v);
-    *hi = h;
-    *lo = tf32_bits((float)(v - (double)__uint_as_float(h)));
+// v 2^-sc for the FP64 value with bit pattern `bits`, split into TF32 parts
+// (FP32 bit patterns) by integer operations only (this GPU's FP64 pipe retires
+// one warp instruction per 16 cycles per SM): hi = the leading 11 significant
+// bits (truncated), lo = the rest rounded to TF32, so |v 2^-sc - hi - lo| <=
+// 2^-22 |v 2^-sc|.  The scaling is an exponent subtraction (exact); a scaled
+// value below FP32's normal range (2^-126 of a row or column maximum brought
+// to [1, 2)) becomes 0, as do FP64 zeros and subnormals.
+__device__ __forceinline__ void split_scaled(unsigned long long bits, int sc, uint32_t* hi, uint32_t* lo) {
+    const uint32_t sign = (uint32_t)(bits >> 32) & 0x80000000u;
+    const int e = (int)((bits >> 52) & 0x7ff);
+    const int E = e - 1023 - sc;
+    if (e == 0 || E < -126) {
+        *hi = *lo = 0u;
+        return;
+    }
+    const unsigned long long m = bits & 0xFFFFFFFFFFFFFull;   // 52 fraction bits
+    *hi = sign | ((uint32_t)(E + 127) << 23) | ((uint32_t)(m >> 42) << 13);
+    const unsigned long long r = m & ((1ull << 42) - 1);      // value r 2^(E - 52)
+    if (r == 0ull) {
+        *lo = 0u;
+        return;
+    }
+    const int lz = __clzll((long long)r);                      // leading one at bit 63 - lz
+    const int El = E - 52 + (63 - lz);
+    if (El < -126) {
+        *lo = 0u;
+        return;
+    }
+    const uint32_t frac = (uint32_t)((r << (lz + 1)) >> 41);   // the 23 bits after the leading one
+    *lo = (((sign | ((uint32_t)(El + 127) << 23) | frac) + 0x1000u) & 0xFFFFE000u);
+}
+
+// acc 2^sh in FP64 from the FP32 accumulator bits by exponent arithmetic, with
+// ldexp only for FP32 subnormals and results outside the FP64 normal range.
+__device__ __forceinline__ double scale_out(uint32_t a, int sh) {
+    const int e = (int)((a >> 23) & 0xff);
+    if (e == 0 || e == 255) return ldexp((double)__uint_as_float(a), sh);
+    const int E = e - 127 + sh + 1023;
+    if (E <= 0 || E >= 2047) return ldexp((double)__uint_as_float(a), sh);
+    const unsigned long long b = ((unsigned long long)(a & 0x80000000u) << 32) | ((unsigned long long)E << 52) |
+                                 ((unsigned long long)(a & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
 }
 
 // Exponent e with 2^-e x in [1, 2) for the largest magnitude x given by its bit
@@ -96,23 +135,29 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
     for (int r = threadIdx.x; r < kTcM; r += kTcThreads) row_max[r] = 0ull;
     for (int c = threadIdx.x; c < kTcN; c += kTcThreads) col_max[c] = 0ull;
     __syncthreads();
+    // magnitudes compared as integers (the bit patterns of non-negative doubles
+    // are ordered like their values)
+    constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
     for (int c = o.beg; c < o.end; ++c) {
         const GemmIn in = ins[c];
         const double aa = fabs(in.alpha);
+        const unsigned long long* Ab = (const unsigned long long*)in.A;
+        const unsigned long long* Bb = (const unsigned long long*)in.B;
         for (int r = warp; r < kTcM; r += kTcThreads / 32) {
             const int gm = tl.m0 + r;
             if (gm >= o.M) break;
-            double mx = 0.0;
-            for (int k = lane; k < in.K; k += 32) mx = fmax(mx, fabs(in.A[(int64_t)gm * in.lda + k]));
-            for (int d = 16; d > 0; d >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, d));
-            if (lane == 0 && mx * aa > 0.0) atomicMax(&row_max[r], (unsigned long long)__double_as_longlong(mx * aa));
+            unsigned long long mx = 0ull;
+            for (int k = lane; k < in.K; k += 32) mx = max(mx, Ab[(int64_t)gm * in.lda + k] & kAbs);
+            for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+            const double mxa = __longlong_as_double((long long)mx) * aa;
+            if (lane == 0 && mxa > 0.0) atomicMax(&row_max[r], (unsigned long long)__double_as_longlong(mxa));
         }
         for (int n = threadIdx.x; n < kTcN; n += kTcThreads) {
             const int gn = tl.n0 + n;
             if (gn >= o.N) continue;
-            double mx = 0.0;
-            for (int k = 0; k < in.K; ++k) mx = fmax(mx, fabs(in.B[(int64_t)k * in.ldb + gn]));
-            if (mx > 0.0) atomicMax(&col_max[n], (unsigned long long)__double_as_longlong(mx));
+            unsigned long long mx = 0ull;
+            for (int k = 0; k < in.K; ++k) mx = max(mx, Bb[(int64_t)k * in.ldb + gn] & kAbs);
+            if (mx > 0ull) atomicMax(&col_max[n], mx);
         }
     }
     __syncthreads();
@@ -145,10 +190,10 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
             for (int idx = threadIdx.x; idx < kTcM * kTcK; idx += kTcThreads) {
                 const int r = idx / kTcK, k = idx % kTcK;
                 const int gm = tl.m0 + r, gk = k0 + k;
-                const double v = (gm < o.M && gk < in.K)
-                                     ? ldexp(in.alpha * in.A[(int64_t)gm * in.lda + gk], -row_sc[r]) : 0.0;
-                uint32_t hi, lo;
-                tf32_split(v, &hi, &lo);
+                uint32_t hi = 0u, lo = 0u;
+                if (gm < o.M && gk < in.K)
+                    split_scaled((unsigned long long)__double_as_longlong(in.alpha * in.A[(int64_t)gm * in.lda + gk]),
+                                 row_sc[r], &hi, &lo);
                 const uint32_t off = tc_off(r, k);
                 *(uint32_t*)(a_hi + off) = hi;
                 *(uint32_t*)(a_lo + off) = lo;
@@ -157,9 +202,9 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
             for (int idx = threadIdx.x; idx < kTcN * kTcK; idx += kTcThreads) {
                 const int k = idx / kTcN, n = idx % kTcN;
                 const int gk = k0 + k, gn = tl.n0 + n;
-                const double v = (gk < in.K && gn < o.N) ? ldexp(in.B[(int64_t)gk * in.ldb + gn], -col_sc[n]) : 0.0;
-                uint32_t hi, lo;
-                tf32_split(v, &hi, &lo);
+                uint32_t hi = 0u, lo = 0u;
+                if (gk < in.K && gn < o.N)
+                    split_scaled(((const unsigned long long*)in.B)[(int64_t)gk * in.ldb + gn], col_sc[n], &hi, &lo);
                 const uint32_t off = tc_off(n, k);
                 *(uint32_t*)(b_hi + off) = hi;
                 *(uint32_t*)(b_lo + off) = lo;
@@ -216,7 +261,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tf32x3(const GemmOut* __res
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = tl.n0 + c0 + j;
-                    const double acc = ldexp((double)__uint_as_float(v[j]), row_sc[warp * 32 + lane] + col_sc[c0 + j]);
+                    const double acc = scale_out(v[j], row_sc[warp * 32 + lane] + col_sc[c0 + j]);
                     if (col < o.N) cr[col] = o.beta == 0.0 ? acc : o.beta * cr[col] + acc;
                 }
             }

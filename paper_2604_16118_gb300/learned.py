@@ -164,15 +164,21 @@ def choose(net, wl):
     return sel if sel is not None else PLAIN
 
 
-def solve(ctx, net, wl, n_steps, r_max=64):
+def solve(ctx, net, wl, n_steps, r_max=64, params=None, stop=None, trace=None):
     """Alg. 2 steps with the learned parameters, each judged against the plain
     guarantee of Thm. conv: the energy after a learned step must satisfy
     E(x') <= E_* + t_eig (E(x) - E_*) with E_* the step's lower Ritz value (all
     energies lambda - gamma, since the shifts of the two parameter sets differ).
     A step that misses it is redone from x with the plain parameters, which are
     kept from then on (as they are when the prediction is unusable).  Returns
-    (energies at the start of every step, flops per step, parameters per step)."""
-    learned = choose(net, wl)
+    (energies at the start of every step, flops per step, parameters per step).
+    params: a (c_0, margin) to use instead of the network's choice (PLAIN runs
+    the plain solver); stop(E): ends the run when true for the energy after a
+    step; trace: a list that receives (seconds since the start, energy) after
+    every step (the context synchronised)."""
+    import time
+    t0 = time.perf_counter()
+    learned = params if params is not None else choose(net, wl)
     plain_s = setup(ctx, wl, PLAIN[0], PLAIN[1], r_max)
     try:
         learned_s = setup(ctx, wl, learned[0], learned[1], r_max) if learned != PLAIN else plain_s
@@ -186,8 +192,10 @@ def solve(ctx, net, wl, n_steps, r_max=64):
     t_eig = SOLVER["t_eig"]
     for _ in range(n_steps):
         S = plain_s if use_plain else learned_s
-        x_prev = x.export(), x.bonds()
-        st_prev = nat.SolverState(st.eta_res, st.n, st.last_tries, st.last_sum_norms, st.fp64_locked)
+        if S is learned_s:
+            # kept for a redo with the plain parameters
+            x_prev = x.export(), x.bonds()
+            st_prev = nat.SolverState(st.eta_res, st.n, st.last_tries, st.last_sum_norms, st.fp64_locked)
         x, info = nat.eigensolve_step(ctx, S["W"], S["p"], S["sp"], st, x)
         e = info["lambda"] - S["gamma"]
         if pending is not None:
@@ -210,7 +218,10 @@ def solve(ctx, net, wl, n_steps, r_max=64):
         E.append(e)
         F.append(info["flops"])
         used.append(PLAIN if S is plain_s else learned)
-        if info["converged"]:
+        if trace is not None:
+            ctx.sync()
+            trace.append((time.perf_counter() - t0, e))
+        if info["converged"] or (stop is not None and stop(e)):
             break
         if S is learned_s and "lambda_star" in info:
             pending = (e, info["lambda_star"] - S["gamma"])
