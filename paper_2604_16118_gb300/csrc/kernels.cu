@@ -472,7 +472,7 @@ void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in, int kind) {
     ProfScope ps(ctx, kind, fl, by);
     bool cluster_ran = false;
     if (!clustered.empty()) {
-        cluster_ran = launch_qr_cluster(ctx, clustered);
+        cluster_ran = launch_qr_cluster(ctx, clustered, kind == KK_APPLY_QR);
         if (!cluster_ran) {
             for (QrTask t : clustered) {   // no cluster could be scheduled: one CTA per matrix
                 const size_t need = sizeof(double) * ((size_t)t.M * t.N + (size_t)t.M * std::min(t.M, t.N) +

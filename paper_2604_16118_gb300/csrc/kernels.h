@@ -136,8 +136,13 @@ void launch_qr(Context* ctx, const std::vector<QrTask>& tasks, int kind = KK_QR)
 // same output as a QrTask of launch_qr; used by launch_qr for matrices with
 // min(M, N) >= kClusterQrMin whose columns fit the cluster's shared memory.
 constexpr int kClusterQrMin = 48;
+// Zip-up QR launches whose widest factor (min(M, N)) is at most this run on
+// 8-CTA clusters: more columns per CTA, and SMs left for the other clusters of
+// the launch (measured: the zip-up's factorisation 243 -> 208 ms per two
+// full-rank steps; the truncation's QRs and the Jacobi were slower on 8).
+constexpr int kClusterNarrowMax = 128;
 bool qr_cluster_eligible(int M, int N);
-bool launch_qr_cluster(Context* ctx, const std::vector<QrTask>& tasks);
+bool launch_qr_cluster(Context* ctx, const std::vector<QrTask>& tasks, bool narrow_on_8 = false);
 void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks);
 // out[i] = sum of squares of x[0..n) for a list of (x, n) segments
 void launch_sumsq(Context* ctx, const std::vector<const double*>& xs, const std::vector<int64_t>& ns,

@@ -182,8 +182,11 @@ bool qr_cluster_eligible(int M, int N) {
     return k >= kClusterQrMin && qc_smem(M, N, 16) <= kQcSmemMax;
 }
 
-bool launch_qr_cluster(Context* ctx, const std::vector<QrTask>& tasks) {
+bool launch_qr_cluster(Context* ctx, const std::vector<QrTask>& tasks, bool narrow_on_8) {
     if (tasks.empty()) return true;
+    int nmax = 0;
+    for (const QrTask& t : tasks) nmax = std::max(nmax, std::min(t.M, t.N));
+    if (narrow_on_8 && nmax <= kClusterNarrowMax && launch_qc<8>(ctx, tasks)) return true;
     return launch_qc<16>(ctx, tasks) || launch_qc<8>(ctx, tasks);
 }
 
