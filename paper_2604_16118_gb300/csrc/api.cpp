@@ -39,6 +39,7 @@ namespace bsm {
 Context* context_of(bsmps_ctx c) {
     BSM_REQUIRE(c != nullptr, BSMPS_ERR_INVALID_ARG, "null context");
     BSM_CUDA(cudaSetDevice(c->c.device));
+    (void)cudaGetLastError();   // see C(): a stale error is not this call's
     return &c->c;
 }
 
@@ -196,6 +197,10 @@ bsmps_status guarded(bsmps_ctx ctx, F&& f) {
 bsm::Context* C(bsmps_ctx ctx) {
     BSM_REQUIRE(ctx != nullptr, BSMPS_ERR_INVALID_ARG, "null context");
     BSM_CUDA(cudaSetDevice(ctx->c.device));
+    // an error another caller left in the runtime's last-error slot (not a
+    // sticky device error, which every later call reports anyway) must not be
+    // taken for the result of this call's launches
+    (void)cudaGetLastError();
     return &ctx->c;
 }
 

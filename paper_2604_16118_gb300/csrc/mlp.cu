@@ -372,6 +372,7 @@ bsmps_status mlp_guard(bsm::Context* ctx, const std::function<void()>& f) {
 bsm::Context* ctx_of(bsmps_mlp m) {
     if (!m || !m->ctx) throw bsm::Error(BSMPS_ERR_INVALID_ARG, "null MLP handle");
     BSM_CUDA(cudaSetDevice(m->ctx->device));
+    (void)cudaGetLastError();   // a stale error left by another caller is not this call's
     return m->ctx;
 }
 }  // namespace
