@@ -119,3 +119,47 @@ def test_truncate_with_emulated_block_products(nat, ctx, min_log2):
             assert np.sqrt(max(OB.dot(d, d), 0.0)) <= eps_rel * nrm * (1 + 1e-6) + 1e-12 * nrm
     finally:
         ctx.set_gemm_emulation(0)
+
+
+@pytest.mark.parametrize("eps_rel", [1e-7, 1e-9])
+@pytest.mark.parametrize("precond", [0, 48])
+def test_truncate_graded_spectrum(nat, ctx, precond, eps_rel):
+    """x = sum_i 10^(-2i) y_i, i = 0..5, with y_i random iterates of rank 48
+    (spinless K = 20, N = 10): each term lives in its own subspace of the wide
+    middle sectors (spaces up to 252), so the bond spectra of the sum fall in six
+    groups from 1 to 1e-10 -- the regime in which the FP32 Jacobi start has to
+    rotate the small columns too (sectors up to 119 wide).  The cuts fall
+    between groups (1e-7) and inside the range of singular values near 1e-8 of
+    the largest, below what FP32 resolves (1e-9).  With and without that start
+    the truncation keeps the oracle's dims and norm, and its discarded norm
+    (singular values fixed to about 1e-16 of the largest) agrees to 1e-4.  (A
+    distance ||z - x|| from the contracted <d, d> would sit below its own
+    rounding floor, sqrt(eps) ||x||, here.)"""
+    from oracle import fermion as OF
+    K, N, r = 20, 10, 48
+    species = OF.site_species(K, 0)
+    dims = OB.default_dims(species, (N, 0), r)
+    n = OB.BSMPS(species, (N, 0), dims, [dict() for _ in range(K)]).layout()[1]
+    ctx.set_jacobi_precond(precond)
+    try:
+        x = ox = None
+        for i in range(6):
+            w = 10.0 ** (-2 * i)
+            vals = random_block_values(n, 90 + i)
+            y = nat.mps_create(ctx, K, 0, N, 0, r, vals)
+            oy = OB.random_mps(species, (N, 0), r, vals)
+            if x is None:
+                x, ox = nat.add(ctx, y, y, w, 0.0), OB.add(oy, oy, w, 0.0)
+            else:
+                x, ox = nat.add(ctx, x, y, 1.0, w), OB.add(ox, oy, 1.0, w)
+        assert x.bonds() == ox.bonds
+        assert max(max(b.values()) for b in ox.bonds if b) >= 96   # sectors wide enough for the FP32 start
+        nrm = float(np.sqrt(OB.dot(ox, ox)))
+        z, dt, _ = nat.truncate(ctx, x, eps_rel * nrm)
+        oz, odt, _ = OB.truncate(ox, eps_rel * nrm)
+        assert z.bonds() == oz.bonds
+        gz = OB.dot(to_oracle_k(z, species, N), to_oracle_k(z, species, N))
+        assert abs(gz - OB.dot(oz, oz)) <= 1e-12 * OB.dot(oz, oz)
+        assert odt > 0.1 * eps_rel * nrm and abs(dt - odt) <= 1e-4 * odt
+    finally:
+        ctx.set_jacobi_precond(48)
