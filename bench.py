@@ -17,8 +17,21 @@ The whole step's algorithmic flops and time are reported beside it ("step").
 (the solver's policy falls back to FP64 once the split error estimate nears the
 residual tolerance).
 
-Other workloads: hubbard_e1 (the Alg. 2 trajectory from e_1), hubbard_tta
-(time to convergence from e_1), coulomb14_alg4_D4, coulomb14_alg3, ozaki_gemm.
+Other workloads (--workload):
+  tta_learned   time to |E - E_ref| <= 1e-8 Eh on the config-1 chain from e_1,
+                FP64 / split precision x plain / learned controller parameters
+  tta_k12       the same chain from its random rank-32 start, golden constants
+  hubbard_tta   the config-2 trajectory from e_1 (time to rho <= 1e-8 or to the
+                settled energy)
+  hubbard_e1    Alg. 2 steps of that trajectory
+  batched       128 independent Hamiltonians: recorded CUDA graph, one batched
+                call, one call per instance
+  mlp           the controller network's training step on the tensor cores
+  coulomb14_alg3, coulomb14_alg4_D4   the paper's K = 14 Coulomb-like runs
+  ozaki_gemm    the FP64 GEMM emulated on the tensor cores vs cuBLAS DGEMM
+  profile_step, profile_apply, profile_truncation   fixed runs for profilers
+--jacobi-precond sets the k from which truncation SVDs start from an FP32
+Jacobi (0: never).
 Usage (contract): python bench.py --gpus N --steps K --warmup W [--impl reference]
 """
 
