@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_jacobi_cluster(const JacTas
             dst[e] = v;
             f += v * v;
             const int j = (int)(e / k), i = (int)(e % k);
-            tk.V[off + e] = i == beta * b + j ? 1.0 : 0.0;
+            if (!tk.v_given) tk.V[off + e] = i == beta * b + j ? 1.0 : 0.0;
         }
     }
     f = dev::block_sum(f, red);

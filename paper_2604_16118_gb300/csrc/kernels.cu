@@ -595,7 +595,9 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
                 gi.push_back({pr.Qp, jt.G, jt.k, jt.k, jt.k, 0, 1.0});
                 jt.G = G1;
                 R[mid_i[pr.m]] = G1;   // the rotated G that step 4 reads
-                jt.V = pr.V1;
+                // the cluster Jacobi rotates Qp's columns: V = Qp V1 without a product
+                jt.V = pr.Qp;
+                jt.v_given = 1;
             }
             launch_gemm(ctx, go, gi, KK_SVD);
         } else {
@@ -605,7 +607,14 @@ void launch_svd(Context* ctx, const std::vector<SvdTask>& tasks) {
     }
     {
         ProfScope ps(ctx, KK_SVD, fl, by);
-        if (!mid.empty() && !launch_jacobi_cluster(ctx, mid)) {
+        if (!mid.empty() && launch_jacobi_cluster(ctx, mid)) {
+            for (const Pre& pr : pre) V[mid_i[pr.m]] = pr.Qp;   // Qp V1, in place
+            pre.clear();
+        } else if (!mid.empty()) {
+            // one CTA per matrix: those kernels start from the identity, so the
+            // preconditioned tasks accumulate V1 and V = Qp V1 follows below
+            for (size_t m = 0; m < mid.size(); ++m) mid[m].v_given = 0;
+            for (const Pre& pr : pre) mid[pr.m].V = pr.V1;
             for (const JacTask& t : mid) (t.k <= kSmemJacobiMax ? small : large).push_back(t);
         }
         if (!small.empty()) {

@@ -73,6 +73,8 @@ struct JacTask {
     double* Sraw;
     int k;
     int smem;        // 1: iterate in shared memory (one CTA per matrix)
+    int v_given = 0; // 1: V holds the starting columns (the cluster kernel rotates them
+                     // instead of the identity); the other Jacobi kernels ignore it
 };
 
 // Jacobi of several large matrices in one cooperative launch: the disjoint
