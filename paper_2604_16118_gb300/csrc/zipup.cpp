@@ -125,6 +125,12 @@ struct ZipJob {
         }
         T.assign(nb, nullptr);
         for (int i = 0; i < nb; ++i) T[i] = tsize > 0 ? (double*)ctx->alloc((size_t)tsize * sizeof(double)) : nullptr;
+        // the site's MPO entries by (s', b), in entry order
+        std::vector<std::vector<int>> by_sob((size_t)2 * wr);
+        for (int ei = 0; ei < (int)W->entries[t].size(); ++ei) {
+            const MpoEntry& e = W->entries[t][ei];
+            if (e.so >= 0 && e.so < 2 && e.b >= 0 && e.b < wr) by_sob[(size_t)e.so * wr + e.b].push_back(ei);
+        }
         for (const TB& tb : tbs) {
             const Charge m = yb.q[tb.mi], m2 = ex[t + 1].q[tb.em];
             const int ldc = ex[t + 1].dim[tb.em];
@@ -137,9 +143,8 @@ struct ZipJob {
                 for (int i = 0; i < nb; ++i) {
                     GemmOut o{T[i] + stack_off[tb.em] + (int64_t)tb.r0 * ldc + coff, yb.dim[tb.mi], ncols, ldc,
                               (int)ins.size(), (int)ins.size(), 0.0};
-                    for (int ei = 0; ei < (int)W->entries[t].size(); ++ei) {
+                    for (const int ei : by_sob[(size_t)tb.so * wr + b]) {
                         const MpoEntry& e = W->entries[t][ei];
-                        if (e.so != tb.so || e.b != b) continue;
                         const int la = X.bonds[t].find(m - W->charges[t][e.a]);
                         if (la < 0) continue;
                         const int xb = xlook[la * 2 + e.si];
