@@ -243,6 +243,22 @@ struct Context {
     }
 };
 
+// Joins the context's second stream back into its stream when the scope ends
+// with the fork still open (an error unwinding between fork and join): work
+// released after this point in stream order then also waits for the side
+// stream's kernels.  A no-op after an explicit join_side().
+struct SideJoin {
+    Context* ctx;
+    explicit SideJoin(Context* c) : ctx(c) {}
+    ~SideJoin() {
+        if (ctx && ctx->side_open) {
+            cudaEventRecord(ctx->join_ev, ctx->side);
+            cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0);
+            ctx->side_open = false;
+        }
+    }
+};
+
 // RAII bracket of one launch for the optional profiler.
 struct ProfScope {
     Context* ctx;
