@@ -366,8 +366,9 @@ BSMPS_API bsmps_status bsmps_apply_zipup_batch(bsmps_ctx ctx, int n, const bsmps
  * plan.  bsmps_plan_launch replays every launch of the batch with one graph
  * launch on the context's stream: it reads the blocks x[i] hold at that point
  * in stream order (update them in place with bsmps_mps_write) and overwrites
- * the plan's outputs.  ctx: a context created with a non-default stream.  W, x:
- * n handles each, which must outlive the plan; shift: n values, read now.
+ * the plan's outputs.  ctx: a context created with a non-default stream, which
+ * must outlive the plan.  W, x: n handles each, which must outlive the plan;
+ * shift: n values, read now.
  * y: n new handles to the outputs, whose blocks belong to the plan (valid from
  * the first bsmps_plan_launch until bsmps_plan_destroy; bsmps_mps_destroy on
  * them releases the handle only).  flops (may be NULL): algorithmic FP64 flops
