@@ -246,7 +246,9 @@ struct Context {
 // Joins the context's second stream back into its stream when the scope ends
 // with the fork still open (an error unwinding between fork and join): work
 // released after this point in stream order then also waits for the side
-// stream's kernels.  A no-op after an explicit join_side().
+// stream's kernels.  Constructed with the context only by the scope that forks
+// (nullptr otherwise, so that a nested scope never joins an outer fork); a
+// no-op after an explicit join_side().
 struct SideJoin {
     Context* ctx;
     explicit SideJoin(Context* c) : ctx(c) {}

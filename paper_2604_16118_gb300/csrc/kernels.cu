@@ -489,7 +489,7 @@ void launch_qr(Context* ctx, const std::vector<QrTask>& tasks_in, int kind) {
     QrTask* d_small = small.empty() ? nullptr : s.up(small);
     QrTask* d_large = large.empty() ? nullptr : s.up(large);
     const bool overlap = cluster_ran && (d_small || d_large) && !ctx->profiling && !ctx->rec && !ctx->side_open;
-    SideJoin guard(ctx);   // declared after s: joins before s releases the task lists
+    SideJoin guard(overlap ? ctx : nullptr);   // after s: joins before s releases the task lists
     const cudaStream_t st = overlap ? ctx->fork_side() : ctx->stream;
     if (d_small) {
         BSM_CUDA(cudaFuncSetAttribute(k_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));

@@ -568,7 +568,7 @@ void right_sweep_sitewise(Context* ctx, TruncJob& J) {
         // on the context's second stream (joined before the singular values
         // are read; their buffers live in s until the end of the bond)
         const bool overlap = !site_sec.empty() && !gen_sec.empty() && !ctx->profiling && !ctx->rec;
-        SideJoin guard(ctx);   // after s: an error between fork and join still joins before s is released
+        SideJoin guard(overlap ? ctx : nullptr);   // after s: an error between fork and join still joins first
         if (!site_sec.empty()) {
             std::vector<SvdSiteTask> st;
             std::vector<SvdPart> parts;
